@@ -1,0 +1,296 @@
+"""Benchmark: EB multi-material Poisson solves to 1e-10 relative residual.
+
+Workload (one step = one complete solve from phi = 0): the 2D multi-material
+rod-plane problem on 1024 x 1024 cells -- rod electrode at phi = 1 over a
+grounded plane, rough dielectric slab eps_r = 4, seeded surface charge on the
+dielectric interface, Gaussian space-charge filament -- solved by FP32
+V-cycles inside FP64 defect correction until max|r| <= 1e-10 max|b|.
+Geometry and the multigrid hierarchy are built once (timed separately).
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank solves its own copy
+of the workload (independent problems, weak scaling, no collective on the
+data path).  ``--impl reference`` times the CPU FP64 oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson cells/s at 1e-10 rel. residual"
+WORKLOAD = "2D multi-material rod-plane 1024x1024, rough dielectric eps_r=4, surface charge, " \
+           "FP32 V-cycles in FP64 defect correction, tol 1e-10"
+N_CELLS_SIDE = 1024
+REF_SIDE = 256   # oracle sample size per step
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        time.sleep(0.1)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def cpu_oracle_sample(side=REF_SIDE, reps=1):
+    """Time the FP64 oracle (geometry + assembly + sparse LU) on the same
+    workload at side x side cells; returns (cells/s, seconds, cells)."""
+    import oracle
+    from paper_1809_03745_gb300 import workloads as W
+    desc, S, sig = W.c2_inputs(side)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.solve(desc, s=S, sigma=sig)
+    dt = time.perf_counter() - t0
+    return side * side * reps / dt, dt, side * side * reps
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        cpu_oracle_sample(REF_SIDE)
+    times = []
+    for _ in range(args.steps):
+        _, dt, _ = cpu_oracle_sample(REF_SIDE)
+        times.append(dt)
+    ms = 1000.0 * sum(times) / len(times)
+    value = REF_SIDE * REF_SIDE / (ms / 1000.0)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("1024x1024", f"{REF_SIDE}x{REF_SIDE} sample"),
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                             "sample": f"full oracle pipeline (geometry, assembly, SuperLU solve) on the same "
+                                       f"workload at {REF_SIDE}x{REF_SIDE} cells per step"},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1809_03745_gb300 import ebpoisson as E
+    from paper_1809_03745_gb300 import workloads as W
+    E.load(build_if_missing=True)
+
+    desc, S, sig = W.c2_inputs(N_CELLS_SIDE)
+    ncell = N_CELLS_SIDE * N_CELLS_SIDE
+    t0 = time.perf_counter()
+    g = E.Geometry(desc, device=dev)
+    P = E.Poisson(g, precision="mixed", tol=1e-10, max_cycles=200)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    rhs = torch.from_numpy(S).to(dev)
+    sigma = torch.from_numpy(sig).to(dev)
+    phi = torch.zeros(2, ncell, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        phi.zero_()
+        _, info = P.solve(rhs, sigma, phi)
+        return info
+
+    for _ in range(max(args.warmup, 3)):
+        info = step()
+    assert info["status"] == 0 and info["rel_res"] <= 1e-10, info
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    infos = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        infos.append(step())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    # dominant kernel: one colour sweep of the FP32 finest-level smoother, timed live
+    kms, kbytes = P.profile(0, reps=200)
+    rms, rbytes = P.profile(1, reps=100)
+    clk = clocks.stop()
+    ms = sum(ms_steps) / len(ms_steps)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * ncell / (ms / 1000.0)
+
+    # end to end through the public API with host buffers
+    h_rhs = torch.from_numpy(S).pin_memory()
+    h_sig = torch.from_numpy(sig).pin_memory()
+    h_phi = torch.empty(2, ncell, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        d_rhs = h_rhs.to(dev, non_blocking=True)
+        d_sig = h_sig.to(dev, non_blocking=True)
+        d_phi = torch.zeros(2, ncell, dtype=torch.float64, device=dev)
+        _, inf = P.solve(d_rhs, d_sig, d_phi)
+        h_phi.copy_(d_phi, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e = world * ncell / (sum(e2e_ms) / len(e2e_ms) / 1000.0)
+
+    if rank != 0:
+        return
+    peaks = _peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = kbytes / (kms / 1000.0) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("smooth_dense_fp32_1024", None)
+        except Exception:
+            traffic = None
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            import oracle
+            oracle.build()
+            v, dt, cells = cpu_oracle_sample(REF_SIDE, reps=3)
+            cpu = {"value": v, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                   "sample": f"3 complete oracle solves (geometry, assembly, SuperLU) of the same workload at "
+                             f"{REF_SIDE}x{REF_SIDE} cells, {dt:.1f} s"}
+        except Exception as exc:  # the baseline is reported, never required
+            cpu = {"value": None, "unit": "cells/s", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+    launches = int(statistics.median([i["kernel_launches"] for i in infos]))
+    line = {
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": ncell, "levels": g.info["n_levels"],
+                   "vcycles_per_solve": infos[-1]["vcycles"], "outer_iters": infos[-1]["outer_iters"],
+                   "rel_res": infos[-1]["rel_res"], "setup_s": setup_s,
+                   "l2": "256 MB buffer written between timed solves",
+                   "parallelism": f"{world} independent solves (one per GPU)"},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": "k_smooth_dense<float> (one red-black colour, finest level)",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic, "peak_source": "measured" if peaks else "fallback",
+                     "ms_per_launch": kms, "bytes_per_launch": kbytes,
+                     "resid_restrict_gbs": rbytes / (rms / 1000.0) / 1e9},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": "cells/s", "h2d_bytes_per_step": int(3 * ncell * 8),
+                "d2h_bytes_per_step": int(2 * ncell * 8)},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * ebpoisson.h -- C ABI of the GB300 embedded-boundary multi-material Poisson
+ * solver.
+ *
+ * The library solves the electrostatic equation of Marskar, arXiv:1809.03745,
+ * Sec. 2.1, Eq. (poisson):
+ *
+ *     div(eps_r grad phi) = -rho / eps0
+ *
+ * on a Cartesian grid whose cells may be cut by embedded boundaries (EBs):
+ * electrodes (Dirichlet, held at a potential) and dielectric interfaces across
+ * which eps_r jumps and on which a surface charge sigma sits (Sec. 3.3.1,
+ * Eq. matching).  The discretisation is the cut-cell finite-volume method of
+ * Sec. 3.1 and 3.3 (integral form Eq. poisson_integral, centroid-interpolated
+ * face fluxes, ray-cast EB normal-derivative stencils Eq. bndry_stencil,
+ * multifluid boundary state eliminated); the linear system is solved by
+ * geometric multigrid V-cycles with red-black Gauss-Seidel smoothing
+ * (Sec. 3.3.2), optionally in FP32 inside an FP64 defect-correction loop.
+ *
+ * Conventions shared by every entry point:
+ *   - Cells are indexed x fastest, then y, then z: c = i + n0*(j + n1*k).
+ *     Cell i covers [lo + i h, lo + (i+1) h]; its centre is lo + (i + 1/2) h.
+ *   - Two phases: 0 = gas (eps_gas), 1 = dielectric (eps_diel).  Per-phase
+ *     fields are laid out [phase][cell].  Single-phase problems (no dielectric)
+ *     still use two phase slots; slot 1 is ignored on input and zero on output.
+ *   - "d_" arguments are DEVICE pointers owned by the caller, on the device
+ *     that was current when the handle was created; "h_" arguments are host
+ *     pointers.  The library never keeps a caller pointer past the call.
+ *   - Work is enqueued on the given CUDA stream (a cudaStream_t passed as
+ *     void*, NULL = legacy default stream).  Calls that return information
+ *     (counts, convergence) synchronise that stream before returning.
+ *   - Every call returns an eb_status; no exception crosses the ABI.  On error
+ *     the outputs are unspecified and eb_last_error() describes the failure.
+ *   - Handles are not thread-safe: one host thread per handle at a time.
+ */
+#ifndef EBPOISSON_H
+#define EBPOISSON_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EB_OK = 0,
+  EB_ERR_INVALID = 1,       /* bad argument or description */
+  EB_ERR_OOM = 2,           /* device allocation failed or budget exceeded */
+  EB_ERR_NOT_CONVERGED = 3, /* cycle cap reached before the tolerance */
+  EB_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+  EB_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+  EB_ERR_UNSUPPORTED = 6,   /* geometry outside the method's model (see eb_geom_build) */
+  EB_ERR_BUSY = 7           /* serving queue full / result not ready */
+} eb_status;
+
+/* Static description of a status code; never freed. */
+const char* eb_status_str(eb_status s);
+/* Detail of the last error raised on the calling thread; valid until the next call. */
+const char* eb_last_error(void);
+
+/* ------------------------------------------------------------- geometry
+ * Implicit functions (Sec. 3.1, 3.2): each region is the NEGATIVE set of a
+ * function s(x) built by CSG from primitives.  All formulas below are
+ * evaluated in double precision in the stated order; 2D problems use z = 0.
+ */
+enum {
+  EB_PRIM_SPHERE = 0,    /* p = [cx, cy, cz, r]:              |x - c| - r */
+  EB_PRIM_CAPSULE = 1,   /* p = [ax, ay, az, bx, by, bz, r]:  dist(x, segment ab) - r */
+  EB_PRIM_HALFSPACE = 2, /* p = [nx, ny, nz, d]:              n.x - d */
+  EB_PRIM_SINE = 3,      /* p = [up, c, A, k, ph, t]:         x[up] - (c + A sin(2 pi k x[t] + ph)) */
+  EB_PRIM_CYLINDER = 4,  /* p = [axis, px, py, pz, r, lo, hi]: max(dist_to_axis - r, lo - x[axis], x[axis] - hi) */
+  EB_PRIM_BOX = 5        /* p = [lox, loy, loz, hix, hiy, hiz]: max_k max(lo_k - x_k, x_k - hi_k) */
+};
+enum { EB_CSG_PRIM = 0, EB_CSG_UNION = 1, EB_CSG_INTERSECT = 2, EB_CSG_NEGATE = 3 };
+enum { EB_BC_NEUMANN = 0, EB_BC_DIRICHLET = 1 };
+
+#define EB_MAX_PRIMS 32
+#define EB_MAX_NODES 64
+#define EB_MAX_ELECTRODES 4
+
+typedef struct {
+  int kind;      /* EB_PRIM_* */
+  double p[10];  /* parameters, see above */
+} eb_prim;
+
+typedef struct {
+  int op;   /* EB_CSG_*: PRIM -> primitive a; UNION -> min(a,b); INTERSECT -> max(a,b); NEGATE -> -a */
+  int a, b; /* primitive index (PRIM) or child node indices, children listed before parents */
+} eb_csg;
+
+typedef struct {
+  int dim;        /* 2 or 3 */
+  int n[3];       /* cells per axis; each a multiple of 8 and >= 8; n[2] ignored in 2D */
+  double lo[3];   /* lower domain corner */
+  double h;       /* cell size, the same on every axis */
+  const eb_prim* prims;
+  int n_prims;    /* <= EB_MAX_PRIMS */
+  const eb_csg* nodes;
+  int n_nodes;    /* <= EB_MAX_NODES */
+  int electrode_root;                       /* node whose negative set is all electrodes, -1 = none */
+  int n_electrodes;                         /* <= EB_MAX_ELECTRODES */
+  int electrode_node[EB_MAX_ELECTRODES];    /* each electrode's own node */
+  double electrode_phi[EB_MAX_ELECTRODES];  /* each electrode's potential */
+  int dielectric_root;                      /* node whose negative set is the dielectric, -1 = none */
+  double eps_gas, eps_diel;                 /* relative permittivities */
+  int bc_type[6];     /* EB_BC_* per wall: xlo, xhi, ylo, yhi, zlo, zhi */
+  double bc_value[6]; /* Dirichlet value per wall (Neumann walls are homogeneous) */
+} eb_geom_desc;
+
+typedef struct eb_geom eb_geom;
+
+#define EB_MAX_LEVELS 16
+typedef struct {
+  int dim;
+  int n_phase;                   /* 1 without a dielectric, else 2 */
+  long long n_cells;             /* finest level */
+  long long n_dof;               /* fluid fragments with an unknown, finest level */
+  long long n_eb;                /* cut cells with at least one unknown (the EB list) */
+  long long n_irregular;         /* cells with a sparse operator row, finest level */
+  int n_levels;                  /* multigrid levels (finest = 0) */
+  int level_n[EB_MAX_LEVELS][3]; /* cells per axis on each level */
+  long long stencil_order[3];    /* EB stencils of order 2, order 1, least squares */
+  long long device_bytes;        /* device memory held by the handle */
+} eb_geom_info;
+
+/* Cut-cell geometry pass (Sec. 3.1): node labels, edge crossings (exactly 60
+ * bisection halvings on the implicit function, midpoint of the final bracket),
+ * face apertures and centroids, EB area, normal and centroid (EB normal from
+ * the apertures by the divergence theorem), volume fractions by the divergence
+ * theorem; then the coarsened multigrid hierarchy (Sec. 3.1, 3.3.2), stopping
+ * where a coarse cell would be multi-valued or hold two kinds of boundary.
+ * A node with s = 0 belongs to the non-negative side.
+ * Errors: EB_ERR_INVALID (bad sizes, h, tree), EB_ERR_UNSUPPORTED (a cell cut
+ * by an electrode and the dielectric at once, a face with four crossings, a
+ * cell whose crossings do not form one loop, an EB stencil with no candidate
+ * cells), EB_ERR_OOM, EB_ERR_CUDA.  *out is NULL on error. */
+eb_status eb_geom_build(const eb_geom_desc* desc, void* stream, eb_geom** out);
+eb_status eb_geom_query(const eb_geom* g, eb_geom_info* out);
+void eb_geom_destroy(eb_geom* g);
+
+/* Device copies of the finest-level geometry, for inspection.  Any pointer
+ * may be NULL to skip it.  Sizes: flags [n_cells] (bit0 gas unknown, bit1
+ * dielectric unknown, bit2 sparse row); kappa [2][n_cells]; eb_cell [n_eb]
+ * ascending cell indices of the EB list; eb_area [n_eb] (units of h^{D-1});
+ * eb_normal [n_eb][3] (unit, out of the gas fragment, or out of the fluid for
+ * an electrode); eb_centroid [n_eb][3] (physical); eb_kind [n_eb] (1 electrode,
+ * 2 dielectric interface); stencil_order [n_eb][2] (2, 1, 3 = least squares,
+ * 0 = phase absent). */
+typedef struct {
+  uint8_t* flags;
+  double* kappa;
+  int32_t* eb_cell;
+  double* eb_area;
+  double* eb_normal;
+  double* eb_centroid;
+  uint8_t* eb_kind;
+  int32_t* stencil_order;
+} eb_geom_arrays;
+eb_status eb_geom_export(const eb_geom* g, eb_geom_arrays* out, void* stream);
+
+/* ------------------------------------------------------------- solver */
+enum { EB_PREC_FP64 = 0, EB_PREC_MIXED = 1 };
+
+typedef struct {
+  double tol;        /* stop when max|r| <= tol * max|b| (Sec. 3.3.2), default 1e-10 */
+  int max_cycles;    /* cap on V-cycles in total, default 100 */
+  int nu1, nu2;      /* red-black Gauss-Seidel sweeps before / after the coarse correction, default 2, 2 */
+  int precision;     /* EB_PREC_FP64: FP64 V-cycles; EB_PREC_MIXED: FP32 V-cycles inside FP64 defect correction */
+  int inner_cycles;  /* FP32 V-cycles per FP64 outer iteration (mixed), default 2 */
+  int bottom_sweeps; /* relaxation sweeps on the coarsest level, default 64 */
+  int use_graph;     /* replay one iteration through a captured CUDA graph, default 1 */
+} eb_solver_opts;
+
+/* Fill opts with the defaults listed above. */
+void eb_solver_opts_default(eb_solver_opts* opts);
+
+typedef struct {
+  int status;       /* eb_status of the solve */
+  int outer_iters;  /* FP64 residual evaluations after the initial one */
+  int vcycles;      /* V-cycles in total */
+  double rel_res;   /* final max|r| / max|b| in FP64 */
+  double bnorm;     /* max|b| */
+  long long kernel_launches; /* kernels this call launched (graph nodes counted per replay) */
+} eb_solve_info;
+
+typedef struct eb_poisson eb_poisson;
+
+/* Builds the finite-volume operator on every multigrid level (Sec. 3.3):
+ * regular cells use the implicit 2D+1-point stencil eps_p/h^2 with
+ * second-order one-sided Dirichlet walls; cut cells get a sparse FP64 row with
+ * centroid-interpolated face fluxes, ray-cast EB derivatives (order 2, then
+ * first order, then least squares) and the multifluid boundary state
+ * eliminated.  The handle keeps a reference to g; destroy the solver first. */
+eb_status eb_poisson_setup(const eb_geom* g, const eb_solver_opts* opts, void* stream, eb_poisson** out);
+void eb_poisson_destroy(eb_poisson* P);
+
+/* r = b - A phi in FP64 on the finest level, [2][n_cells], for given
+ * d_rhs = rho/eps0 [2][n_cells] sampled at cell centres and d_sigma =
+ * sigma/eps0 [n_cells] (read only on dielectric-interface cells; may be NULL
+ * for zero).  b = kappa * rhs + the boundary data (electrode and wall
+ * potentials, surface charge).  With d_phi = 0 this returns b. */
+eb_status eb_poisson_residual(eb_poisson* P, const double* d_rhs, const double* d_sigma, const double* d_phi,
+                              double* d_r, void* stream);
+
+/* Solves A phi = b to max|r| <= tol max|b|.  d_phi [2][n_cells] holds the
+ * initial guess on entry and the solution on exit (entries without an unknown
+ * are written as 0).  info may be NULL.  Returns EB_ERR_NOT_CONVERGED when the
+ * cycle cap is reached (d_phi then holds the last iterate). */
+eb_status eb_poisson_solve(eb_poisson* P, const double* d_rhs, const double* d_sigma, double* d_phi,
+                           eb_solve_info* info, void* stream);
+
+/* E = -grad phi (Sec. 2.1) at cell centres per phase, d_E [D][2][n_cells]:
+ * centred differences where both face neighbours carry an unknown of the
+ * phase across an open face, one-sided where one does, else the EB normal
+ * derivative times the normal; and the normal field -dphi/dn_in at each EB
+ * centroid per phase, d_En [n_eb][2] (EB list order), using the eliminated
+ * boundary state on dielectric interfaces. */
+eb_status eb_field_eval(eb_poisson* P, const double* d_phi, const double* d_sigma, double* d_E, double* d_En,
+                        void* stream);
+
+/* Benchmark hook (no counterpart in the paper): launches one kernel of the
+ * finest multigrid level `reps` times on `stream` between CUDA events and
+ * reports the mean duration per launch and the algorithmic bytes one launch
+ * must move.  It relaxes the solver's own work arrays (left as the last solve
+ * left them); the caller's fields are not touched.  kernel 0: one colour of
+ * the red-black Gauss-Seidel sweep of the inner-precision finest level
+ * (bytes: half of read x, read b, write x, read flags per cell); kernel 1: the
+ * fused residual + restriction of that level (read x, b, flags per fine cell,
+ * write coarse b and x). */
+eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, double* ms_per_launch, double* bytes_per_launch,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EBPOISSON_H */

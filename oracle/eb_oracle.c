@@ -487,10 +487,14 @@ static int cell_geometry(or_geom* g, long c)
   double u[3] = {0.0, 0.0, 0.0};
   int st = eb_centroid(g, I, u);
   if (st != OR_OK) return st;
-  if (!(ar > 0.0)) return OR_UNSUPPORTED;
+  if (!(ar > 0.0)) {
+    /* the boundary runs through a node only: a cut cell without an EB */
+    g->ebkind[c] = EB_NONE;
+    ar = 0.0;
+  }
   g->eba[c] = ar;
   for (int k = 0; k < 3; ++k) {
-    g->ebn[3 * c + k] = vec[k] / ar;
+    g->ebn[3 * c + k] = ar > 0.0 ? vec[k] / ar : 0.0;
     g->ebx[3 * c + k] = (k < D) ? cell_x(g, k, I[k]) + g->d.h * u[k] : 0.0;
   }
   /* volume fractions by the divergence theorem, cell-centre origin, units of h:
@@ -820,10 +824,11 @@ or_geom* or_geom_build(const or_desc* d, int* status)
     if (!g->cut[c]) continue;
     if (g->dof[0][c] < 0 && g->dof[1][c] < 0) continue;
     g->n_eb++;
-    /* an interface cell must keep both fragments as dofs: phi_B couples them */
-    if (g->ebkind[c] == EB_INTERFACE && (g->dof[0][c] < 0 || g->dof[1][c] < 0)) {
-      g->status = OR_UNSUPPORTED; g->bad_cell = c; *status = OR_UNSUPPORTED; return g;
-    }
+    /* an interface cell that keeps a single fragment (the other has no volume
+     * or no open face: the interface runs through a node) carries no
+     * interface flux; its EB is dropped */
+    if (g->ebkind[c] == EB_INTERFACE && (g->dof[0][c] < 0 || g->dof[1][c] < 0)) g->ebkind[c] = EB_NONE;
+    if (g->ebkind[c] == EB_NONE) continue;
     long I[3];
     cell_ijk(g, c, I);
     for (int p = 0; p < 2; ++p) {

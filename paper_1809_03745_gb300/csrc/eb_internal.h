@@ -1,0 +1,72 @@
+// eb_internal.h -- host-side structures shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ebpoisson.h"
+#include "eb_common.cuh"
+
+namespace ebp {
+
+// One multigrid level on the device.
+struct DevLevel {
+  Grid g{};
+  uint8_t* flags = nullptr;     // [ncell]
+  int* cut_of_cell = nullptr;   // [ncell]
+  int* irr_of_cell = nullptr;   // [ncell]
+  CutRecords R{};               // records of cut cells
+  uint8_t* order = nullptr;     // [2][ncut] EB stencil order per phase
+  int* irr_cell = nullptr;      // [nirr]
+  long long nirr = 0, nirr_red = 0;
+  // sparse rows, two slots per irregular cell: row = 2k + phase
+  int* row_ptr = nullptr;       // [2 nirr + 1]
+  int* col = nullptr;           // [nnz]
+  double* val = nullptr;        // [nnz]
+  double* diag = nullptr;       // [2 nirr]; 0 marks an absent phase
+  double* bconst = nullptr;     // [2 nirr] boundary data moved to b (finest level)
+  double* bsig = nullptr;       // [2 nirr] coefficient of sigma/eps0 (finest level)
+  long long nnz = 0;
+  int* eb_q = nullptr;          // finest level: cut-record index of each EB-list cell
+  long long n_eb = 0;
+  std::vector<void*> allocs;
+};
+
+}  // namespace ebp
+
+struct eb_geom {
+  int device = 0;
+  ebp::Csg csg{};
+  ebp::Csg* d_csg = nullptr;
+  uint8_t* d_lab = nullptr;
+  std::vector<ebp::DevLevel> L;
+  int n_phase = 1;
+  long long n_dof = 0;
+  long long stencil_counts[3] = {0, 0, 0};
+  long long bytes = 0;
+  int* d_status = nullptr;
+};
+
+namespace ebp {
+
+// error reporting
+void set_error(const std::string& msg);
+eb_status cuda_fail(cudaError_t e, const char* what);
+
+// device memory owned by a level or handle
+void* dev_alloc(std::vector<void*>& owner, size_t bytes, long long* counter, eb_status* st);
+
+// geometry and operator construction (geometry.cu)
+eb_status build_finest_geometry(eb_geom* G, cudaStream_t s);
+eb_status build_coarse_geometry(eb_geom* G, int fine, cudaStream_t s, bool* stopped);
+eb_status build_rows(eb_geom* G, int level, cudaStream_t s);
+void free_level(DevLevel& L);
+eb_status export_geometry(const eb_geom* G, eb_geom_arrays* out, cudaStream_t s);
+eb_status launch_field(const eb_geom* G, const double* phi, const double* sigma, double* E, double* En,
+                       cudaStream_t s);
+eb_status launch_rhs64(const eb_geom* G, const double* s_rhs, const double* sigma, double* b, double* bnorm,
+                       cudaStream_t s);
+
+}  // namespace ebp

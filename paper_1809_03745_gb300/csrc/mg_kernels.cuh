@@ -1,0 +1,340 @@
+// mg_kernels.cuh -- multigrid kernels (arXiv:1809.03745, Sec. 3.3.2):
+// red-black Gauss-Seidel, residual fused with conservative restriction,
+// prolongation with correction, the single-CTA bottom relaxation, and the FP64
+// defect-correction kernels.  Templated on the V-cycle precision T; sparse
+// rows of cut cells always carry FP64 coefficients.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "eb_common.cuh"
+
+namespace ebp {
+
+template <class T>
+struct Op {
+  int D;
+  int n[3];
+  long long ncell;
+  int bc[6];
+  T* x[2];  // unknown per phase
+  T* b[2];  // right-hand side per phase
+  const uint8_t* flags;
+  const int* irr_cell;
+  const int* irr_of_cell;
+  const int* row_ptr;
+  const int* col;
+  const double* val;
+  const double* diag;
+  T* tmp;  // [2 nirr] row scratch
+  long long nirr, nirr_red;
+  T ceps[2];  // eps_p / h^2
+  T h2e[2];   // h^2 / eps_p
+};
+
+__device__ __forceinline__ float inv_count(int d, float) { return 1.0f / (float)d; }
+__device__ __forceinline__ double inv_count(int d, double) {
+  // reciprocals of the possible diagonal counts (faces + 3 per Dirichlet wall face)
+  switch (d) {
+    case 1: return 1.0;
+    case 2: return 0.5;
+    case 3: return 1.0 / 3.0;
+    case 4: return 0.25;
+    case 5: return 0.2;
+    case 6: return 1.0 / 6.0;
+    case 7: return 1.0 / 7.0;
+    case 8: return 0.125;
+    case 9: return 1.0 / 9.0;
+    case 10: return 0.1;
+    case 11: return 1.0 / 11.0;
+    case 12: return 1.0 / 12.0;
+    default: return 1.0 / (double)d;
+  }
+}
+
+// Implicit stencil of a regular cell: A x = (eps/h^2)(dg x_c - sum); a
+// Dirichlet wall face adds 3 to dg and x_inward/3 to sum (one-sided second
+// order wall flux), a Neumann wall face adds nothing.
+template <class T>
+__device__ __forceinline__ void reg_stencil(const Op<T>& o, const T* x, const int I[3], long long c, T& sum, int& dg) {
+  sum = T(0);
+  dg = 0;
+  long long st = 1;
+  const T third = T(1) / T(3);
+  for (int a = 0; a < o.D; ++a) {
+    if (I[a] > 0) {
+      sum += x[c - st];
+      dg += 1;
+    } else if (o.bc[2 * a]) {
+      sum += x[c + st] * third;
+      dg += 3;
+    }
+    if (I[a] < o.n[a] - 1) {
+      sum += x[c + st];
+      dg += 1;
+    } else if (o.bc[2 * a + 1]) {
+      sum += x[c - st] * third;
+      dg += 3;
+    }
+    st *= o.n[a];
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void ijk(const Op<T>& o, long long c, int I[3]) {
+  I[0] = (int)(c % o.n[0]);
+  I[1] = (int)((c / o.n[0]) % o.n[1]);
+  I[2] = (int)(c / ((long long)o.n[0] * o.n[1]));
+}
+
+// one colour of red-black Gauss-Seidel on regular cells; thread per cell pair along x
+template <class T>
+__global__ void k_smooth_dense(Op<T> o, int colour) {
+  long long half = o.ncell >> 1;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= half) return;
+  int hx = o.n[0] >> 1;
+  long long row = t / hx;
+  int j = (int)(row % o.n[1]);
+  int k = (int)(row / o.n[1]);
+  int i = 2 * (int)(t % hx) + ((j + k + colour) & 1);
+  long long c = (long long)i + (long long)o.n[0] * row;
+  uint8_t f = o.flags[c];
+  if ((f & F_IRR) || !(f & 3)) return;
+  int p = (f & 1) ? 0 : 1;
+  T* x = o.x[p];
+  int I[3] = {i, j, k};
+  T sum;
+  int dg;
+  reg_stencil(o, x, I, c, sum, dg);
+  x[c] = (o.h2e[p] * o.b[p][c] + sum) * inv_count(dg, T(0));
+}
+
+template <class T>
+__device__ __forceinline__ double row_dot(const Op<T>& o, long long r) {
+  double s = 0.0;
+  for (int e = o.row_ptr[r]; e < o.row_ptr[r + 1]; ++e) {
+    unsigned cl = (unsigned)o.col[e];
+    s += o.val[e] * (double)o.x[cl >> 30][cl & 0x3fffffffu];
+  }
+  return s;
+}
+
+// sparse rows [rb, re): mode 0 writes the Gauss-Seidel value, mode 1 the residual, into tmp
+template <class T>
+__global__ void k_rows(Op<T> o, long long rb, long long re, int mode) {
+  long long r = rb + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= re) return;
+  double d = o.diag[r];
+  if (d == 0.0) return;
+  long long cell = o.irr_cell[r >> 1];
+  int p = (int)(r & 1);
+  double s = (double)o.b[p][cell] - row_dot(o, r);
+  o.tmp[r] = mode == 0 ? (T)(s / d) : (T)(s - d * (double)o.x[p][cell]);
+}
+
+template <class T>
+__global__ void k_scatter_rows(Op<T> o, long long rb, long long re) {
+  long long r = rb + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= re) return;
+  if (o.diag[r] == 0.0) return;
+  o.x[r & 1][o.irr_cell[r >> 1]] = o.tmp[r];
+}
+
+// Gauss-Seidel of rows [rb, re) by one CTA: all new values from the current
+// iterate first (rows of one colour may couple through EB stencils), then written.
+template <class T>
+__global__ void k_rows_gs_cta(Op<T> o, long long rb, long long re) {
+  for (long long r = rb + threadIdx.x; r < re; r += blockDim.x) {
+    double d = o.diag[r];
+    if (d == 0.0) continue;
+    long long cell = o.irr_cell[r >> 1];
+    int p = (int)(r & 1);
+    o.tmp[r] = (T)(((double)o.b[p][cell] - row_dot(o, r)) / d);
+  }
+  __syncthreads();
+  for (long long r = rb + threadIdx.x; r < re; r += blockDim.x) {
+    if (o.diag[r] == 0.0) continue;
+    o.x[r & 1][o.irr_cell[r >> 1]] = o.tmp[r];
+  }
+}
+
+template <class T>
+__device__ __forceinline__ T cell_residual(const Op<T>& o, long long c, int p, const int I[3]) {
+  uint8_t f = o.flags[c];
+  if (f & F_IRR) return o.tmp[2 * (long long)o.irr_of_cell[c] + p];
+  T sum;
+  int dg;
+  reg_stencil(o, o.x[p], I, c, sum, dg);
+  return o.b[p][c] - o.ceps[p] * ((T)dg * o.x[p][c] - sum);
+}
+
+// r = b - A x on the fine level, averaged over the 2^D children into the
+// coarse right-hand side (the integral form makes restriction a sum; per unit
+// volume it is the mean); the coarse unknown is zeroed.  Thread per coarse cell.
+template <class T>
+__global__ void k_resid_restrict(Op<T> f, Op<T> c) {
+  long long C = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= c.ncell) return;
+  int IC[3];
+  ijk(c, C, IC);
+  int nch = 1 << f.D;
+  T acc[2] = {T(0), T(0)};
+  for (int k = 0; k < nch; ++k) {
+    int I[3] = {2 * IC[0] + (k & 1), 2 * IC[1] + ((k >> 1) & 1), f.D == 3 ? 2 * IC[2] + ((k >> 2) & 1) : 0};
+    long long cf = (long long)I[0] + (long long)f.n[0] * ((long long)I[1] + (long long)f.n[1] * I[2]);
+    uint8_t fl = f.flags[cf];
+    for (int p = 0; p < 2; ++p)
+      if ((fl >> p) & 1) acc[p] += cell_residual(f, cf, p, I);
+  }
+  uint8_t cf = c.flags[C];
+  T scale = T(1) / T(nch);
+  for (int p = 0; p < 2; ++p) {
+    if (c.b[p] == nullptr) continue;
+    c.b[p][C] = ((cf >> p) & 1) ? acc[p] * scale : T(0);
+    c.x[p][C] = T(0);
+  }
+}
+
+// x_fine += P x_coarse: (bi/tri)linear where every coarse cell of the
+// interpolation carries an unknown of the phase, piecewise constant otherwise.
+template <class T>
+__global__ void k_prolong(Op<T> f, Op<T> c) {
+  long long cf = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cf >= f.ncell) return;
+  uint8_t fl = f.flags[cf];
+  if (!(fl & 3)) return;
+  int I[3];
+  ijk(f, cf, I);
+  int IC[3] = {I[0] >> 1, I[1] >> 1, f.D == 3 ? I[2] >> 1 : 0};
+  int sdir[3];
+  bool inside = true;
+  for (int a = 0; a < 3; ++a) {
+    sdir[a] = (I[a] & 1) ? 1 : -1;
+    if (a < f.D) {
+      int nb = IC[a] + sdir[a];
+      if (nb < 0 || nb >= c.n[a]) inside = false;
+    }
+  }
+  long long C = (long long)IC[0] + (long long)c.n[0] * ((long long)IC[1] + (long long)c.n[1] * IC[2]);
+  long long st[3] = {1, c.n[0], (long long)c.n[0] * c.n[1]};
+  int ncn = 1 << f.D;
+  for (int p = 0; p < 2; ++p) {
+    if (!((fl >> p) & 1)) continue;
+    const T* xc = c.x[p];
+    T v = xc[C];
+    bool lin = inside;
+    if (lin)
+      for (int k = 1; k < ncn && lin; ++k) {
+        long long n = C;
+        for (int a = 0; a < f.D; ++a)
+          if ((k >> a) & 1) n += sdir[a] * st[a];
+        if (!((c.flags[n] >> p) & 1)) lin = false;
+      }
+    if (lin) {
+      // weights 3/4 (own) and 1/4 (neighbour) per axis
+      T acc = T(0);
+      for (int k = 0; k < ncn; ++k) {
+        long long n = C;
+        T w = T(1);
+        for (int a = 0; a < f.D; ++a) {
+          if ((k >> a) & 1) {
+            n += sdir[a] * st[a];
+            w *= T(0.25);
+          } else {
+            w *= T(0.75);
+          }
+        }
+        acc += w * xc[n];
+      }
+      v = acc;
+    }
+    f.x[p][cf] += v;
+  }
+}
+
+// Coarsest level: red-black Gauss-Seidel sweeps by one CTA (Sec. 3.3.2: a
+// relaxation bottom solver for multiphase problems).
+template <class T>
+__global__ void k_bottom(Op<T> o, int sweeps) {
+  long long half = o.ncell >> 1;
+  int hx = o.n[0] >> 1;
+  for (int it = 0; it < sweeps; ++it) {
+    for (int colour = 0; colour < 2; ++colour) {
+      for (long long t = threadIdx.x; t < half; t += blockDim.x) {
+        long long row = t / hx;
+        int j = (int)(row % o.n[1]);
+        int k = (int)(row / o.n[1]);
+        int i = 2 * (int)(t % hx) + ((j + k + colour) & 1);
+        long long c = (long long)i + (long long)o.n[0] * row;
+        uint8_t f = o.flags[c];
+        if ((f & F_IRR) || !(f & 3)) continue;
+        int p = (f & 1) ? 0 : 1;
+        int I[3] = {i, j, k};
+        T sum;
+        int dg;
+        reg_stencil(o, o.x[p], I, c, sum, dg);
+        o.x[p][c] = (o.h2e[p] * o.b[p][c] + sum) * inv_count(dg, T(0));
+      }
+      __syncthreads();
+      long long rb = colour == 0 ? 0 : 2 * o.nirr_red, re = colour == 0 ? 2 * o.nirr_red : 2 * o.nirr;
+      for (long long r = rb + threadIdx.x; r < re; r += blockDim.x) {
+        double d = o.diag[r];
+        if (d == 0.0) continue;
+        long long cell = o.irr_cell[r >> 1];
+        int p = (int)(r & 1);
+        o.tmp[r] = (T)(((double)o.b[p][cell] - row_dot(o, r)) / d);
+      }
+      __syncthreads();
+      for (long long r = rb + threadIdx.x; r < re; r += blockDim.x) {
+        if (o.diag[r] == 0.0) continue;
+        o.x[r & 1][o.irr_cell[r >> 1]] = o.tmp[r];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// FP64 residual of the finest level (irregular rows already in o.tmp) and its
+// max norm; with b32/e32 given, the residual becomes the FP32 inner
+// right-hand side and the FP32 correction is zeroed.
+__global__ void k_resid64_out(Op<double> o, float* b32_0, float* b32_1, float* e32_0, float* e32_1,
+                              unsigned long long* norm) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double mx = 0.0;
+  if (c < o.ncell) {
+    uint8_t f = o.flags[c];
+    int I[3];
+    ijk(o, c, I);
+    float* bo[2] = {b32_0, b32_1};
+    float* eo[2] = {e32_0, e32_1};
+    for (int p = 0; p < 2; ++p) {
+      double r = 0.0;
+      if ((f >> p) & 1) r = cell_residual(o, c, p, I);
+      mx = fmax(mx, fabs(r));
+      if (bo[p]) bo[p][c] = (float)r;
+      if (eo[p]) eo[p][c] = 0.0f;
+    }
+  }
+  // warp max then one atomic per warp (max is order independent)
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(norm, (unsigned long long)__double_as_longlong(mx));
+}
+
+__global__ void k_update64(Op<double> o, const float* e0, const float* e1) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= o.ncell) return;
+  uint8_t f = o.flags[c];
+  if (f & 1) o.x[0][c] += (double)e0[c];
+  if ((f & 2) && e1) o.x[1][c] += (double)e1[c];
+}
+
+// masked copy of a [2][ncell] field: entries without an unknown become 0
+__global__ void k_copy_masked(const uint8_t* flags, long long ncell, const double* src, double* dst) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  uint8_t f = flags[c];
+  for (int p = 0; p < 2; ++p) dst[p * ncell + c] = ((f >> p) & 1) ? src[p * ncell + c] : 0.0;
+}
+
+}  // namespace ebp

@@ -1,0 +1,671 @@
+// solver.cu -- multigrid driver and the C ABI of the EB Poisson library
+// (arXiv:1809.03745, Sec. 3.3.2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "eb_internal.h"
+#include "mg_kernels.cuh"
+
+// ----------------------------------------------------------------- errors
+
+namespace ebp {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+eb_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) return EB_ERR_OOM;
+  return EB_ERR_CUDA;
+}
+
+void* dev_alloc(std::vector<void*>& owner, size_t bytes, long long* counter, eb_status* st) {
+  if (*st != EB_OK) return nullptr;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *st = EB_ERR_OOM;
+    set_error("device allocation of " + std::to_string(bytes) + " bytes failed");
+    return nullptr;
+  }
+  owner.push_back(p);
+  if (counter) *counter += (long long)bytes;
+  return p;
+}
+
+}  // namespace ebp
+
+using namespace ebp;
+
+extern "C" const char* eb_status_str(eb_status s) {
+  switch (s) {
+    case EB_OK: return "ok";
+    case EB_ERR_INVALID: return "invalid argument";
+    case EB_ERR_OOM: return "out of device memory";
+    case EB_ERR_NOT_CONVERGED: return "not converged";
+    case EB_ERR_CUDA: return "CUDA error";
+    case EB_ERR_TIMEOUT: return "timeout";
+    case EB_ERR_UNSUPPORTED: return "unsupported geometry";
+    case EB_ERR_BUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* eb_last_error(void) { return g_last_error.c_str(); }
+
+// --------------------------------------------------------------- geometry
+
+static eb_status validate(const eb_geom_desc* d) {
+  auto bad = [](const char* m) {
+    set_error(m);
+    return EB_ERR_INVALID;
+  };
+  if (!d) return bad("null description");
+  if (d->dim != 2 && d->dim != 3) return bad("dim must be 2 or 3");
+  long long cells = 1;
+  for (int k = 0; k < d->dim; ++k) {
+    if (d->n[k] < 8 || d->n[k] % 8) return bad("cells per axis must be a multiple of 8 and at least 8");
+    cells *= d->n[k];
+  }
+  if (cells >= (1LL << 30)) return bad("at most 2^30 cells");
+  if (!(d->h > 0.0) || !std::isfinite(d->h)) return bad("h must be positive");
+  if (d->n_prims < 0 || d->n_prims > EB_MAX_PRIMS) return bad("too many primitives");
+  if (d->n_nodes < 0 || d->n_nodes > EB_MAX_NODES) return bad("too many CSG nodes");
+  if ((d->n_prims && !d->prims) || (d->n_nodes && !d->nodes)) return bad("null primitive/node array");
+  for (int i = 0; i < d->n_prims; ++i)
+    if (d->prims[i].kind < 0 || d->prims[i].kind > 5) return bad("unknown primitive kind");
+  for (int i = 0; i < d->n_nodes; ++i) {
+    const eb_csg& c = d->nodes[i];
+    if (c.op == EB_CSG_PRIM) {
+      if (c.a < 0 || c.a >= d->n_prims) return bad("CSG primitive index out of range");
+    } else if (c.op == EB_CSG_NEGATE) {
+      if (c.a < 0 || c.a >= i) return bad("CSG child must precede its parent");
+    } else if (c.op == EB_CSG_UNION || c.op == EB_CSG_INTERSECT) {
+      if (c.a < 0 || c.a >= i || c.b < 0 || c.b >= i) return bad("CSG child must precede its parent");
+    } else {
+      return bad("unknown CSG op");
+    }
+  }
+  if (d->electrode_root >= d->n_nodes || d->dielectric_root >= d->n_nodes) return bad("root out of range");
+  if (d->n_electrodes < 0 || d->n_electrodes > EB_MAX_ELECTRODES) return bad("too many electrodes");
+  for (int e = 0; e < d->n_electrodes; ++e)
+    if (d->electrode_node[e] < 0 || d->electrode_node[e] >= d->n_nodes) return bad("electrode node out of range");
+  if (d->electrode_root >= 0 && d->n_electrodes == 0) return bad("an electrode root needs at least one electrode");
+  if (!(d->eps_gas > 0.0) || (d->dielectric_root >= 0 && !(d->eps_diel > 0.0))) return bad("permittivity must be > 0");
+  for (int k = 0; k < 2 * d->dim; ++k)
+    if (d->bc_type[k] != EB_BC_NEUMANN && d->bc_type[k] != EB_BC_DIRICHLET) return bad("unknown wall type");
+  return EB_OK;
+}
+
+extern "C" eb_status eb_geom_build(const eb_geom_desc* d, void* stream, eb_geom** out) {
+  if (!out) {
+    set_error("null output handle");
+    return EB_ERR_INVALID;
+  }
+  *out = nullptr;
+  eb_status st = validate(d);
+  if (st != EB_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  eb_geom* G = new eb_geom();
+  cudaGetDevice(&G->device);
+  Csg& c = G->csg;
+  std::memset(&c, 0, sizeof(c));
+  c.n_prims = d->n_prims;
+  c.n_nodes = d->n_nodes;
+  for (int i = 0; i < d->n_prims; ++i) {
+    c.kind[i] = d->prims[i].kind;
+    for (int k = 0; k < NPAR; ++k) c.par[i][k] = d->prims[i].p[k];
+  }
+  for (int i = 0; i < d->n_nodes; ++i) {
+    c.op[i] = d->nodes[i].op;
+    c.a[i] = d->nodes[i].a;
+    c.b[i] = d->nodes[i].b;
+  }
+  c.root_E = d->electrode_root;
+  c.root_D = d->dielectric_root;
+  c.n_elec = d->n_electrodes;
+  for (int e = 0; e < d->n_electrodes; ++e) {
+    c.elec_node[e] = d->electrode_node[e];
+    c.elec_phi[e] = d->electrode_phi[e];
+  }
+  G->n_phase = d->dielectric_root >= 0 ? 2 : 1;
+  DevLevel L0;
+  Grid& g = L0.g;
+  g.D = d->dim;
+  for (int k = 0; k < 3; ++k) {
+    g.n[k] = k < d->dim ? d->n[k] : 1;
+    g.lo[k] = k < d->dim ? d->lo[k] : 0.0;
+  }
+  g.h = d->h;
+  g.ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  for (int k = 0; k < 6; ++k) {
+    g.bc[k] = (k < 2 * d->dim) ? (d->bc_type[k] == EB_BC_DIRICHLET) : 0;
+    g.bcv[k] = (k < 2 * d->dim && g.bc[k]) ? d->bc_value[k] : 0.0;
+  }
+  g.eps[0] = d->eps_gas;
+  g.eps[1] = d->dielectric_root >= 0 ? d->eps_diel : d->eps_gas;
+  G->L.push_back(L0);
+  std::vector<void*> misc;
+  G->d_csg = (Csg*)dev_alloc(G->L[0].allocs, sizeof(Csg), &G->bytes, &st);
+  G->d_status = (int*)dev_alloc(G->L[0].allocs, sizeof(int), &G->bytes, &st);
+  if (st == EB_OK) {
+    cudaError_t e = cudaMemcpyAsync(G->d_csg, &c, sizeof(Csg), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "description upload");
+  }
+  if (st == EB_OK) st = build_finest_geometry(G, s);
+  if (st == EB_OK) st = build_rows(G, 0, s);
+  // coarsen while every axis keeps at least 8 cells and stays even
+  while (st == EB_OK) {
+    const Grid& f = G->L.back().g;
+    bool ok = true;
+    for (int k = 0; k < f.D; ++k)
+      if (f.n[k] % 2 || f.n[k] / 2 < 8) ok = false;
+    if (!ok || (int)G->L.size() >= EB_MAX_LEVELS) break;
+    bool stopped = false;
+    st = build_coarse_geometry(G, (int)G->L.size() - 1, s, &stopped);
+    if (st != EB_OK || stopped) break;
+    st = build_rows(G, (int)G->L.size() - 1, s);
+    if (st == EB_ERR_UNSUPPORTED) {  // a coarse stencil that cannot be built ends the hierarchy
+      free_level(G->L.back());
+      G->L.pop_back();
+      st = EB_OK;
+      break;
+    }
+  }
+  if (st == EB_OK) {
+    // dof and stencil-order counts of the finest level
+    const DevLevel& F = G->L[0];
+    std::vector<uint8_t> flags(F.g.ncell);
+    cudaMemcpy(flags.data(), F.flags, F.g.ncell, cudaMemcpyDeviceToHost);
+    long long nd = 0;
+    for (uint8_t f : flags) nd += (f & 1) + ((f >> 1) & 1);
+    G->n_dof = nd;
+    long long nq = F.R.ncut;
+    std::vector<uint8_t> ord(2 * std::max<long long>(nq, 1)), dofm(std::max<long long>(nq, 1));
+    if (nq) {
+      cudaMemcpy(ord.data(), F.order, 2 * nq, cudaMemcpyDeviceToHost);
+      cudaMemcpy(dofm.data(), F.R.dofm, nq, cudaMemcpyDeviceToHost);
+    }
+    for (long long q = 0; q < nq; ++q)
+      for (int p = 0; p < 2; ++p) {
+        if (!((dofm[q] >> p) & 1)) continue;
+        int o = ord[p * nq + q];
+        if (o == 2) G->stencil_counts[0]++;
+        if (o == 1) G->stencil_counts[1]++;
+        if (o == 3) G->stencil_counts[2]++;
+      }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_fail(e, "geometry summary");
+  }
+  if (st != EB_OK) {
+    eb_geom_destroy(G);
+    return st;
+  }
+  *out = G;
+  return EB_OK;
+}
+
+extern "C" void eb_geom_destroy(eb_geom* G) {
+  if (!G) return;
+  for (auto& L : G->L) free_level(L);
+  delete G;
+}
+
+extern "C" eb_status eb_geom_query(const eb_geom* G, eb_geom_info* out) {
+  if (!G || !out) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  std::memset(out, 0, sizeof(*out));
+  const DevLevel& F = G->L[0];
+  out->dim = F.g.D;
+  out->n_phase = G->n_phase;
+  out->n_cells = F.g.ncell;
+  out->n_dof = G->n_dof;
+  out->n_eb = F.n_eb;
+  out->n_irregular = F.nirr;
+  out->n_levels = (int)G->L.size();
+  for (size_t l = 0; l < G->L.size(); ++l)
+    for (int k = 0; k < 3; ++k) out->level_n[l][k] = G->L[l].g.n[k];
+  for (int k = 0; k < 3; ++k) out->stencil_order[k] = G->stencil_counts[k];
+  out->device_bytes = G->bytes;
+  return EB_OK;
+}
+
+extern "C" eb_status eb_geom_export(const eb_geom* G, eb_geom_arrays* out, void* stream) {
+  if (!G || !out) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  return export_geometry(G, out, (cudaStream_t)stream);
+}
+
+// ----------------------------------------------------------------- solver
+
+struct eb_poisson {
+  const eb_geom* G = nullptr;
+  eb_solver_opts o{};
+  int nlev = 0;
+  std::vector<Op<double>> op64;
+  std::vector<Op<float>> op32;
+  double* phi64 = nullptr;
+  double* b64 = nullptr;
+  unsigned long long* d_norm = nullptr;  // [0] residual max, [1] rhs max
+  unsigned long long* h_norm = nullptr;  // pinned
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  long long launches = 0;   // kernels launched by the current call
+  long long per_iter = 0;   // kernels in one iteration
+  std::vector<void*> allocs;
+  long long bytes = 0;
+};
+
+extern "C" void eb_solver_opts_default(eb_solver_opts* o) {
+  if (!o) return;
+  o->tol = 1e-10;
+  o->max_cycles = 100;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->precision = EB_PREC_MIXED;
+  o->inner_cycles = 2;
+  o->bottom_sweeps = 64;
+  o->use_graph = 1;
+}
+
+template <class T>
+static Op<T> make_op(const DevLevel& L, std::vector<void*>& owner, long long* bytes, eb_status* st, int nphase,
+                     T* x0 = nullptr, T* b0 = nullptr, T* x1 = nullptr, T* b1 = nullptr) {
+  Op<T> o;
+  std::memset(&o, 0, sizeof(o));
+  o.D = L.g.D;
+  for (int k = 0; k < 3; ++k) o.n[k] = L.g.n[k];
+  o.ncell = L.g.ncell;
+  for (int k = 0; k < 6; ++k) o.bc[k] = L.g.bc[k];
+  size_t n = (size_t)L.g.ncell;
+  o.x[0] = x0 ? x0 : (T*)dev_alloc(owner, n * sizeof(T), bytes, st);
+  o.b[0] = b0 ? b0 : (T*)dev_alloc(owner, n * sizeof(T), bytes, st);
+  if (nphase == 2) {
+    o.x[1] = x1 ? x1 : (T*)dev_alloc(owner, n * sizeof(T), bytes, st);
+    o.b[1] = b1 ? b1 : (T*)dev_alloc(owner, n * sizeof(T), bytes, st);
+  }
+  o.flags = L.flags;
+  o.irr_cell = L.irr_cell;
+  o.irr_of_cell = L.irr_of_cell;
+  o.row_ptr = L.row_ptr;
+  o.col = L.col;
+  o.val = L.val;
+  o.diag = L.diag;
+  o.tmp = (T*)dev_alloc(owner, sizeof(T) * std::max<long long>(2 * L.nirr, 1), bytes, st);
+  o.nirr = L.nirr;
+  o.nirr_red = L.nirr_red;
+  for (int p = 0; p < 2; ++p) {
+    double e = L.g.eps[p], h2 = L.g.h * L.g.h;
+    o.ceps[p] = (T)(e / h2);
+    o.h2e[p] = (T)(h2 / e);
+  }
+  if (*st == EB_OK) {
+    cudaMemset(o.x[0], 0, n * sizeof(T));
+    cudaMemset(o.b[0], 0, n * sizeof(T));
+    if (nphase == 2) {
+      cudaMemset(o.x[1], 0, n * sizeof(T));
+      cudaMemset(o.b[1], 0, n * sizeof(T));
+    }
+  }
+  return o;
+}
+
+static inline int blocks(long long n, int tb = 256) { return (int)std::max<long long>(1, (n + tb - 1) / tb); }
+
+static thread_local long long* g_count = nullptr;  // launch counter of the current call
+static inline void counted(int k = 1) {
+  if (g_count) *g_count += k;
+}
+
+template <class T>
+static void smooth(const Op<T>& o, cudaStream_t s) {
+  long long half = o.ncell >> 1;
+  for (int colour = 0; colour < 2; ++colour) {
+    k_smooth_dense<T><<<blocks(half), 256, 0, s>>>(o, colour);
+    counted();
+    long long rb = colour == 0 ? 0 : 2 * o.nirr_red, re = colour == 0 ? 2 * o.nirr_red : 2 * o.nirr;
+    if (re <= rb) continue;
+    if (re - rb <= 16384) {
+      k_rows_gs_cta<T><<<1, 1024, 0, s>>>(o, rb, re);
+      counted();
+    } else {
+      k_rows<T><<<blocks(re - rb), 256, 0, s>>>(o, rb, re, 0);
+      k_scatter_rows<T><<<blocks(re - rb), 256, 0, s>>>(o, rb, re);
+      counted(2);
+    }
+  }
+}
+
+template <class T>
+static void vcycle(eb_poisson* P, std::vector<Op<T>>& ops, int l, cudaStream_t s) {
+  const Op<T>& o = ops[l];
+  if (l == P->nlev - 1) {
+    k_bottom<T><<<1, 1024, 0, s>>>(o, P->o.bottom_sweeps);
+    counted();
+    return;
+  }
+  for (int i = 0; i < P->o.nu1; ++i) smooth(o, s);
+  if (o.nirr) {
+    k_rows<T><<<blocks(2 * o.nirr), 256, 0, s>>>(o, 0, 2 * o.nirr, 1);
+    counted();
+  }
+  k_resid_restrict<T><<<blocks(ops[l + 1].ncell), 256, 0, s>>>(o, ops[l + 1]);
+  counted();
+  vcycle(P, ops, l + 1, s);
+  k_prolong<T><<<blocks(o.ncell), 256, 0, s>>>(o, ops[l + 1]);
+  counted();
+  for (int i = 0; i < P->o.nu2; ++i) smooth(o, s);
+}
+
+// FP64 residual of the finest level; writes the FP32 inner rhs in mixed mode
+static void resid64(eb_poisson* P, cudaStream_t s, bool to32) {
+  const Op<double>& o = P->op64[0];
+  cudaMemsetAsync(P->d_norm, 0, sizeof(unsigned long long), s);
+  if (o.nirr) {
+    k_rows<double><<<blocks(2 * o.nirr), 256, 0, s>>>(o, 0, 2 * o.nirr, 1);
+    counted();
+  }
+  float *b0 = nullptr, *b1 = nullptr, *e0 = nullptr, *e1 = nullptr;
+  if (to32) {
+    const Op<float>& f = P->op32[0];
+    b0 = f.b[0];
+    b1 = f.b[1];
+    e0 = f.x[0];
+    e1 = f.x[1];
+  }
+  k_resid64_out<<<blocks(o.ncell), 256, 0, s>>>(o, b0, b1, e0, e1, P->d_norm);
+  counted();
+}
+
+// one iteration: mixed -> inner FP32 V-cycles, FP64 update, FP64 residual;
+// FP64 -> one V-cycle and the residual
+static void iteration(eb_poisson* P, cudaStream_t s) {
+  if (P->o.precision == EB_PREC_MIXED) {
+    for (int i = 0; i < P->o.inner_cycles; ++i) vcycle(P, P->op32, 0, s);
+    const Op<float>& f = P->op32[0];
+    k_update64<<<blocks(P->op64[0].ncell), 256, 0, s>>>(P->op64[0], f.x[0], f.x[1]);
+    counted();
+    resid64(P, s, true);
+  } else {
+    vcycle(P, P->op64, 0, s);
+    resid64(P, s, false);
+  }
+}
+
+extern "C" eb_status eb_poisson_setup(const eb_geom* G, const eb_solver_opts* opts, void* stream, eb_poisson** out) {
+  if (!G || !out) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  *out = nullptr;
+  eb_poisson* P = new eb_poisson();
+  P->G = G;
+  if (opts) P->o = *opts;
+  else eb_solver_opts_default(&P->o);
+  eb_solver_opts& o = P->o;
+  if (!(o.tol > 0.0) || o.max_cycles < 1 || o.nu1 < 0 || o.nu2 < 0 || o.inner_cycles < 1 || o.bottom_sweeps < 1 ||
+      (o.precision != EB_PREC_FP64 && o.precision != EB_PREC_MIXED)) {
+    delete P;
+    set_error("invalid solver options");
+    return EB_ERR_INVALID;
+  }
+  P->nlev = (int)G->L.size();
+  eb_status st = EB_OK;
+  int np = G->n_phase;
+  const DevLevel& F = G->L[0];
+  size_t n0 = (size_t)F.g.ncell;
+  P->phi64 = (double*)dev_alloc(P->allocs, 2 * n0 * sizeof(double), &P->bytes, &st);
+  P->b64 = (double*)dev_alloc(P->allocs, 2 * n0 * sizeof(double), &P->bytes, &st);
+  P->d_norm = (unsigned long long*)dev_alloc(P->allocs, 2 * sizeof(unsigned long long), &P->bytes, &st);
+  if (st == EB_OK) {
+    cudaMemset(P->phi64, 0, 2 * n0 * sizeof(double));
+    cudaMemset(P->b64, 0, 2 * n0 * sizeof(double));
+  }
+  // finest FP64 operator over the solver's own phi and b
+  P->op64.push_back(make_op<double>(F, P->allocs, &P->bytes, &st, np, P->phi64, P->b64, P->phi64 + n0, P->b64 + n0));
+  if (o.precision == EB_PREC_FP64) {
+    for (int l = 1; l < P->nlev; ++l) P->op64.push_back(make_op<double>(G->L[l], P->allocs, &P->bytes, &st, np));
+  } else {
+    for (int l = 0; l < P->nlev; ++l) P->op32.push_back(make_op<float>(G->L[l], P->allocs, &P->bytes, &st, np));
+  }
+  if (st == EB_OK) {
+    cudaError_t e = cudaStreamCreateWithFlags(&P->s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&P->h_norm, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = cuda_fail(e, "solver setup");
+  }
+  if (st == EB_OK && o.use_graph) {
+    cudaError_t e = cudaStreamBeginCapture(P->s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      g_count = &P->per_iter;
+      iteration(P, P->s);
+      g_count = nullptr;
+      e = cudaStreamEndCapture(P->s, &P->graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&P->gexec, P->graph, 0);
+    if (e != cudaSuccess) st = cuda_fail(e, "graph capture");
+  }
+  (void)stream;
+  if (st != EB_OK) {
+    eb_poisson_destroy(P);
+    return st;
+  }
+  *out = P;
+  return EB_OK;
+}
+
+extern "C" void eb_poisson_destroy(eb_poisson* P) {
+  if (!P) return;
+  if (P->s) cudaStreamSynchronize(P->s);
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  if (P->ev) cudaEventDestroy(P->ev);
+  if (P->s) cudaStreamDestroy(P->s);
+  if (P->h_norm) cudaFreeHost(P->h_norm);
+  for (void* p : P->allocs) cudaFree(p);
+  delete P;
+}
+
+static double as_double(unsigned long long v) {
+  double d;
+  std::memcpy(&d, &v, sizeof(d));
+  return d;
+}
+
+// the solver's stream waits for the caller's, and the other way round at the end
+static void join_in(eb_poisson* P, cudaStream_t user) {
+  cudaEventRecord(P->ev, user);
+  cudaStreamWaitEvent(P->s, P->ev, 0);
+}
+static void join_out(eb_poisson* P, cudaStream_t user) {
+  cudaEventRecord(P->ev, P->s);
+  cudaStreamWaitEvent(user, P->ev, 0);
+}
+
+static eb_status read_norms(eb_poisson* P, double* r, double* b) {
+  cudaError_t e = cudaMemcpyAsync(P->h_norm, P->d_norm, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, P->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
+  if (e != cudaSuccess) return cuda_fail(e, "norm readback");
+  *r = as_double(P->h_norm[0]);
+  if (b) *b = as_double(P->h_norm[1]);
+  return EB_OK;
+}
+
+__global__ void k_resid_field(Op<double> o, double* r) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= o.ncell) return;
+  uint8_t f = o.flags[c];
+  int I[3];
+  ijk(o, c, I);
+  for (int p = 0; p < 2; ++p) r[p * o.ncell + c] = ((f >> p) & 1) ? cell_residual(o, c, p, I) : 0.0;
+}
+
+extern "C" eb_status eb_poisson_residual(eb_poisson* P, const double* d_rhs, const double* d_sigma,
+                                         const double* d_phi, double* d_r, void* stream) {
+  if (!P || !d_rhs || !d_phi || !d_r) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  cudaStream_t user = (cudaStream_t)stream;
+  const DevLevel& F = P->G->L[0];
+  long long n = F.g.ncell;
+  join_in(P, user);
+  cudaMemsetAsync(P->d_norm + 1, 0, sizeof(unsigned long long), P->s);
+  eb_status st = launch_rhs64(P->G, d_rhs, d_sigma, P->b64, (double*)(P->d_norm + 1), P->s);
+  if (st != EB_OK) return st;
+  k_copy_masked<<<blocks(n), 256, 0, P->s>>>(F.flags, n, d_phi, P->phi64);
+  const Op<double>& o = P->op64[0];
+  if (o.nirr) k_rows<double><<<blocks(2 * o.nirr), 256, 0, P->s>>>(o, 0, 2 * o.nirr, 1);
+  k_resid_field<<<blocks(n), 256, 0, P->s>>>(o, d_r);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
+  join_out(P, user);
+  return e == cudaSuccess ? EB_OK : cuda_fail(e, "residual");
+}
+
+extern "C" eb_status eb_poisson_solve(eb_poisson* P, const double* d_rhs, const double* d_sigma, double* d_phi,
+                                      eb_solve_info* info, void* stream) {
+  if (!P || !d_rhs || !d_phi) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  cudaStream_t user = (cudaStream_t)stream;
+  const DevLevel& F = P->G->L[0];
+  long long n = F.g.ncell;
+  eb_solve_info inf;
+  std::memset(&inf, 0, sizeof(inf));
+  P->launches = 0;
+  g_count = &P->launches;
+  join_in(P, user);
+  cudaMemsetAsync(P->d_norm + 1, 0, sizeof(unsigned long long), P->s);
+  eb_status st = launch_rhs64(P->G, d_rhs, d_sigma, P->b64, (double*)(P->d_norm + 1), P->s);
+  if (st != EB_OK) {
+    g_count = nullptr;
+    return st;
+  }
+  k_copy_masked<<<blocks(n), 256, 0, P->s>>>(F.flags, n, d_phi, P->phi64);
+  counted(2);
+  bool mixed = P->o.precision == EB_PREC_MIXED;
+  resid64(P, P->s, mixed);
+  double r = 0.0, b = 0.0;
+  st = read_norms(P, &r, &b);
+  if (st != EB_OK) return st;
+  inf.bnorm = b;
+  double r0 = r;
+  int cycles = 0, outer = 0;
+  st = EB_OK;
+  if (b == 0.0) {
+    cudaMemsetAsync(P->phi64, 0, 2 * n * sizeof(double), P->s);
+    r = 0.0;
+  } else {
+    int per = mixed ? P->o.inner_cycles : 1;
+    while (r > P->o.tol * b) {
+      if (cycles + per > P->o.max_cycles || !std::isfinite(r) || r > 1e6 * r0) {
+        st = EB_ERR_NOT_CONVERGED;
+        set_error("cycle cap reached or residual diverged");
+        break;
+      }
+      cudaError_t e = P->gexec ? cudaGraphLaunch(P->gexec, P->s) : cudaSuccess;
+      if (!P->gexec) iteration(P, P->s);
+      else counted((int)P->per_iter);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "iteration");
+        break;
+      }
+      cycles += per;
+      ++outer;
+      eb_status rs = read_norms(P, &r, nullptr);
+      if (rs != EB_OK) {
+        st = rs;
+        break;
+      }
+    }
+  }
+  k_copy_masked<<<blocks(n), 256, 0, P->s>>>(F.flags, n, P->phi64, d_phi);
+  counted();
+  g_count = nullptr;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
+  if (e != cudaSuccess && st == EB_OK) st = cuda_fail(e, "solve");
+  join_out(P, user);
+  inf.kernel_launches = P->launches;
+  inf.status = st;
+  inf.outer_iters = outer;
+  inf.vcycles = cycles;
+  inf.rel_res = b > 0.0 ? r / b : 0.0;
+  if (info) *info = inf;
+  return st;
+}
+
+extern "C" eb_status eb_field_eval(eb_poisson* P, const double* d_phi, const double* d_sigma, double* d_E,
+                                   double* d_En, void* stream) {
+  if (!P || !d_phi) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  cudaStream_t user = (cudaStream_t)stream;
+  join_in(P, user);
+  eb_status st = launch_field(P->G, d_phi, d_sigma, d_E, d_En, P->s);
+  cudaError_t e = cudaStreamSynchronize(P->s);
+  join_out(P, user);
+  if (st != EB_OK) return st;
+  return e == cudaSuccess ? EB_OK : cuda_fail(e, "field");
+}
+
+extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, double* ms, double* bytes, void* stream) {
+  if (!P || reps < 1 || (kernel != 0 && kernel != 1) || !ms || !bytes) {
+    set_error("invalid argument");
+    return EB_ERR_INVALID;
+  }
+  if (kernel == 1 && P->nlev < 2) {
+    set_error("no coarse level");
+    return EB_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  bool mixed = P->o.precision == EB_PREC_MIXED;
+  long long n = P->G->L[0].g.ncell;
+  int D = P->G->L[0].g.D;
+  double tb = mixed ? 4.0 : 8.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto launch = [&](int i) {
+    if (kernel == 0) {
+      if (mixed) k_smooth_dense<float><<<blocks(n >> 1), 256, 0, s>>>(P->op32[0], i & 1);
+      else k_smooth_dense<double><<<blocks(n >> 1), 256, 0, s>>>(P->op64[0], i & 1);
+    } else {
+      if (mixed) k_resid_restrict<float><<<blocks(P->op32[1].ncell), 256, 0, s>>>(P->op32[0], P->op32[1]);
+      else k_resid_restrict<double><<<blocks(P->op64[1].ncell), 256, 0, s>>>(P->op64[0], P->op64[1]);
+    }
+  };
+  launch(0);
+  cudaEventRecord(e0, s);
+  for (int i = 0; i < reps; ++i) launch(i);
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "profile");
+  *ms = (double)t / reps;
+  if (kernel == 0) *bytes = (double)n * (3.0 * tb + 1.0) / 2.0;
+  else *bytes = (double)n * (2.0 * tb + 1.0) + (double)n / (double)(1 << D) * 2.0 * tb;
+  return EB_OK;
+}

@@ -1,0 +1,347 @@
+"""Thin ctypes binding of libebpoisson (include/ebpoisson.h).
+
+Argument marshalling only: every step of the geometry pass, the operator
+construction, the multigrid solve and the field evaluation runs in the CUDA
+library.  PyTorch provides device memory and streams.  There is no CPU
+fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+EB_OK, EB_ERR_INVALID, EB_ERR_OOM, EB_ERR_NOT_CONVERGED, EB_ERR_CUDA, EB_ERR_TIMEOUT, EB_ERR_UNSUPPORTED, \
+    EB_ERR_BUSY = range(8)
+EB_PREC_FP64, EB_PREC_MIXED = 0, 1
+
+
+class EBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class _Prim(C.Structure):
+    _fields_ = [("kind", C.c_int), ("p", C.c_double * 10)]
+
+
+class _Csg(C.Structure):
+    _fields_ = [("op", C.c_int), ("a", C.c_int), ("b", C.c_int)]
+
+
+class GeomDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("h", C.c_double),
+                ("prims", C.POINTER(_Prim)), ("n_prims", C.c_int), ("nodes", C.POINTER(_Csg)), ("n_nodes", C.c_int),
+                ("electrode_root", C.c_int), ("n_electrodes", C.c_int), ("electrode_node", C.c_int * 4),
+                ("electrode_phi", C.c_double * 4), ("dielectric_root", C.c_int), ("eps_gas", C.c_double),
+                ("eps_diel", C.c_double), ("bc_type", C.c_int * 6), ("bc_value", C.c_double * 6)]
+
+
+class GeomInfo(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_phase", C.c_int), ("n_cells", C.c_longlong), ("n_dof", C.c_longlong),
+                ("n_eb", C.c_longlong), ("n_irregular", C.c_longlong), ("n_levels", C.c_int),
+                ("level_n", (C.c_int * 3) * 16), ("stencil_order", C.c_longlong * 3), ("device_bytes", C.c_longlong)]
+
+
+class GeomArrays(C.Structure):
+    _fields_ = [("flags", C.c_void_p), ("kappa", C.c_void_p), ("eb_cell", C.c_void_p), ("eb_area", C.c_void_p),
+                ("eb_normal", C.c_void_p), ("eb_centroid", C.c_void_p), ("eb_kind", C.c_void_p),
+                ("stencil_order", C.c_void_p)]
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_cycles", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
+                ("precision", C.c_int), ("inner_cycles", C.c_int), ("bottom_sweeps", C.c_int), ("use_graph", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("vcycles", C.c_int), ("rel_res", C.c_double),
+                ("bnorm", C.c_double), ("kernel_launches", C.c_longlong)]
+
+
+EXPORTS = ["eb_status_str", "eb_last_error", "eb_geom_build", "eb_geom_query", "eb_geom_destroy", "eb_geom_export",
+           "eb_solver_opts_default", "eb_poisson_setup", "eb_poisson_destroy", "eb_poisson_residual",
+           "eb_poisson_solve", "eb_field_eval", "eb_poisson_profile"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libebpoisson.so; raises if it is not built (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"CUDA library {path} is not built: run __graft_entry__.build()")
+            _build.build()
+        lib = C.CDLL(path)
+        P = C.c_void_p
+        lib.eb_status_str.restype = C.c_char_p
+        lib.eb_status_str.argtypes = [C.c_int]
+        lib.eb_last_error.restype = C.c_char_p
+        lib.eb_geom_build.restype = C.c_int
+        lib.eb_geom_build.argtypes = [C.POINTER(GeomDesc), P, C.POINTER(P)]
+        lib.eb_geom_query.restype = C.c_int
+        lib.eb_geom_query.argtypes = [P, C.POINTER(GeomInfo)]
+        lib.eb_geom_destroy.argtypes = [P]
+        lib.eb_geom_export.restype = C.c_int
+        lib.eb_geom_export.argtypes = [P, C.POINTER(GeomArrays), P]
+        lib.eb_solver_opts_default.argtypes = [C.POINTER(SolverOpts)]
+        lib.eb_poisson_setup.restype = C.c_int
+        lib.eb_poisson_setup.argtypes = [P, C.POINTER(SolverOpts), P, C.POINTER(P)]
+        lib.eb_poisson_destroy.argtypes = [P]
+        lib.eb_poisson_residual.restype = C.c_int
+        lib.eb_poisson_residual.argtypes = [P, P, P, P, P, P]
+        lib.eb_poisson_solve.restype = C.c_int
+        lib.eb_poisson_solve.argtypes = [P, P, P, P, C.POINTER(SolveInfo), P]
+        lib.eb_field_eval.restype = C.c_int
+        lib.eb_field_eval.argtypes = [P, P, P, P, P, P]
+        lib.eb_poisson_profile.restype = C.c_int
+        lib.eb_poisson_profile.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), P]
+        _lib = lib
+        return lib
+
+
+def _check(st: int, what: str):
+    if st != EB_OK:
+        lib = load()
+        raise EBError(st, f"{what}: {lib.eb_status_str(st).decode()}: {lib.eb_last_error().decode()}")
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _dev(t, dtype, device):
+    if t is None:
+        return None
+    t = torch.as_tensor(t)
+    return t.to(device=device, dtype=dtype).contiguous()
+
+
+def make_desc(desc: dict):
+    """Problem dict (see workloads.py) -> GeomDesc plus the arrays it points to."""
+    prims = (_Prim * max(1, len(desc["prims"])))()
+    for i, (k, p) in enumerate(desc["prims"]):
+        prims[i].kind = int(k)
+        for j, v in enumerate(p):
+            prims[i].p[j] = float(v)
+    nodes = (_Csg * max(1, len(desc["nodes"])))()
+    for i, (op, a, b) in enumerate(desc["nodes"]):
+        nodes[i].op, nodes[i].a, nodes[i].b = int(op), int(a), int(b)
+    d = GeomDesc()
+    d.dim = int(desc["dim"])
+    for k in range(3):
+        d.n[k] = int(desc["n"][k]) if k < len(desc["n"]) else 1
+        d.lo[k] = float(desc["lo"][k]) if k < len(desc["lo"]) else 0.0
+    d.h = float(desc["h"])
+    d.prims = C.cast(prims, C.POINTER(_Prim))
+    d.n_prims = len(desc["prims"])
+    d.nodes = C.cast(nodes, C.POINTER(_Csg))
+    d.n_nodes = len(desc["nodes"])
+    d.electrode_root = int(desc.get("root_E", -1))
+    elec = desc.get("electrodes")
+    if elec is None:
+        elec = [(d.electrode_root, desc.get("phi_E", 0.0))] if d.electrode_root >= 0 else []
+    d.n_electrodes = len(elec)
+    for i, (r, v) in enumerate(elec):
+        d.electrode_node[i] = int(r)
+        d.electrode_phi[i] = float(v)
+    d.dielectric_root = int(desc.get("root_D", -1))
+    d.eps_gas, d.eps_diel = float(desc["eps"][0]), float(desc["eps"][1])
+    for k in range(6):
+        d.bc_type[k] = int(desc["bc"][k])
+        d.bc_value[k] = float(desc.get("phi_wall", [0.0] * 6)[k])
+    return d, (prims, nodes)
+
+
+# ------------------------------------------------------------- C-ABI mirrors
+
+def eb_geom_build(desc: dict, stream=None):
+    lib = load()
+    d, keep = make_desc(desc)
+    h = C.c_void_p()
+    _check(lib.eb_geom_build(C.byref(d), _stream(stream), C.byref(h)), "eb_geom_build")
+    del keep
+    return h
+
+
+def eb_geom_query(handle) -> dict:
+    lib = load()
+    info = GeomInfo()
+    _check(lib.eb_geom_query(handle, C.byref(info)), "eb_geom_query")
+    return dict(dim=info.dim, n_phase=info.n_phase, n_cells=info.n_cells, n_dof=info.n_dof, n_eb=info.n_eb,
+                n_irregular=info.n_irregular, n_levels=info.n_levels,
+                level_n=[tuple(info.level_n[l]) for l in range(info.n_levels)],
+                stencil_order=dict(order2=info.stencil_order[0], order1=info.stencil_order[1],
+                                   ls=info.stencil_order[2]), device_bytes=info.device_bytes)
+
+
+def eb_solver_opts_default() -> SolverOpts:
+    o = SolverOpts()
+    load().eb_solver_opts_default(C.byref(o))
+    return o
+
+
+def eb_poisson_setup(geom_handle, opts: SolverOpts | None = None, stream=None):
+    lib = load()
+    h = C.c_void_p()
+    _check(lib.eb_poisson_setup(geom_handle, C.byref(opts) if opts is not None else None, _stream(stream),
+                                C.byref(h)), "eb_poisson_setup")
+    return h
+
+
+def eb_poisson_residual(handle, rhs, sigma, phi, out, stream=None):
+    _check(load().eb_poisson_residual(handle, _ptr(rhs), _ptr(sigma), _ptr(phi), _ptr(out), _stream(stream)),
+           "eb_poisson_residual")
+
+
+def eb_poisson_solve(handle, rhs, sigma, phi, stream=None) -> dict:
+    info = SolveInfo()
+    st = load().eb_poisson_solve(handle, _ptr(rhs), _ptr(sigma), _ptr(phi), C.byref(info), _stream(stream))
+    if st not in (EB_OK, EB_ERR_NOT_CONVERGED):
+        _check(st, "eb_poisson_solve")
+    return dict(status=info.status, outer_iters=info.outer_iters, vcycles=info.vcycles, rel_res=info.rel_res,
+                bnorm=info.bnorm, kernel_launches=info.kernel_launches)
+
+
+def eb_poisson_profile(handle, kernel: int, reps: int, stream=None):
+    ms, by = C.c_double(), C.c_double()
+    _check(load().eb_poisson_profile(handle, kernel, reps, C.byref(ms), C.byref(by), _stream(stream)),
+           "eb_poisson_profile")
+    return ms.value, by.value
+
+
+def eb_field_eval(handle, phi, sigma, E, En, stream=None):
+    _check(load().eb_field_eval(handle, _ptr(phi), _ptr(sigma), _ptr(E), _ptr(En), _stream(stream)),
+           "eb_field_eval")
+
+
+# ------------------------------------------------------------- convenience
+
+class Geometry:
+    """Cut-cell geometry and the multigrid hierarchy of one problem (owns an eb_geom)."""
+
+    def __init__(self, desc: dict, device="cuda", stream=None):
+        self.desc = desc
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self._h = eb_geom_build(desc, stream)
+        self.info = eb_geom_query(self._h)
+        self.ncell = int(self.info["n_cells"])
+        self.dim = int(desc["dim"])
+
+    def export(self, stream=None) -> dict:
+        n, neb = self.ncell, int(self.info["n_eb"])
+        dev = self.device
+        out = dict(flags=torch.empty(n, dtype=torch.uint8, device=dev),
+                   kappa=torch.empty(2, n, dtype=torch.float64, device=dev),
+                   eb_cell=torch.empty(max(neb, 1), dtype=torch.int32, device=dev),
+                   eb_area=torch.empty(max(neb, 1), dtype=torch.float64, device=dev),
+                   eb_normal=torch.empty(max(neb, 1), 3, dtype=torch.float64, device=dev),
+                   eb_centroid=torch.empty(max(neb, 1), 3, dtype=torch.float64, device=dev),
+                   eb_kind=torch.empty(max(neb, 1), dtype=torch.uint8, device=dev),
+                   stencil_order=torch.empty(max(neb, 1), 2, dtype=torch.int32, device=dev))
+        a = GeomArrays(*[C.c_void_p(out[k].data_ptr()) for k in
+                         ("flags", "kappa", "eb_cell", "eb_area", "eb_normal", "eb_centroid", "eb_kind",
+                          "stencil_order")])
+        _check(load().eb_geom_export(self._h, C.byref(a), _stream(stream)), "eb_geom_export")
+        for k in list(out):
+            if k.startswith("eb_") or k == "stencil_order":
+                out[k] = out[k][:neb]
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().eb_geom_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Poisson:
+    """Multigrid solver bound to a Geometry (owns an eb_poisson)."""
+
+    def __init__(self, geom: Geometry, *, precision="mixed", tol=1e-10, max_cycles=100, nu1=2, nu2=2,
+                 inner_cycles=2, bottom_sweeps=64, use_graph=True, stream=None):
+        self.geom = geom
+        o = eb_solver_opts_default()
+        o.tol, o.max_cycles, o.nu1, o.nu2 = tol, max_cycles, nu1, nu2
+        o.precision = EB_PREC_MIXED if precision == "mixed" else EB_PREC_FP64
+        o.inner_cycles, o.bottom_sweeps, o.use_graph = inner_cycles, bottom_sweeps, int(bool(use_graph))
+        self.opts = o
+        with torch.cuda.device(geom.device):
+            self._h = eb_poisson_setup(geom._h, o, stream)
+
+    def _fields(self, rhs, sigma):
+        n, dev = self.geom.ncell, self.geom.device
+        rhs = _dev(rhs, torch.float64, dev)
+        if rhs.dim() == 1:
+            rhs = torch.stack([rhs, torch.zeros_like(rhs)])
+        rhs = rhs.reshape(2, n).contiguous()
+        sigma = _dev(sigma, torch.float64, dev)
+        if sigma is not None:
+            sigma = sigma.reshape(n).contiguous()
+        return rhs, sigma
+
+    def residual(self, rhs, sigma, phi, stream=None):
+        rhs, sigma = self._fields(rhs, sigma)
+        phi = _dev(phi, torch.float64, self.geom.device).reshape(2, -1).contiguous()
+        out = torch.empty_like(phi)
+        eb_poisson_residual(self._h, rhs, sigma, phi, out, stream)
+        return out
+
+    def solve(self, rhs, sigma=None, phi=None, stream=None):
+        rhs, sigma = self._fields(rhs, sigma)
+        if phi is None:
+            phi = torch.zeros(2, self.geom.ncell, dtype=torch.float64, device=self.geom.device)
+        info = eb_poisson_solve(self._h, rhs, sigma, phi, stream)
+        return phi, info
+
+    def field(self, phi, sigma=None, stream=None):
+        n, neb = self.geom.ncell, int(self.geom.info["n_eb"])
+        dev = self.geom.device
+        phi = _dev(phi, torch.float64, dev).reshape(2, n).contiguous()
+        sigma = _dev(sigma, torch.float64, dev)
+        E = torch.empty(self.geom.dim, 2, n, dtype=torch.float64, device=dev)
+        En = torch.empty(max(neb, 1), 2, dtype=torch.float64, device=dev)
+        eb_field_eval(self._h, phi, sigma, E, En, stream)
+        return E, En[:neb]
+
+    def profile(self, kernel: int, reps: int = 50, stream=None):
+        """(ms per launch, algorithmic bytes per launch) of a finest-level kernel."""
+        return eb_poisson_profile(self._h, kernel, reps, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().eb_poisson_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

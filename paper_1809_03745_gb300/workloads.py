@@ -213,11 +213,12 @@ def batched_instances(count=64, seed=SEED_BASE + 4, *, n2=(64, 1024), n3=(32, 19
         V = rng.uniform(0.5, 2.0)
         peak = math.exp(rng.uniform(math.log(10.0), math.log(1e3)))
         if is3d:
-            desc = pin_plane_3d(n, tip_z=gap, radius=tip_r, V=V, eps_d=eps_d, disk_t=min(0.05, gap - 8 * h - 2 * h))
+            desc = pin_plane_3d(n, tip_z=gap, radius=tip_r, V=V, eps_d=eps_d,
+                                disk_t=min(0.05, gap - 10 * h) + 0.3 * h)
             x, y, z = cell_centres(desc)
             s = peak * np.exp(-((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - (gap - 0.05)) ** 2) / (2 * 0.03 ** 2))
         else:
-            slab = min(0.1, gap - 8 * h - 2 * h)
+            slab = min(0.1, gap - 10 * h) + 0.3 * h  # keep the flat slab top off the node rows
             desc = rod_plane_2d(n, dielectric=True, tip_y=gap, half_width=tip_r, V=V, eps_d=eps_d, slab_y=slab,
                                 rough_amp=0.0)
             x, y, _ = cell_centres(desc)

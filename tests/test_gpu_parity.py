@@ -1,0 +1,181 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Geometry and stencil orders must match exactly (same set of cut cells, same
+unknowns, same EB list) and moments to rounding; the operator residual
+b - A phi matches per cell to 1e-12 relative; solves match the oracle's direct
+solution to 1e-9 relative L-infinity; the field to 1e-9.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1809_03745_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1809_03745_gb300 import ebpoisson as E
+
+
+def _cases():
+    out = []
+    d, S, sig = W.c1_inputs(128)
+    out.append(("c1_128", d, S, sig))
+    d, S, sig = W.c2_inputs(200)  # not a power of two: ragged tiles, odd-size bottom
+    out.append(("c2_200", d, S, sig))
+    d = W.coaxial_2d(136)
+    out.append(("coax_136_sigma", d, np.zeros((2, W.ncells(d))), np.full(W.ncells(d), 0.7)))
+    d, S, sig = W.c2_inputs(256)
+    out.append(("c2_256", d, S, sig))
+    return out
+
+
+CASES = _cases()
+IDS = [c[0] for c in CASES]
+
+
+@pytest.fixture(scope="module")
+def oracles():
+    cache = {}
+    for name, d, S, sig in CASES:
+        og, phi, A, b, data = oracle.solve(d, s=S, sigma=sig)
+        cache[name] = (og, phi, A, b, data)
+    return cache
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_geometry_parity(case, oracles):
+    name, d, S, sig = case
+    og = oracles[name][0]
+    g = E.Geometry(d)
+    ex = g.export()
+    flags = ex["flags"].cpu().numpy()
+    dofbits = (og.dof[0] >= 0).astype(np.uint8) | ((og.dof[1] >= 0).astype(np.uint8) << 1)
+    assert np.array_equal(flags & 3, dofbits)
+    assert np.abs(ex["kappa"].cpu().numpy() - og.kappa).max() < 1e-13
+    eb = ex["eb_cell"].cpu().numpy()
+    assert np.array_equal(eb, og.eb_cells)
+    assert np.abs(ex["eb_area"].cpu().numpy() - og.eba[eb]).max() < 1e-13
+    assert np.abs(ex["eb_normal"].cpu().numpy() - og.ebn[eb]).max() < 1e-12
+    assert np.abs(ex["eb_centroid"].cpu().numpy() - og.ebx[eb]).max() < 1e-13
+    assert np.array_equal(ex["eb_kind"].cpu().numpy(), og.ebkind[eb])
+    oo = og.stencil_order()
+    so = ex["stencil_order"].cpu().numpy()
+    for p in range(2):
+        m = og.dof[p, eb] >= 0
+        assert np.array_equal(so[m, p], oo[p, eb][m])
+    assert g.info["stencil_order"] == og.stencil_counts
+    assert g.info["n_dof"] == og.ndof
+    assert g.info["n_eb"] == og.n_eb
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_operator_residual_parity(case, oracles):
+    """r = b - A phi for a random phi, per cell, against the oracle's assembled system."""
+    name, d, S, sig = case
+    og, _, A, b, data = oracles[name]
+    rng = np.random.default_rng(11)
+    phi = og.to_cells(rng.normal(size=og.ndof))
+    g = E.Geometry(d)
+    P = E.Poisson(g, precision="fp64")
+    r = P.residual(torch.from_numpy(S), torch.from_numpy(sig), torch.from_numpy(phi)).cpu().numpy()
+    ro = og.to_cells(b - A @ og.to_dofs(phi))
+    scale = np.abs(b).max() + np.abs(A).max() * np.abs(phi).max()
+    assert np.abs(r - ro).max() <= 1e-12 * scale
+    # phi = 0 returns b
+    r0 = P.residual(torch.from_numpy(S), torch.from_numpy(sig), torch.zeros(2, og.ncell, dtype=torch.float64))
+    assert np.abs(r0.cpu().numpy() - og.to_cells(b)).max() <= 1e-13 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_solve_parity(case, precision, oracles):
+    name, d, S, sig = case
+    og, ophi = oracles[name][:2]
+    g = E.Geometry(d)
+    P = E.Poisson(g, precision=precision, tol=1e-13, max_cycles=200)
+    phi, info = P.solve(torch.from_numpy(S), torch.from_numpy(sig))
+    assert info["status"] == 0, info
+    got = phi.cpu().numpy()
+    assert np.abs(got - ophi).max() <= 1e-9 * np.abs(ophi).max(), info
+    # entries without an unknown are zero
+    for p in range(2):
+        assert np.all(got[p][og.dof[p] < 0] == 0.0)
+
+
+def test_solve_reaches_1e10_and_is_deterministic():
+    d, S, sig = W.c2_inputs(256)
+    g = E.Geometry(d)
+    P = E.Poisson(g, precision="mixed", tol=1e-10)
+    phi1, i1 = P.solve(torch.from_numpy(S), torch.from_numpy(sig))
+    phi2, i2 = P.solve(torch.from_numpy(S), torch.from_numpy(sig))
+    assert i1["status"] == 0 and i1["rel_res"] <= 1e-10
+    assert torch.equal(phi1, phi2)
+    assert i1["vcycles"] == i2["vcycles"]
+    # warm start from the solution: no cycle needed
+    phi3, i3 = P.solve(torch.from_numpy(S), torch.from_numpy(sig), phi=phi1.clone())
+    assert i3["vcycles"] == 0 and i3["rel_res"] <= 1e-10
+
+
+@pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
+def test_field_parity(case, oracles):
+    name, d, S, sig = case
+    og, ophi, A, b, data = oracles[name]
+    Eo, Eno = og.field(data, og.to_dofs(ophi))
+    g = E.Geometry(d)
+    P = E.Poisson(g, precision="fp64")
+    Eg, Eng = P.field(torch.from_numpy(ophi), torch.from_numpy(sig))
+    Eg, Eng = Eg.cpu().numpy(), Eng.cpu().numpy()
+    scale = np.abs(Eo).max()
+    assert np.abs(Eg - Eo).max() <= 1e-9 * scale
+    assert np.abs(Eng - Eno[og.eb_cells]).max() <= 1e-9 * scale
+
+
+def test_full_size_multimaterial_1024():
+    """The 1024^2 multi-material workload at the benchmark's settings: geometry
+    identical to the oracle's, and the GPU solution satisfies the ORACLE's
+    system to the solve tolerance (a property that holds at any size)."""
+    d, S, sig = W.c2_inputs(1024)
+    og = oracle.Geometry(d)
+    data = og.data(s=S, sigma=sig)
+    A, b = og.assemble(data)
+    g = E.Geometry(d)
+    ex = g.export()
+    flags = ex["flags"].cpu().numpy()
+    dofbits = (og.dof[0] >= 0).astype(np.uint8) | ((og.dof[1] >= 0).astype(np.uint8) << 1)
+    assert np.array_equal(flags & 3, dofbits)
+    assert np.array_equal(ex["eb_cell"].cpu().numpy(), og.eb_cells)
+    P = E.Poisson(g, precision="mixed", tol=1e-10)
+    phi, info = P.solve(torch.from_numpy(S), torch.from_numpy(sig))
+    assert info["status"] == 0 and info["rel_res"] <= 1e-10
+    x = og.to_dofs(phi.cpu().numpy())
+    rel = np.abs(b - A @ x).max() / np.abs(b).max()
+    assert rel <= 2e-10, rel
+    # sampled cells: the oracle's residual row by row vanishes where the GPU solved
+    rng = np.random.default_rng(5)
+    rows = rng.choice(og.ndof, 64, replace=False)
+    assert np.all(np.abs((b - A @ x)[rows]) <= 2e-10 * np.abs(b).max())
+
+
+def test_rejects_unsupported_geometry():
+    d = W.rod_plane_2d(32, dielectric=True, tip_y=0.21, slab_y=0.2, rough_amp=0.0)
+    with pytest.raises(E.EBError) as ei:
+        E.Geometry(d)
+    assert ei.value.status == E.EB_ERR_UNSUPPORTED
+
+
+def test_no_boundary_pure_dirichlet_box():
+    """No electrode, no dielectric: every cell regular; matches the oracle."""
+    n = 64
+    d = W._desc(2, (n, n), (0, 0), 1.0 / n, [], [], -1, -1, (1.0, 1.0), [1, 1, 1, 1, 0, 0], 0.0,
+                [0.0, 1.0, 0.5, -0.25, 0, 0])
+    x, y, _ = W.cell_centres(d)
+    S = np.zeros((2, n * n))
+    S[0] = np.sin(3 * x) * np.cos(2 * y)
+    og, ophi, A, b, data = oracle.solve(d, s=S)
+    g = E.Geometry(d)
+    assert g.info["n_eb"] == 0 and g.info["n_irregular"] == 0
+    P = E.Poisson(g, precision="fp64", tol=1e-13)
+    phi, info = P.solve(torch.from_numpy(S))
+    assert np.abs(phi.cpu().numpy() - ophi).max() <= 1e-9 * np.abs(ophi).max()
