@@ -168,7 +168,9 @@ typedef struct {
   int precision;     /* EB_PREC_FP64: FP64 V-cycles; EB_PREC_MIXED: FP32 V-cycles inside FP64 defect correction */
   int inner_cycles;  /* FP32 V-cycles per FP64 outer iteration (mixed), default 2 */
   int bottom_sweeps; /* relaxation sweeps on the coarsest level, default 64 */
-  int use_graph;     /* replay one iteration through a captured CUDA graph, default 1 */
+  int launch_mode;   /* 0 (default): the whole solve in one persistent cooperative kernel (falls back to 1
+                        when the device cannot launch cooperatively); 1: per-phase kernels, one iteration
+                        replayed through a captured CUDA graph; 2: per-phase kernels, plain launches */
 } eb_solver_opts;
 
 /* Fill opts with the defaults listed above. */

@@ -363,13 +363,10 @@ __global__ void k_row_fill(LevelGeom L, const int* row_ptr, int* col, double* va
 
 // ------------------------------------------------------- rhs, field, export
 
-__global__ void k_rhs64(LevelGeom L, const double* s, const double* sigma, const double* bconst, const double* bsig,
-                        double* b, unsigned long long* bnorm) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void rhs_cell(const LevelGeom& L, long long c, const double* s, const double* sigma,
+                                         const double* bconst, const double* bsig, double* b, double& mx) {
   const Grid& g = L.g;
-  if (c >= g.ncell) return;
   uint8_t f = L.flags[c];
-  double mx = 0.0;
   for (int p = 0; p < 2; ++p) {
     double v = 0.0;
     if ((f >> p) & 1) {
@@ -394,7 +391,16 @@ __global__ void k_rhs64(LevelGeom L, const double* s, const double* sigma, const
     b[p * g.ncell + c] = v;
     mx = fmax(mx, fabs(v));
   }
-  atomicMax(bnorm, (unsigned long long)__double_as_longlong(mx));
+}
+
+// b = kappa s + boundary data + sigma terms, and max|b| (one atomic per warp)
+__global__ void k_rhs64(LevelGeom L, const double* s, const double* sigma, const double* bconst, const double* bsig,
+                        double* b, unsigned long long* bnorm) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double mx = 0.0;
+  if (c < L.g.ncell) rhs_cell(L, c, s, sigma, bconst, bsig, b, mx);
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(bnorm, (unsigned long long)__double_as_longlong(mx));
 }
 
 __device__ double eval_dn(const LevelGeom& L, long long q, const int I[3], int p, const double* phi,

@@ -1,0 +1,530 @@
+// persistent.cuh -- the whole solve in one cooperative launch.
+//
+// Multigrid phases (arXiv:1809.03745, Sec. 3.3.2) run as grid-stride loops
+// separated by a software grid barrier; levels small enough for one CTA run
+// inside CTA 0 with block barriers while the other CTAs wait; the coarsest
+// level is solved by a precomputed dense inverse.  The FP64 outer loop
+// (residual, convergence test ||r||_inf <= tol ||b||_inf of Sec. 3.3.2,
+// update) runs on the device, so a solve needs no host round trip.
+#pragma once
+
+#include "mg_kernels.cuh"
+
+namespace ebp {
+
+constexpr int MAXLEV = 16;
+constexpr int PT = 512;                          // threads per CTA of the persistent kernel
+constexpr long long BAR_WAIT_CYCLES = 4000000000LL;  // ~2 s of SM clock: a barrier wait gives up after this
+
+template <class T>
+struct Hier {
+  int nlev;  // multigrid levels
+  int lc;    // first level handled inside CTA 0
+  int nu1, nu2;
+  int bm;       // order of the bottom inverse (0: relax the bottom instead)
+  int bsweeps;  // relaxation sweeps when bm == 0
+  const T* binv;  // [bm][bm], slot s = p * ncell + c of the coarsest level
+  Op<T> op[MAXLEV];
+};
+
+struct Barrier {
+  unsigned* count;
+  unsigned* gen;
+  int* err;  // set when a wait gave up
+};
+
+struct SolveCtl {
+  double tol;
+  int max_cycles;
+  int inner;       // V-cycles per FP64 outer iteration
+  int mixed;       // 1: FP32 V-cycles on the correction; 0: FP64 V-cycles on phi
+  const double* bnorm;        // max |b|
+  unsigned long long* norms;  // [max_cycles + 2] per-iteration residual max, zeroed by the host
+  int* out;                   // [0] status, [1] outer iterations, [2] V-cycles, [3] norm slot of the final residual
+};
+
+// Grid barrier with a bounded wait: returns false (and leaves err set) when
+// some CTA did not arrive in time, after which every CTA falls through.
+__device__ __forceinline__ bool grid_sync(const Barrier& B) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile int* ve = B.err;
+    if (*ve == 0) {
+      volatile unsigned* vg = B.gen;
+      unsigned g = *vg;
+      __threadfence();
+      unsigned arrived = atomicAdd(B.count, 1u);
+      if (arrived == gridDim.x - 1) {
+        atomicExch(B.count, 0u);
+        __threadfence();
+        atomicAdd(B.gen, 1u);
+      } else {
+        long long t0 = clock64();
+        while (*vg == g) {
+          if (clock64() - t0 > BAR_WAIT_CYCLES) {
+            atomicOr(B.err, 1);
+            break;
+          }
+          __nanosleep(20);
+        }
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  volatile int* ve = B.err;
+  return *ve == 0;
+}
+
+// execution context of a phase: the whole grid, or CTA 0 alone
+struct Ctx {
+  long long i0, st;
+  bool local;
+  Barrier B;
+  __device__ __forceinline__ bool sync() const {
+    if (local) {
+      __syncthreads();
+      return true;
+    }
+    return grid_sync(B);
+  }
+};
+
+template <class T>
+__device__ __forceinline__ void ph_dense(const Op<T>& o, int colour, const Ctx& c) {
+  long long half = o.ncell >> 1;
+  int hx = o.n[0] >> 1;
+  for (long long t = c.i0; t < half; t += c.st) {
+    long long row = t / hx;
+    int j = (int)(row % o.n[1]);
+    int k = (int)(row / o.n[1]);
+    int i = 2 * (int)(t % hx) + ((j + k + colour) & 1);
+    long long cc = (long long)i + (long long)o.n[0] * row;
+    uint8_t f = o.flags[cc];
+    if ((f & F_IRR) || !(f & 3)) continue;
+    int p = (f & 1) ? 0 : 1;
+    T* x = o.x[p];
+    int I[3] = {i, j, k};
+    T sum;
+    int dg;
+    reg_stencil(o, x, I, cc, sum, dg);
+    x[cc] = (o.h2e[p] * o.b[p][cc] + sum) * inv_count(dg, T(0));
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void ph_rows(const Op<T>& o, long long rb, long long re, int mode, const Ctx& c) {
+  for (long long r = rb + c.i0; r < re; r += c.st) {
+    double d = o.diag[r];
+    if (d == 0.0) continue;
+    long long cell = o.irr_cell[r >> 1];
+    int p = (int)(r & 1);
+    double s = (double)o.b[p][cell] - row_dot(o, r);
+    o.tmp[r] = mode == 0 ? (T)(s / d) : (T)(s - d * (double)o.x[p][cell]);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void ph_write(const Op<T>& o, long long rb, long long re, const Ctx& c) {
+  for (long long r = rb + c.i0; r < re; r += c.st) {
+    if (o.diag[r] == 0.0) continue;
+    o.x[r & 1][o.irr_cell[r >> 1]] = o.tmp[r];
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void ph_restrict(const Op<T>& f, const Op<T>& co, const Ctx& c) {
+  int nch = 1 << f.D;
+  T scale = T(1) / T(nch);
+  for (long long C = c.i0; C < co.ncell; C += c.st) {
+    int IC[3];
+    ijk(co, C, IC);
+    T acc[2] = {T(0), T(0)};
+    for (int k = 0; k < nch; ++k) {
+      int I[3] = {2 * IC[0] + (k & 1), 2 * IC[1] + ((k >> 1) & 1), f.D == 3 ? 2 * IC[2] + ((k >> 2) & 1) : 0};
+      long long cf = (long long)I[0] + (long long)f.n[0] * ((long long)I[1] + (long long)f.n[1] * I[2]);
+      uint8_t fl = f.flags[cf];
+      for (int p = 0; p < 2; ++p)
+        if ((fl >> p) & 1) acc[p] += cell_residual(f, cf, p, I);
+    }
+    uint8_t cf = co.flags[C];
+    for (int p = 0; p < 2; ++p) {
+      if (co.b[p] == nullptr) continue;
+      co.b[p][C] = ((cf >> p) & 1) ? acc[p] * scale : T(0);
+      co.x[p][C] = T(0);
+    }
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void ph_prolong(const Op<T>& f, const Op<T>& co, const Ctx& c) {
+  long long st3[3] = {1, co.n[0], (long long)co.n[0] * co.n[1]};
+  int ncn = 1 << f.D;
+  for (long long cf = c.i0; cf < f.ncell; cf += c.st) {
+    uint8_t fl = f.flags[cf];
+    if (!(fl & 3)) continue;
+    int I[3];
+    ijk(f, cf, I);
+    int IC[3] = {I[0] >> 1, I[1] >> 1, f.D == 3 ? I[2] >> 1 : 0};
+    int sdir[3];
+    bool inside = true;
+    for (int a = 0; a < 3; ++a) {
+      sdir[a] = (I[a] & 1) ? 1 : -1;
+      if (a < f.D) {
+        int nb = IC[a] + sdir[a];
+        if (nb < 0 || nb >= co.n[a]) inside = false;
+      }
+    }
+    long long C = (long long)IC[0] + (long long)co.n[0] * ((long long)IC[1] + (long long)co.n[1] * IC[2]);
+    for (int p = 0; p < 2; ++p) {
+      if (!((fl >> p) & 1)) continue;
+      const T* xc = co.x[p];
+      bool lin = inside;
+      if (lin)
+        for (int k = 1; k < ncn && lin; ++k) {
+          long long n = C;
+          for (int a = 0; a < f.D; ++a)
+            if ((k >> a) & 1) n += sdir[a] * st3[a];
+          if (!((co.flags[n] >> p) & 1)) lin = false;
+        }
+      T v;
+      if (lin) {
+        T acc = T(0);
+        for (int k = 0; k < ncn; ++k) {
+          long long n = C;
+          T w = T(1);
+          for (int a = 0; a < f.D; ++a) {
+            if ((k >> a) & 1) {
+              n += sdir[a] * st3[a];
+              w *= T(0.25);
+            } else {
+              w *= T(0.75);
+            }
+          }
+          acc += w * xc[n];
+        }
+        v = acc;
+      } else {
+        v = xc[C];
+      }
+      f.x[p][cf] += v;
+    }
+  }
+}
+
+// one red-black Gauss-Seidel sweep: regular cells of a colour, then the
+// sparse rows of that colour (new values from the current iterate, then written)
+template <class T>
+__device__ bool ph_smooth(const Op<T>& o, int nu, const Ctx& c) {
+  for (int s = 0; s < nu; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      ph_dense(o, colour, c);
+      if (!c.sync()) return false;
+      long long rb = colour == 0 ? 0 : 2 * o.nirr_red, re = colour == 0 ? 2 * o.nirr_red : 2 * o.nirr;
+      if (re > rb) {
+        ph_rows(o, rb, re, 0, c);
+        if (!c.sync()) return false;
+        ph_write(o, rb, re, c);
+        if (!c.sync()) return false;
+      }
+    }
+  return true;
+}
+
+template <class T>
+__device__ bool ph_bottom(const Hier<T>& H, const Ctx& c) {
+  const Op<T>& o = H.op[H.nlev - 1];
+  if (H.bm == 0) return ph_smooth(o, H.bsweeps, c);
+  long long nc = o.ncell;
+  for (long long i = c.i0; i < H.bm; i += c.st) {
+    int p = (int)(i / nc);
+    long long cell = i - p * nc;
+    if (!((o.flags[cell] >> p) & 1)) continue;
+    const T* row = H.binv + i * H.bm;
+    T acc = T(0);
+    for (int j = 0; j < H.bm; ++j) {
+      int q = j / (int)nc;
+      long long cj = j - q * nc;
+      acc += row[j] * o.b[q][cj];
+    }
+    o.x[p][cell] = acc;
+  }
+  return c.sync();
+}
+
+template <class T>
+__device__ bool vcycle_dev(const Hier<T>& H, const Ctx& G) {
+  for (int l = 0; l < H.lc; ++l) {
+    const Op<T>& o = H.op[l];
+    if (!ph_smooth(o, H.nu1, G)) return false;
+    if (o.nirr) {
+      ph_rows(o, 0, 2 * o.nirr, 1, G);
+      if (!G.sync()) return false;
+    }
+    ph_restrict(o, H.op[l + 1], G);
+    if (!G.sync()) return false;
+  }
+  if (blockIdx.x == 0) {
+    Ctx L{(long long)threadIdx.x, (long long)blockDim.x, true, G.B};
+    for (int l = H.lc; l < H.nlev - 1; ++l) {
+      const Op<T>& o = H.op[l];
+      ph_smooth(o, H.nu1, L);
+      if (o.nirr) {
+        ph_rows(o, 0, 2 * o.nirr, 1, L);
+        L.sync();
+      }
+      ph_restrict(o, H.op[l + 1], L);
+      L.sync();
+    }
+    ph_bottom(H, L);
+    for (int l = H.nlev - 2; l >= H.lc; --l) {
+      ph_prolong(H.op[l], H.op[l + 1], L);
+      L.sync();
+      ph_smooth(H.op[l], H.nu2, L);
+    }
+  }
+  if (!G.sync()) return false;
+  for (int l = H.lc - 1; l >= 0; --l) {
+    ph_prolong(H.op[l], H.op[l + 1], G);
+    if (!G.sync()) return false;
+    if (!ph_smooth(H.op[l], H.nu2, G)) return false;
+  }
+  return true;
+}
+
+// FP64 residual of the finest level and its max norm into norms[slot]; in
+// mixed mode it also becomes the FP32 inner right-hand side (correction zeroed)
+template <class T>
+__device__ bool ph_resid64(const Op<double>& o, const Hier<T>& H, int mixed, unsigned long long* norm,
+                           const Ctx& G) {
+  if (o.nirr) {
+    ph_rows(o, 0, 2 * o.nirr, 1, G);
+    if (!G.sync()) return false;
+  }
+  double mx = 0.0;
+  const Op<T>& inner = H.op[0];
+  for (long long cc = G.i0; cc < o.ncell; cc += G.st) {
+    uint8_t f = o.flags[cc];
+    int I[3];
+    ijk(o, cc, I);
+    for (int p = 0; p < 2; ++p) {
+      double r = 0.0;
+      if ((f >> p) & 1) r = cell_residual(o, cc, p, I);
+      mx = fmax(mx, fabs(r));
+      if (mixed && inner.b[p]) {
+        inner.b[p][cc] = (T)r;
+        inner.x[p][cc] = T(0);
+      }
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(norm, (unsigned long long)__double_as_longlong(mx));
+  return G.sync();
+}
+
+template <class T>
+__device__ void ph_update64(const Op<double>& o, const Op<T>& inner, const Ctx& G) {
+  for (long long cc = G.i0; cc < o.ncell; cc += G.st) {
+    uint8_t f = o.flags[cc];
+    if (f & 1) o.x[0][cc] += (double)inner.x[0][cc];
+    if ((f & 2) && inner.x[1]) o.x[1][cc] += (double)inner.x[1][cc];
+  }
+}
+
+__device__ __forceinline__ double load_norm(const unsigned long long* p) {
+  volatile const unsigned long long* vp = p;
+  return __longlong_as_double((long long)*vp);
+}
+
+// The solve: residual, test, (inner V-cycles, update)*, until converged or capped.
+template <class T>
+__global__ void __launch_bounds__(PT) k_solve(const Hier<T>* __restrict__ Hg, const Op<double>* __restrict__ Fg,
+                                              SolveCtl ctl, Barrier B) {
+  __shared__ Hier<T> H;
+  __shared__ Op<double> F;
+  {
+    const int* src = (const int*)Hg;
+    int* dst = (int*)&H;
+    for (int i = threadIdx.x; i < (int)(sizeof(Hier<T>) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    const int* s2 = (const int*)Fg;
+    int* d2 = (int*)&F;
+    for (int i = threadIdx.x; i < (int)(sizeof(Op<double>) / sizeof(int)); i += blockDim.x) d2[i] = s2[i];
+  }
+  __syncthreads();
+  Ctx G{(long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x, false, B};
+  const double bn = *ctl.bnorm;
+  int it = 0, cycles = 0, status = 0;
+  double r0 = 0.0, r = 0.0;
+  if (bn == 0.0) {  // b = 0: the solution is 0
+    for (long long cc = G.i0; cc < F.ncell; cc += G.st) {
+      F.x[0][cc] = 0.0;
+      if (F.x[1]) F.x[1][cc] = 0.0;
+    }
+  }
+  for (; bn != 0.0;) {
+    if (!ph_resid64(F, H, ctl.mixed, ctl.norms + it, G)) {
+      status = 5;
+      break;
+    }
+    r = load_norm(ctl.norms + it);
+    if (it == 0) r0 = r;
+    if (r <= ctl.tol * bn) break;
+    if (cycles + ctl.inner > ctl.max_cycles || !(r == r) || r > 1e6 * r0) {
+      status = 3;
+      break;
+    }
+    bool ok = true;
+    for (int k = 0; k < ctl.inner && ok; ++k) ok = vcycle_dev(H, G);
+    if (ok && ctl.mixed) {
+      ph_update64(F, H.op[0], G);
+      ok = G.sync();
+    }
+    if (!ok) {
+      status = 5;
+      break;
+    }
+    cycles += ctl.inner;
+    ++it;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl.out[0] = status;
+    ctl.out[1] = it;
+    ctl.out[2] = cycles;
+    ctl.out[3] = it;
+  }
+}
+
+// ------------------------------------------------------------ bottom inverse
+
+// dense matrix of the coarsest level over slots s = p * ncell + c; rows of
+// slots without an unknown are identity rows
+template <class T>
+__global__ void k_bottom_matrix(Op<T> o, double ceps0, double ceps1, int m, double* M) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  long long nc = o.ncell;
+  int p = (int)(i / nc);
+  long long c = i - p * nc;
+  double* row = M + i * m;
+  for (int j = 0; j < m; ++j) row[j] = 0.0;
+  uint8_t f = o.flags[c];
+  if (!((f >> p) & 1)) {
+    row[i] = 1.0;
+    return;
+  }
+  if (f & F_IRR) {
+    long long r = 2 * (long long)o.irr_of_cell[c] + p;
+    row[i] += o.diag[r];
+    for (int e = o.row_ptr[r]; e < o.row_ptr[r + 1]; ++e) {
+      unsigned cl = (unsigned)o.col[e];
+      long long j = (long long)(cl >> 30) * nc + (cl & 0x3fffffffu);
+      row[j] += o.val[e];
+    }
+    return;
+  }
+  double ce = p ? ceps1 : ceps0;
+  int I[3];
+  ijk(o, c, I);
+  long long st = 1;
+  for (int a = 0; a < o.D; ++a) {
+    if (I[a] > 0) {
+      row[i - st] -= ce;
+      row[i] += ce;
+    } else if (o.bc[2 * a]) {
+      row[i + st] -= ce / 3.0;
+      row[i] += 3.0 * ce;
+    }
+    if (I[a] < o.n[a] - 1) {
+      row[i + st] -= ce;
+      row[i] += ce;
+    } else if (o.bc[2 * a + 1]) {
+      row[i - st] -= ce / 3.0;
+      row[i] += 3.0 * ce;
+    }
+    st *= o.n[a];
+  }
+}
+
+// Gauss-Jordan inversion with partial pivoting by one CTA: A (m x m) is
+// destroyed, Ainv receives the inverse; status[0] = 1 when a pivot vanishes.
+__global__ void k_gauss_jordan(double* A, double* Ainv, int m, int* status) {
+  __shared__ double sv[1024];
+  __shared__ int si[1024];
+  __shared__ int piv;
+  __shared__ double pval;
+  for (long long e = threadIdx.x; e < (long long)m * m; e += blockDim.x) Ainv[e] = (e / m == e % m) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
+      double v = fabs(A[(long long)r * m + k]);
+      if (v > best) {
+        best = v;
+        bi = r;
+      }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if ((int)threadIdx.x < s) {
+        double a = sv[threadIdx.x], b = sv[threadIdx.x + s];
+        int ia = si[threadIdx.x], ib = si[threadIdx.x + s];
+        if (b > a || (b == a && ib < ia)) {
+          sv[threadIdx.x] = b;
+          si[threadIdx.x] = ib;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      piv = si[0];
+      pval = A[(long long)si[0] * m + k];
+      if (!(fabs(pval) > 1e-300)) status[0] = 1;
+    }
+    __syncthreads();
+    if (status[0]) return;
+    int pr = piv;
+    if (pr != k)
+      for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double t = A[(long long)k * m + j];
+        A[(long long)k * m + j] = A[(long long)pr * m + j];
+        A[(long long)pr * m + j] = t;
+        t = Ainv[(long long)k * m + j];
+        Ainv[(long long)k * m + j] = Ainv[(long long)pr * m + j];
+        Ainv[(long long)pr * m + j] = t;
+      }
+    __syncthreads();
+    double inv = 1.0 / pval;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      A[(long long)k * m + j] *= inv;
+      Ainv[(long long)k * m + j] *= inv;
+    }
+    __syncthreads();
+    for (long long e = threadIdx.x; e < (long long)m * m; e += blockDim.x) {
+      int r = (int)(e / m), j = (int)(e % m);
+      if (r == k) continue;
+      double fct = A[(long long)r * m + k];
+      if (j == k) continue;
+      A[e] -= fct * A[(long long)k * m + j];
+      Ainv[e] -= fct * Ainv[(long long)k * m + j];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+      if (r == k) continue;
+      double fct = A[(long long)r * m + k];
+      Ainv[(long long)r * m + k] -= fct * Ainv[(long long)k * m + k];
+      A[(long long)r * m + k] = 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+__global__ void k_convert(const double* a, T* b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (T)a[i];
+}
+
+}  // namespace ebp

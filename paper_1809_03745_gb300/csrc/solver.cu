@@ -10,7 +10,7 @@
 #include <vector>
 
 #include "eb_internal.h"
-#include "mg_kernels.cuh"
+#include "persistent.cuh"
 
 // ----------------------------------------------------------------- errors
 
@@ -266,6 +266,17 @@ struct eb_poisson {
   cudaGraphExec_t gexec = nullptr;
   long long launches = 0;   // kernels launched by the current call
   long long per_iter = 0;   // kernels in one iteration
+  // persistent solve
+  bool persistent = false;
+  int grid = 0;
+  void* d_hier = nullptr;     // Hier<float> or Hier<double>
+  Op<double>* d_fine = nullptr;
+  unsigned* d_bar = nullptr;  // count, gen, err
+  int* d_out = nullptr;       // status, iterations, cycles, slot
+  int* h_out = nullptr;       // pinned
+  unsigned long long* d_norms = nullptr;
+  void* d_binv = nullptr;
+  int bm = 0;
   std::vector<void*> allocs;
   long long bytes = 0;
 };
@@ -279,7 +290,7 @@ extern "C" void eb_solver_opts_default(eb_solver_opts* o) {
   o->precision = EB_PREC_MIXED;
   o->inner_cycles = 2;
   o->bottom_sweeps = 64;
-  o->use_graph = 1;
+  o->launch_mode = 0;
 }
 
 template <class T>
@@ -406,6 +417,141 @@ static void iteration(eb_poisson* P, cudaStream_t s) {
   }
 }
 
+
+template <class T>
+static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
+  Hier<T> H;
+  std::memset(&H, 0, sizeof(H));
+  H.nlev = P->nlev;
+  H.nu1 = P->o.nu1;
+  H.nu2 = P->o.nu2;
+  H.bsweeps = P->o.bottom_sweeps;
+  // levels of at most 4096 cells run inside one CTA
+  H.lc = P->nlev - 1;
+  for (int l = 0; l < P->nlev; ++l)
+    if (ops[l].ncell <= 4096) {
+      H.lc = std::min(l, P->nlev - 1);
+      break;
+    }
+  for (int l = 0; l < P->nlev; ++l) H.op[l] = ops[l];
+  eb_status st = EB_OK;
+  // dense inverse of the coarsest operator (FP64 Gauss-Jordan on the device)
+  const Op<T>& ob = ops[P->nlev - 1];
+  int m = (int)(P->G->n_phase * ob.ncell);
+  if (m <= 256) {
+    std::vector<void*> tmp;
+    double* M = (double*)dev_alloc(tmp, sizeof(double) * m * m, nullptr, &st);
+    double* Mi = (double*)dev_alloc(tmp, sizeof(double) * m * m, nullptr, &st);
+    int* stat = (int*)dev_alloc(tmp, sizeof(int), nullptr, &st);
+    T* binv = (T*)dev_alloc(P->allocs, sizeof(T) * m * m, &P->bytes, &st);
+    if (st == EB_OK) {
+      const DevLevel& Lb = P->G->L[P->nlev - 1];
+      double h2 = Lb.g.h * Lb.g.h;
+      cudaMemsetAsync(stat, 0, sizeof(int), P->s);
+      k_bottom_matrix<T><<<blocks(m), 256, 0, P->s>>>(ob, Lb.g.eps[0] / h2, Lb.g.eps[1] / h2, m, M);
+      k_gauss_jordan<<<1, 1024, 0, P->s>>>(M, Mi, m, stat);
+      k_convert<T><<<blocks((long long)m * m), 256, 0, P->s>>>(Mi, binv, (long long)m * m);
+      int hs = 0;
+      cudaError_t e = cudaMemcpyAsync(&hs, stat, sizeof(int), cudaMemcpyDeviceToHost, P->s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
+      if (e != cudaSuccess) st = cuda_fail(e, "bottom inverse");
+      if (st == EB_OK && hs == 0) {
+        H.bm = m;
+        H.binv = binv;
+      }
+    }
+    for (void* p : tmp) cudaFree(p);
+  }
+  if (st != EB_OK) return st;
+  P->bm = H.bm;
+  P->d_hier = dev_alloc(P->allocs, sizeof(Hier<T>), &P->bytes, &st);
+  if (st == EB_OK) {
+    cudaError_t e = cudaMemcpy(P->d_hier, &H, sizeof(Hier<T>), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = cuda_fail(e, "hierarchy upload");
+  }
+  return st;
+}
+
+static eb_status setup_persistent(eb_poisson* P) {
+  int dev = P->G->device, coop = 0, nsm = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  eb_status st = EB_OK;
+  bool mixed = P->o.precision == EB_PREC_MIXED;
+  st = mixed ? build_hier<float>(P, P->op32) : build_hier<double>(P, P->op64);
+  if (st != EB_OK) return st;
+  P->d_fine = (Op<double>*)dev_alloc(P->allocs, sizeof(Op<double>), &P->bytes, &st);
+  P->d_bar = (unsigned*)dev_alloc(P->allocs, 4 * sizeof(unsigned), &P->bytes, &st);
+  P->d_out = (int*)dev_alloc(P->allocs, 4 * sizeof(int), &P->bytes, &st);
+  P->d_norms = (unsigned long long*)dev_alloc(P->allocs, sizeof(unsigned long long) * (P->o.max_cycles + 2),
+                                              &P->bytes, &st);
+  if (st != EB_OK) return st;
+  cudaError_t e = cudaMemcpy(P->d_fine, &P->op64[0], sizeof(Op<double>), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMallocHost(&P->h_out, 4 * sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "persistent setup");
+  if (!coop || P->o.launch_mode != 0) return EB_OK;  // per-phase kernels
+  int per_sm = 0;
+  e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<float>, PT, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<double>, PT, 0);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return EB_OK;
+  }
+  P->grid = nsm * std::min(per_sm, 2);
+  P->persistent = true;
+  return EB_OK;
+}
+
+static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cycles, int* status) {
+  cudaStream_t s = P->s;
+  cudaMemsetAsync(P->d_bar, 0, 4 * sizeof(unsigned), s);
+  cudaMemsetAsync(P->d_norms, 0, sizeof(unsigned long long) * (P->o.max_cycles + 2), s);
+  SolveCtl ctl;
+  ctl.tol = P->o.tol;
+  ctl.max_cycles = P->o.max_cycles;
+  ctl.mixed = P->o.precision == EB_PREC_MIXED;
+  ctl.inner = ctl.mixed ? P->o.inner_cycles : 1;
+  ctl.bnorm = (const double*)(P->d_norm + 1);
+  ctl.norms = P->d_norms;
+  ctl.out = P->d_out;
+  Barrier B{P->d_bar, P->d_bar + 1, (int*)(P->d_bar + 2)};
+  void* args[4];
+  cudaError_t e;
+  if (ctl.mixed) {
+    const Hier<float>* H = (const Hier<float>*)P->d_hier;
+    const Op<double>* F = P->d_fine;
+    args[0] = (void*)&H;
+    args[1] = (void*)&F;
+    args[2] = (void*)&ctl;
+    args[3] = (void*)&B;
+    e = cudaLaunchCooperativeKernel((const void*)k_solve<float>, dim3(P->grid), dim3(PT), args, 0, s);
+  } else {
+    const Hier<double>* H = (const Hier<double>*)P->d_hier;
+    const Op<double>* F = P->d_fine;
+    args[0] = (void*)&H;
+    args[1] = (void*)&F;
+    args[2] = (void*)&ctl;
+    args[3] = (void*)&B;
+    e = cudaLaunchCooperativeKernel((const void*)k_solve<double>, dim3(P->grid), dim3(PT), args, 0, s);
+  }
+  counted();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(P->h_out, P->d_out, 4 * sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent solve");
+  int slot = P->h_out[3];
+  unsigned long long nv = 0, berr = 0;
+  e = cudaMemcpy(&nv, P->d_norms + slot, sizeof(nv), cudaMemcpyDeviceToHost);
+  unsigned bar[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(bar, P->d_bar, sizeof(bar), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent readback");
+  (void)berr;
+  std::memcpy(r, &nv, sizeof(double));
+  *iters = P->h_out[1];
+  *cycles = P->h_out[2];
+  *status = bar[2] ? EB_ERR_TIMEOUT : P->h_out[0];
+  return EB_OK;
+}
+
 extern "C" eb_status eb_poisson_setup(const eb_geom* G, const eb_solver_opts* opts, void* stream, eb_poisson** out) {
   if (!G || !out) {
     set_error("null argument");
@@ -418,7 +564,7 @@ extern "C" eb_status eb_poisson_setup(const eb_geom* G, const eb_solver_opts* op
   else eb_solver_opts_default(&P->o);
   eb_solver_opts& o = P->o;
   if (!(o.tol > 0.0) || o.max_cycles < 1 || o.nu1 < 0 || o.nu2 < 0 || o.inner_cycles < 1 || o.bottom_sweeps < 1 ||
-      (o.precision != EB_PREC_FP64 && o.precision != EB_PREC_MIXED)) {
+      (o.precision != EB_PREC_FP64 && o.precision != EB_PREC_MIXED) || o.launch_mode < 0 || o.launch_mode > 2) {
     delete P;
     set_error("invalid solver options");
     return EB_ERR_INVALID;
@@ -449,7 +595,8 @@ extern "C" eb_status eb_poisson_setup(const eb_geom* G, const eb_solver_opts* op
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) st = cuda_fail(e, "solver setup");
   }
-  if (st == EB_OK && o.use_graph) {
+  if (st == EB_OK) st = setup_persistent(P);
+  if (st == EB_OK && o.launch_mode != 2 && !P->persistent) {
     cudaError_t e = cudaStreamBeginCapture(P->s, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       g_count = &P->per_iter;
@@ -477,6 +624,7 @@ extern "C" void eb_poisson_destroy(eb_poisson* P) {
   if (P->ev) cudaEventDestroy(P->ev);
   if (P->s) cudaStreamDestroy(P->s);
   if (P->h_norm) cudaFreeHost(P->h_norm);
+  if (P->h_out) cudaFreeHost(P->h_out);
   for (void* p : P->allocs) cudaFree(p);
   delete P;
 }
@@ -561,6 +709,32 @@ extern "C" eb_status eb_poisson_solve(eb_poisson* P, const double* d_rhs, const 
   k_copy_masked<<<blocks(n), 256, 0, P->s>>>(F.flags, n, d_phi, P->phi64);
   counted(2);
   bool mixed = P->o.precision == EB_PREC_MIXED;
+  if (P->persistent) {
+    double r = 0.0, b = 0.0;
+    int iters = 0, cycles = 0, status = 0;
+    st = solve_persistent(P, &r, &iters, &cycles, &status);
+    if (st == EB_OK) {
+      cudaMemcpy(&b, P->d_norm + 1, sizeof(double), cudaMemcpyDeviceToHost);
+      if (status == EB_ERR_NOT_CONVERGED) set_error("cycle cap reached or residual diverged");
+      if (status == EB_ERR_TIMEOUT) set_error("a grid barrier wait gave up");
+      st = (eb_status)status;
+    }
+    k_copy_masked<<<blocks(n), 256, 0, P->s>>>(F.flags, n, P->phi64, d_phi);
+    counted();
+    g_count = nullptr;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
+    if (e != cudaSuccess && st == EB_OK) st = cuda_fail(e, "solve");
+    join_out(P, user);
+    inf.kernel_launches = P->launches;
+    inf.status = st;
+    inf.outer_iters = iters;
+    inf.vcycles = cycles;
+    inf.bnorm = b;
+    inf.rel_res = b > 0.0 ? r / b : 0.0;
+    if (info) *info = inf;
+    return st;
+  }
   resid64(P, P->s, mixed);
   double r = 0.0, b = 0.0;
   st = read_norms(P, &r, &b);

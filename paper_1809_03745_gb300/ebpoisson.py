@@ -59,7 +59,7 @@ class GeomArrays(C.Structure):
 
 class SolverOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_cycles", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
-                ("precision", C.c_int), ("inner_cycles", C.c_int), ("bottom_sweeps", C.c_int), ("use_graph", C.c_int)]
+                ("precision", C.c_int), ("inner_cycles", C.c_int), ("bottom_sweeps", C.c_int), ("launch_mode", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -286,12 +286,12 @@ class Poisson:
     """Multigrid solver bound to a Geometry (owns an eb_poisson)."""
 
     def __init__(self, geom: Geometry, *, precision="mixed", tol=1e-10, max_cycles=100, nu1=2, nu2=2,
-                 inner_cycles=2, bottom_sweeps=64, use_graph=True, stream=None):
+                 inner_cycles=2, bottom_sweeps=64, launch_mode=0, stream=None):
         self.geom = geom
         o = eb_solver_opts_default()
         o.tol, o.max_cycles, o.nu1, o.nu2 = tol, max_cycles, nu1, nu2
         o.precision = EB_PREC_MIXED if precision == "mixed" else EB_PREC_FP64
-        o.inner_cycles, o.bottom_sweeps, o.use_graph = inner_cycles, bottom_sweeps, int(bool(use_graph))
+        o.inner_cycles, o.bottom_sweeps, o.launch_mode = inner_cycles, bottom_sweeps, int(launch_mode)
         self.opts = o
         with torch.cuda.device(geom.device):
             self._h = eb_poisson_setup(geom._h, o, stream)

@@ -94,7 +94,9 @@ def test_solve_parity(case, precision, oracles):
     name, d, S, sig = case
     og, ophi = oracles[name][:2]
     g = E.Geometry(d)
-    P = E.Poisson(g, precision=precision, tol=1e-13, max_cycles=200)
+    # 1e-12 relative residual is above the FP64 rounding floor of every case
+    # here; the oracle's direct solve is exact to ~1e-15
+    P = E.Poisson(g, precision=precision, tol=1e-12, max_cycles=200)
     phi, info = P.solve(torch.from_numpy(S), torch.from_numpy(sig))
     assert info["status"] == 0, info
     got = phi.cpu().numpy()
