@@ -231,6 +231,15 @@ eb_status eb_field_eval(eb_poisson* P, const double* d_phi, const double* d_sigm
  * write coarse b and x). */
 eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, double* ms_per_launch, double* bytes_per_launch,
                              void* stream);
+/* kernel 2 of eb_poisson_profile times `reps` grid barriers of the persistent
+ * solve kernel (bytes_per_launch receives the number of CTAs). */
+
+/* Diagnostics (no counterpart in the paper): durations in ms of the first
+ * V-cycle of the last persistent solve, split into [0] the down leg over the
+ * levels that use the whole grid, [1] the levels solved inside one CTA
+ * including the bottom, [2] the up leg, [3] one FP64 residual evaluation with
+ * its convergence test.  Writes min(n, 4) values. */
+eb_status eb_poisson_trace(eb_poisson* P, double* ms, int n);
 
 #ifdef __cplusplus
 }

@@ -234,7 +234,12 @@ static double edge_crossing(const or_geom* g, const long I[3], int a, int la)
     else hi = m;
   }
   double c = 0.5 * (lo + hi);
-  return (c - node_x(g, a, I[a])) / d->h;
+  double fr = (c - node_x(g, a, I[a])) / d->h;
+  /* a crossing within 1e-8 h of a node is put on the node: the boundary moves
+   * by less than 1e-8 h, and fragments of vanishing size become exactly empty */
+  if (fr < 1e-8) fr = 0.0;
+  if (fr > 1.0 - 1e-8) fr = 1.0;
+  return fr;
 }
 
 /* ---------------------------------------------------- geometry: one face */
@@ -439,8 +444,15 @@ static int eb_centroid(or_geom* g, const long I[3], double u[3])
     W = W + ar;
     for (int q = 0; q < 3; ++q) S[q] = S[q] + ar * ((v0[q] + v1[q] + v2[q]) / 3.0);
   }
-  if (!(W > 0.0)) return OR_UNSUPPORTED;
-  for (int q = 0; q < 3; ++q) u[q] = S[q] / W;
+  if (W > 0.0) {
+    for (int q = 0; q < 3; ++q) u[q] = S[q] / W;
+  } else { /* all crossings on one line or point: their mean */
+    for (int q = 0; q < 3; ++q) {
+      double t = 0.0;
+      for (int k = 0; k < len; ++k) t = t + P[loop[k]][q];
+      u[q] = t / (double)len;
+    }
+  }
   return OR_OK;
 }
 
@@ -806,15 +818,16 @@ or_geom* or_geom_build(const or_desc* d, int* status)
     int st = cell_geometry(g, c);
     if (st != OR_OK) { g->status = st; g->bad_cell = c; *status = st; return g; }
   }
-  /* 5. degrees of freedom: a fragment with positive volume fraction and an
-   * open face that is interior or a Dirichlet wall */
+  /* 5. degrees of freedom: a fragment with an open face that is interior or a
+   * Dirichlet wall (a fragment of zero volume with such a face carries the
+   * boundary condition of its EB into the neighbouring cell) */
   g->ndof = 0;
   for (long c = 0; c < g->ncell; ++c) {
     long I[3];
     cell_ijk(g, c, I);
     for (int p = 0; p < 2; ++p) {
       g->dof[p][c] = -1;
-      if (g->kappa[p][c] > 0.0 && open_face(g, I, p)) g->dof[p][c] = g->ndof++;
+      if (open_face(g, I, p)) g->dof[p][c] = g->ndof++;
     }
   }
   /* 6. EB stencils */

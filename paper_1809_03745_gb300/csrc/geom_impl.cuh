@@ -113,7 +113,12 @@ EBP_HDN double edge_crossing(const Csg& c, const Grid& g, const uint8_t* lab, co
     else hi = m;
   }
   double cr = 0.5 * (lo + hi);
-  return (cr - node_x(g, a, I[a])) / g.h;
+  double fr = (cr - node_x(g, a, I[a])) / g.h;
+  // a crossing within 1e-8 h of a node is put on the node: the boundary moves
+  // by less than 1e-8 h, and fragments of vanishing size become exactly empty
+  if (fr < 1e-8) fr = 0.0;
+  if (fr > 1.0 - 1e-8) fr = 1.0;
+  return fr;
 }
 
 // ------------------------------------------------------------------ faces
@@ -330,8 +335,15 @@ EBP_HDN int eb_centroid_local(const Csg& c, const Grid& g, const uint8_t* lab, c
     W = W + ar;
     for (int q = 0; q < 3; ++q) S[q] = S[q] + ar * ((v0[q] + v1[q] + v2[q]) / 3.0);
   }
-  if (!(W > 0.0)) return ST_UNSUPPORTED;
-  for (int q = 0; q < 3; ++q) u[q] = S[q] / W;
+  if (W > 0.0) {
+    for (int q = 0; q < 3; ++q) u[q] = S[q] / W;
+  } else {  // all crossings on one line or point: their mean
+    for (int q = 0; q < 3; ++q) {
+      double t = 0.0;
+      for (int k = 0; k < len; ++k) t = t + P[loop[k]][q];
+      u[q] = t / (double)len;
+    }
+  }
   return 0;
 }
 

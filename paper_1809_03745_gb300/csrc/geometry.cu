@@ -238,8 +238,8 @@ __global__ void k_cut_geom(const Csg* csg, Grid g, const uint8_t* lab, CutRecord
   if (st) atomicOr(status, st);
 }
 
-// unknowns of cut fragments: positive volume and an open interior or
-// Dirichlet face
+// unknowns of cut fragments: an open interior or Dirichlet face (a fragment
+// of zero volume with such a face carries its EB's boundary condition)
 __global__ void k_dofs(Grid g, CutRecords R) {
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= R.ncut) return;
@@ -247,7 +247,7 @@ __global__ void k_dofs(Grid g, CutRecords R) {
   cell_ijk(g, R.cell[q], I);
   uint8_t m = 0;
   for (int p = 0; p < 2; ++p)
-    if (R.kappa[p * R.ncut + q] > 0.0 && record_open_face(g, R, q, I, p)) m |= (uint8_t)(1 << p);
+    if (record_open_face(g, R, q, I, p)) m |= (uint8_t)(1 << p);
   R.dofm[q] = m;
   // an interface cell that keeps a single fragment (the interface runs
   // through a node, or the other fragment has no open face) carries no

@@ -41,7 +41,14 @@ struct SolveCtl {
   const double* bnorm;        // max |b|
   unsigned long long* norms;  // [max_cycles + 2] per-iteration residual max, zeroed by the host
   int* out;                   // [0] status, [1] outer iterations, [2] V-cycles, [3] norm slot of the final residual
+  unsigned long long* stamps; // [8] globaltimer stamps of the first V-cycle (diagnostics)
 };
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // Grid barrier with a bounded wait: returns false (and leaves err set) when
 // some CTA did not arrive in time, after which every CTA falls through.
@@ -253,7 +260,9 @@ __device__ bool ph_bottom(const Hier<T>& H, const Ctx& c) {
 }
 
 template <class T>
-__device__ bool vcycle_dev(const Hier<T>& H, const Ctx& G) {
+__device__ bool vcycle_dev(const Hier<T>& H, const Ctx& G, unsigned long long* stamps) {
+  const bool stamp = stamps && blockIdx.x == 0 && threadIdx.x == 0;
+  if (stamp) stamps[0] = now_ns();
   for (int l = 0; l < H.lc; ++l) {
     const Op<T>& o = H.op[l];
     if (!ph_smooth(o, H.nu1, G)) return false;
@@ -264,6 +273,7 @@ __device__ bool vcycle_dev(const Hier<T>& H, const Ctx& G) {
     ph_restrict(o, H.op[l + 1], G);
     if (!G.sync()) return false;
   }
+  if (stamp) stamps[1] = now_ns();
   if (blockIdx.x == 0) {
     Ctx L{(long long)threadIdx.x, (long long)blockDim.x, true, G.B};
     for (int l = H.lc; l < H.nlev - 1; ++l) {
@@ -283,12 +293,14 @@ __device__ bool vcycle_dev(const Hier<T>& H, const Ctx& G) {
       ph_smooth(H.op[l], H.nu2, L);
     }
   }
+  if (stamp) stamps[2] = now_ns();
   if (!G.sync()) return false;
   for (int l = H.lc - 1; l >= 0; --l) {
     ph_prolong(H.op[l], H.op[l + 1], G);
     if (!G.sync()) return false;
     if (!ph_smooth(H.op[l], H.nu2, G)) return false;
   }
+  if (stamp) stamps[3] = now_ns();
   return true;
 }
 
@@ -362,11 +374,13 @@ __global__ void __launch_bounds__(PT) k_solve(const Hier<T>* __restrict__ Hg, co
     }
   }
   for (; bn != 0.0;) {
+    if (it == 1 && ctl.stamps && blockIdx.x == 0 && threadIdx.x == 0) ctl.stamps[4] = now_ns();
     if (!ph_resid64(F, H, ctl.mixed, ctl.norms + it, G)) {
       status = 5;
       break;
     }
     r = load_norm(ctl.norms + it);
+    if (it == 1 && ctl.stamps && blockIdx.x == 0 && threadIdx.x == 0) ctl.stamps[5] = now_ns();
     if (it == 0) r0 = r;
     if (r <= ctl.tol * bn) break;
     if (cycles + ctl.inner > ctl.max_cycles || !(r == r) || r > 1e6 * r0) {
@@ -374,7 +388,7 @@ __global__ void __launch_bounds__(PT) k_solve(const Hier<T>* __restrict__ Hg, co
       break;
     }
     bool ok = true;
-    for (int k = 0; k < ctl.inner && ok; ++k) ok = vcycle_dev(H, G);
+    for (int k = 0; k < ctl.inner && ok; ++k) ok = vcycle_dev(H, G, (it == 0 && k == 0) ? ctl.stamps : nullptr);
     if (ok && ctl.mixed) {
       ph_update64(F, H.op[0], G);
       ok = G.sync();
@@ -527,4 +541,12 @@ __global__ void k_convert(const double* a, T* b, long long n) {
   if (i < n) b[i] = (T)a[i];
 }
 
+}  // namespace ebp
+
+namespace ebp {
+// barrier microbenchmark: reps grid barriers
+__global__ void __launch_bounds__(PT) k_barrier_bench(Barrier B, int reps) {
+  for (int i = 0; i < reps; ++i)
+    if (!grid_sync(B)) return;
+}
 }  // namespace ebp

@@ -275,6 +275,7 @@ struct eb_poisson {
   int* d_out = nullptr;       // status, iterations, cycles, slot
   int* h_out = nullptr;       // pinned
   unsigned long long* d_norms = nullptr;
+  unsigned long long* d_stamps = nullptr;  // [8] first-V-cycle timestamps of the last solve
   void* d_binv = nullptr;
   int bm = 0;
   std::vector<void*> allocs;
@@ -485,6 +486,8 @@ static eb_status setup_persistent(eb_poisson* P) {
   P->d_out = (int*)dev_alloc(P->allocs, 4 * sizeof(int), &P->bytes, &st);
   P->d_norms = (unsigned long long*)dev_alloc(P->allocs, sizeof(unsigned long long) * (P->o.max_cycles + 2),
                                               &P->bytes, &st);
+  P->d_stamps = (unsigned long long*)dev_alloc(P->allocs, sizeof(unsigned long long) * 8, &P->bytes, &st);
+  if (st == EB_OK) cudaMemset(P->d_stamps, 0, sizeof(unsigned long long) * 8);
   if (st != EB_OK) return st;
   cudaError_t e = cudaMemcpy(P->d_fine, &P->op64[0], sizeof(Op<double>), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMallocHost(&P->h_out, 4 * sizeof(int));
@@ -514,6 +517,7 @@ static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cyc
   ctl.bnorm = (const double*)(P->d_norm + 1);
   ctl.norms = P->d_norms;
   ctl.out = P->d_out;
+  ctl.stamps = P->d_stamps;
   Barrier B{P->d_bar, P->d_bar + 1, (int*)(P->d_bar + 2)};
   void* args[4];
   cudaError_t e;
@@ -803,6 +807,31 @@ extern "C" eb_status eb_field_eval(eb_poisson* P, const double* d_phi, const dou
 }
 
 extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, double* ms, double* bytes, void* stream) {
+  if (P && kernel == 2 && reps >= 1 && ms && bytes) {
+    if (!P->persistent) {
+      set_error("no persistent kernel on this device");
+      return EB_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(P->d_bar, 0, 4 * sizeof(unsigned), s);
+    Barrier B{P->d_bar, P->d_bar + 1, (int*)(P->d_bar + 2)};
+    void* args[2] = {(void*)&B, (void*)&reps};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_barrier_bench, dim3(P->grid), dim3(PT), args, 0, s);
+    cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "barrier benchmark");
+    *ms = (double)t / reps;
+    *bytes = (double)P->grid;
+    return EB_OK;
+  }
   if (!P || reps < 1 || (kernel != 0 && kernel != 1) || !ms || !bytes) {
     set_error("invalid argument");
     return EB_ERR_INVALID;
@@ -841,5 +870,22 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
   *ms = (double)t / reps;
   if (kernel == 0) *bytes = (double)n * (3.0 * tb + 1.0) / 2.0;
   else *bytes = (double)n * (2.0 * tb + 1.0) + (double)n / (double)(1 << D) * 2.0 * tb;
+  return EB_OK;
+}
+
+extern "C" eb_status eb_poisson_trace(eb_poisson* P, double* ms, int n) {
+  if (!P || !ms || n < 1) {
+    set_error("invalid argument");
+    return EB_ERR_INVALID;
+  }
+  if (!P->d_stamps) {
+    set_error("no trace on this path");
+    return EB_ERR_UNSUPPORTED;
+  }
+  unsigned long long t[8];
+  cudaError_t e = cudaMemcpy(t, P->d_stamps, sizeof(t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "trace");
+  double v[4] = {(t[1] - t[0]) * 1e-6, (t[2] - t[1]) * 1e-6, (t[3] - t[2]) * 1e-6, (t[5] - t[4]) * 1e-6};
+  for (int i = 0; i < n && i < 4; ++i) ms[i] = v[i];
   return EB_OK;
 }

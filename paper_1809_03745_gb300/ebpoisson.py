@@ -69,7 +69,7 @@ class SolveInfo(C.Structure):
 
 EXPORTS = ["eb_status_str", "eb_last_error", "eb_geom_build", "eb_geom_query", "eb_geom_destroy", "eb_geom_export",
            "eb_solver_opts_default", "eb_poisson_setup", "eb_poisson_destroy", "eb_poisson_residual",
-           "eb_poisson_solve", "eb_field_eval", "eb_poisson_profile"]
+           "eb_poisson_solve", "eb_field_eval", "eb_poisson_profile", "eb_poisson_trace"]
 
 
 def lib_path() -> str:
@@ -109,6 +109,8 @@ def load(build_if_missing: bool = False):
         lib.eb_poisson_solve.argtypes = [P, P, P, P, C.POINTER(SolveInfo), P]
         lib.eb_field_eval.restype = C.c_int
         lib.eb_field_eval.argtypes = [P, P, P, P, P, P]
+        lib.eb_poisson_trace.restype = C.c_int
+        lib.eb_poisson_trace.argtypes = [P, C.POINTER(C.c_double), C.c_int]
         lib.eb_poisson_profile.restype = C.c_int
         lib.eb_poisson_profile.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), P]
         _lib = lib
@@ -334,6 +336,12 @@ class Poisson:
     def profile(self, kernel: int, reps: int = 50, stream=None):
         """(ms per launch, algorithmic bytes per launch) of a finest-level kernel."""
         return eb_poisson_profile(self._h, kernel, reps, stream)
+
+    def trace(self):
+        """ms of the first V-cycle of the last solve: down leg, one-CTA coarse levels, up leg, FP64 residual."""
+        v = (C.c_double * 4)()
+        _check(load().eb_poisson_trace(self._h, v, 4), "eb_poisson_trace")
+        return dict(down=v[0], coarse=v[1], up=v[2], resid64=v[3])
 
     def close(self):
         if getattr(self, "_h", None):
