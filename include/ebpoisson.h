@@ -234,12 +234,14 @@ eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, double* ms_per
 /* kernel 2 of eb_poisson_profile times `reps` grid barriers of the persistent
  * solve kernel (bytes_per_launch receives the number of CTAs). */
 
-/* Diagnostics (no counterpart in the paper): durations in ms of the first
- * V-cycle of the last persistent solve, split into [0] the down leg over the
- * levels that use the whole grid, [1] the levels solved inside one CTA
- * including the bottom, [2] the up leg, [3] one FP64 residual evaluation with
- * its convergence test.  Writes min(n, 4) values. */
-eb_status eb_poisson_trace(eb_poisson* P, double* ms, int n);
+/* Diagnostics (no counterpart in the paper): the phases of the first V-cycle
+ * of the last persistent solve.  out[0] = number of phases m; then for each
+ * phase i, out[1+2i] = its code ((level << 4) | kind; kinds 1 red regular
+ * cells, 3 black regular cells, 2 sparse rows computed, 4 sparse rows
+ * written, 5 sparse residual rows, 6 residual + restriction, 7 prolongation,
+ * 8 end of the one-CTA levels, 9 bottom solve) and
+ * out[2+2i] its duration in ms.  n is the capacity of out. */
+eb_status eb_poisson_trace(eb_poisson* P, double* out, int n);
 
 #ifdef __cplusplus
 }

@@ -11,8 +11,27 @@
 
 namespace ebp {
 
+// Division of 32-bit unsigned values by a fixed divisor with a multiply-high
+// and a shift (Granlund-Montgomery round-up method); exact for every 32-bit x.
+struct FastDiv {
+  unsigned d, m, s;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f;
+  f.d = d;
+  unsigned s = 0;
+  while ((1ull << s) < d) ++s;
+  f.s = s;
+  f.m = (unsigned)((((1ull << s) - d) << 32) / d + 1);
+  return f;
+}
+__device__ __forceinline__ unsigned fdiv(unsigned x, const FastDiv& f) {
+  return (unsigned)(((unsigned long long)__umulhi(x, f.m) + x) >> f.s);
+}
+
 template <class T>
 struct Op {
+  FastDiv dn0, dn1, dhx;  // n[0], n[1] and the cells of one colour per x row, (n[0] + 1) / 2
   int D;
   int n[3];
   long long ncell;
@@ -82,22 +101,25 @@ __device__ __forceinline__ void reg_stencil(const Op<T>& o, const T* x, const in
 
 template <class T>
 __device__ __forceinline__ void ijk(const Op<T>& o, long long c, int I[3]) {
-  I[0] = (int)(c % o.n[0]);
-  I[1] = (int)((c / o.n[0]) % o.n[1]);
-  I[2] = (int)(c / ((long long)o.n[0] * o.n[1]));
+  unsigned cu = (unsigned)c;
+  unsigned r = fdiv(cu, o.dn0);
+  unsigned k = fdiv(r, o.dn1);
+  I[0] = (int)(cu - r * (unsigned)o.n[0]);
+  I[1] = (int)(r - k * (unsigned)o.n[1]);
+  I[2] = (int)k;
 }
 
 // one colour of red-black Gauss-Seidel on regular cells; thread per cell pair along x
 template <class T>
 __global__ void k_smooth_dense(Op<T> o, int colour) {
-  long long half = o.ncell >> 1;
+  int hx = (o.n[0] + 1) >> 1;  // cells of one colour per x row (either parity of n0)
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= half) return;
-  int hx = o.n[0] >> 1;
+  if (t >= (o.ncell / o.n[0]) * hx) return;
   long long row = t / hx;
   int j = (int)(row % o.n[1]);
   int k = (int)(row / o.n[1]);
   int i = 2 * (int)(t % hx) + ((j + k + colour) & 1);
+  if (i >= o.n[0]) return;
   long long c = (long long)i + (long long)o.n[0] * row;
   uint8_t f = o.flags[c];
   if ((f & F_IRR) || !(f & 3)) return;
@@ -110,12 +132,29 @@ __global__ void k_smooth_dense(Op<T> o, int colour) {
   x[c] = (o.h2e[p] * o.b[p][c] + sum) * inv_count(dg, T(0));
 }
 
+// sum over the off-diagonal entries of sparse row r; entries are taken eight
+// at a time with every load of a batch issued before the products
 template <class T>
 __device__ __forceinline__ double row_dot(const Op<T>& o, long long r) {
   double s = 0.0;
-  for (int e = o.row_ptr[r]; e < o.row_ptr[r + 1]; ++e) {
-    unsigned cl = (unsigned)o.col[e];
-    s += o.val[e] * (double)o.x[cl >> 30][cl & 0x3fffffffu];
+  const int e0 = o.row_ptr[r], e1 = o.row_ptr[r + 1];
+  for (int e = e0; e < e1; e += 8) {
+    unsigned cl[8];
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      cl[k] = 0u;
+      v[k] = 0.0;
+      if (e + k < e1) {
+        cl[k] = (unsigned)o.col[e + k];
+        v[k] = o.val[e + k];
+      }
+    }
+    T xv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) xv[k] = (e + k < e1) ? o.x[cl[k] >> 30][cl[k] & 0x3fffffffu] : T(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += v[k] * (double)xv[k];
   }
   return s;
 }
@@ -257,15 +296,16 @@ __global__ void k_prolong(Op<T> f, Op<T> c) {
 // relaxation bottom solver for multiphase problems).
 template <class T>
 __global__ void k_bottom(Op<T> o, int sweeps) {
-  long long half = o.ncell >> 1;
-  int hx = o.n[0] >> 1;
+  int hx = (o.n[0] + 1) >> 1;
+  long long work = (o.ncell / o.n[0]) * hx;
   for (int it = 0; it < sweeps; ++it) {
     for (int colour = 0; colour < 2; ++colour) {
-      for (long long t = threadIdx.x; t < half; t += blockDim.x) {
+      for (long long t = threadIdx.x; t < work; t += blockDim.x) {
         long long row = t / hx;
         int j = (int)(row % o.n[1]);
         int k = (int)(row / o.n[1]);
         int i = 2 * (int)(t % hx) + ((j + k + colour) & 1);
+        if (i >= o.n[0]) continue;
         long long c = (long long)i + (long long)o.n[0] * row;
         uint8_t f = o.flags[c];
         if ((f & F_IRR) || !(f & 3)) continue;

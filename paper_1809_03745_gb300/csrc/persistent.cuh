@@ -23,14 +23,16 @@ struct Hier {
   int nu1, nu2;
   int bm;       // order of the bottom inverse (0: relax the bottom instead)
   int bsweeps;  // relaxation sweeps when bm == 0
+  int smem;     // 1: levels lc.. keep x, b, flags and row scratch in CTA 0's shared memory
+  int smem_bytes;
   const T* binv;  // [bm][bm], slot s = p * ncell + c of the coarsest level
+  int off_x[MAXLEV][2], off_b[MAXLEV][2], off_f[MAXLEV], off_t[MAXLEV];  // byte offsets into shared memory
   Op<T> op[MAXLEV];
 };
 
 struct Barrier {
-  unsigned* count;
-  unsigned* gen;
-  int* err;  // set when a wait gave up
+  unsigned* count;  // arrivals, monotonically increasing over one launch (zeroed before it)
+  int* err;         // set when a wait gave up
 };
 
 struct SolveCtl {
@@ -41,7 +43,7 @@ struct SolveCtl {
   const double* bnorm;        // max |b|
   unsigned long long* norms;  // [max_cycles + 2] per-iteration residual max, zeroed by the host
   int* out;                   // [0] status, [1] outer iterations, [2] V-cycles, [3] norm slot of the final residual
-  unsigned long long* stamps; // [8] globaltimer stamps of the first V-cycle (diagnostics)
+  unsigned long long* trace;  // [1 + TRMAX]: count, then (code << 48 | ns) per phase of the first V-cycle
 };
 
 __device__ __forceinline__ unsigned long long now_ns() {
@@ -50,30 +52,35 @@ __device__ __forceinline__ unsigned long long now_ns() {
   return t;
 }
 
-// Grid barrier with a bounded wait: returns false (and leaves err set) when
-// some CTA did not arrive in time, after which every CTA falls through.
-__device__ __forceinline__ bool grid_sync(const Barrier& B) {
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier: every CTA adds one arrival to a counter that only grows and
+// waits until it reaches (barriers passed) x (CTAs).  The wait is bounded by
+// the SM clock: on expiry the error word is set and every CTA falls through
+// (returns false) at this and every later barrier.
+__device__ __forceinline__ bool grid_sync(const Barrier& B, unsigned* epoch) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile int* ve = B.err;
     if (*ve == 0) {
-      volatile unsigned* vg = B.gen;
-      unsigned g = *vg;
+      unsigned target = (*epoch + 1u) * gridDim.x;
+      *epoch += 1u;
       __threadfence();
-      unsigned arrived = atomicAdd(B.count, 1u);
-      if (arrived == gridDim.x - 1) {
-        atomicExch(B.count, 0u);
-        __threadfence();
-        atomicAdd(B.gen, 1u);
-      } else {
-        long long t0 = clock64();
-        while (*vg == g) {
-          if (clock64() - t0 > BAR_WAIT_CYCLES) {
-            atomicOr(B.err, 1);
-            break;
-          }
-          __nanosleep(20);
+      red_release_add(B.count, 1u);
+      long long t0 = clock64();
+      while (ld_acquire(B.count) < target) {
+        if (clock64() - t0 > BAR_WAIT_CYCLES) {
+          atomicOr(B.err, 1);
+          break;
         }
+        __nanosleep(16);
       }
       __threadfence();
     }
@@ -84,50 +91,119 @@ __device__ __forceinline__ bool grid_sync(const Barrier& B) {
 }
 
 // execution context of a phase: the whole grid, or CTA 0 alone
+constexpr int TRMAX = 4096;  // phase records of the first V-cycle (diagnostics)
+
 struct Ctx {
   long long i0, st;
   bool local;
   Barrier B;
-  __device__ __forceinline__ bool sync() const {
-    if (local) {
-      __syncthreads();
-      return true;
+  unsigned* epoch;         // shared-memory barrier count of this CTA
+  unsigned long long* tr;  // phase trace (CTA 0, first V-cycle) or null
+  unsigned* tn;            // shared-memory trace length
+  // barrier ending a phase; `code` = (level << 4) | kind names the phase for the trace
+  __device__ __forceinline__ bool sync(int code) const {
+    bool ok = true;
+    if (local) __syncthreads();
+    else ok = grid_sync(B, epoch);
+    if (tr && blockIdx.x == 0 && threadIdx.x == 0 && *tn < TRMAX) {
+      tr[1 + *tn] = ((unsigned long long)code << 48) | (now_ns() & 0xffffffffffffULL);
+      *tn += 1;
     }
-    return grid_sync(B);
+    return ok;
   }
 };
 
+
+// One colour of red-black Gauss-Seidel on regular cells.  Each thread takes
+// U cells a grid stride apart and issues all their loads before any store, so
+// that many loads are in flight per thread (the phase is latency bound).
 template <class T>
 __device__ __forceinline__ void ph_dense(const Op<T>& o, int colour, const Ctx& c) {
-  long long half = o.ncell >> 1;
-  int hx = o.n[0] >> 1;
-  for (long long t = c.i0; t < half; t += c.st) {
-    long long row = t / hx;
-    int j = (int)(row % o.n[1]);
-    int k = (int)(row / o.n[1]);
-    int i = 2 * (int)(t % hx) + ((j + k + colour) & 1);
-    long long cc = (long long)i + (long long)o.n[0] * row;
-    uint8_t f = o.flags[cc];
-    if ((f & F_IRR) || !(f & 3)) continue;
-    int p = (f & 1) ? 0 : 1;
-    T* x = o.x[p];
-    int I[3] = {i, j, k};
-    T sum;
-    int dg;
-    reg_stencil(o, x, I, cc, sum, dg);
-    x[cc] = (o.h2e[p] * o.b[p][cc] + sum) * inv_count(dg, T(0));
+  constexpr int U = 4;
+  int hx = (o.n[0] + 1) >> 1;  // cells of one colour per x row (either parity of n0)
+  long long work = (o.ncell / o.n[0]) * hx;
+  for (long long t0 = c.i0; t0 < work; t0 += U * c.st) {
+    long long cc[U];
+    int I[U][3];
+    bool act[U];
+    int pp[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      long long t = t0 + u * c.st;
+      act[u] = false;
+      cc[u] = 0;
+      pp[u] = 0;
+      if (t < work) {
+        unsigned tu = (unsigned)t;
+        unsigned row = fdiv(tu, o.dhx);
+        unsigned kq = fdiv(row, o.dn1);
+        int j = (int)(row - kq * (unsigned)o.n[1]);
+        int k = (int)kq;
+        int i = 2 * (int)(tu - row * (unsigned)hx) + ((j + k + colour) & 1);
+        I[u][0] = i;
+        I[u][1] = j;
+        I[u][2] = k;
+        if (i < o.n[0]) {
+          cc[u] = (long long)i + (long long)o.n[0] * row;
+          uint8_t f = o.flags[cc[u]];
+          act[u] = !(f & F_IRR) && (f & 3);
+          pp[u] = (f & 1) ? 0 : 1;
+        }
+      }
+    }
+    T val[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      val[u] = T(0);
+      if (act[u]) {
+        T sum;
+        int dg;
+        reg_stencil(o, o.x[pp[u]], I[u], cc[u], sum, dg);
+        val[u] = (o.h2e[pp[u]] * o.b[pp[u]][cc[u]] + sum) * inv_count(dg, T(0));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (act[u]) o.x[pp[u]][cc[u]] = val[u];
   }
 }
 
+// sparse rows [rb, re), one warp per row (lanes over the entries, then a
+// shuffle reduction): mode 0 writes the Gauss-Seidel value, mode 1 the
+// residual, into tmp.  Warps of the grid are interleaved over the CTAs so a
+// few hundred rows still spread over every SM.
 template <class T>
 __device__ __forceinline__ void ph_rows(const Op<T>& o, long long rb, long long re, int mode, const Ctx& c) {
-  for (long long r = rb + c.i0; r < re; r += c.st) {
+  if (c.local) {  // inside one CTA: a thread per row keeps every warp busy
+    for (long long r = rb + threadIdx.x; r < re; r += blockDim.x) {
+      double d = o.diag[r];
+      if (d == 0.0) continue;
+      long long cell = o.irr_cell[r >> 1];
+      int p = (int)(r & 1);
+      double v = (double)o.b[p][cell] - row_dot(o, r);
+      o.tmp[r] = mode == 0 ? (T)(v / d) : (T)(v - d * (double)o.x[p][cell]);
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const long long w0 = c.local ? (threadIdx.x >> 5) : (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const long long ws = c.local ? (blockDim.x >> 5) : (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long r = rb + w0; r < re; r += ws) {
     double d = o.diag[r];
     if (d == 0.0) continue;
-    long long cell = o.irr_cell[r >> 1];
-    int p = (int)(r & 1);
-    double s = (double)o.b[p][cell] - row_dot(o, r);
-    o.tmp[r] = mode == 0 ? (T)(s / d) : (T)(s - d * (double)o.x[p][cell]);
+    const int e0 = o.row_ptr[r], e1 = o.row_ptr[r + 1];
+    double s = 0.0;
+    for (int e = e0 + lane; e < e1; e += 32) {
+      unsigned cl = (unsigned)o.col[e];
+      s += o.val[e] * (double)o.x[cl >> 30][cl & 0x3fffffffu];
+    }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+      long long cell = o.irr_cell[r >> 1];
+      int p = (int)(r & 1);
+      double v = (double)o.b[p][cell] - s;
+      o.tmp[r] = mode == 0 ? (T)(v / d) : (T)(v - d * (double)o.x[p][cell]);
+    }
   }
 }
 
@@ -163,144 +239,186 @@ __device__ __forceinline__ void ph_restrict(const Op<T>& f, const Op<T>& co, con
   }
 }
 
+// x_fine += P x_coarse, (bi/tri)linear where all coarse cells of the
+// interpolation carry an unknown of the phase, else piecewise constant; two
+// fine cells per thread with their loads issued first.
+template <class T>
+__device__ __forceinline__ T prolong_value(const Op<T>& f, const Op<T>& co, long long C, const int sdir[3], bool inside,
+                                           int p) {
+  const long long st3[3] = {1, co.n[0], (long long)co.n[0] * co.n[1]};
+  const int ncn = 1 << f.D;
+  const T* xc = co.x[p];
+  bool lin = inside;
+  if (lin)
+    for (int k = 1; k < ncn && lin; ++k) {
+      long long n = C;
+      for (int a = 0; a < f.D; ++a)
+        if ((k >> a) & 1) n += sdir[a] * st3[a];
+      if (!((co.flags[n] >> p) & 1)) lin = false;
+    }
+  if (!lin) return xc[C];
+  T acc = T(0);
+  for (int k = 0; k < ncn; ++k) {
+    long long n = C;
+    T w = T(1);
+    for (int a = 0; a < f.D; ++a) {
+      if ((k >> a) & 1) {
+        n += sdir[a] * st3[a];
+        w *= T(0.25);
+      } else {
+        w *= T(0.75);
+      }
+    }
+    acc += w * xc[n];
+  }
+  return acc;
+}
+
 template <class T>
 __device__ __forceinline__ void ph_prolong(const Op<T>& f, const Op<T>& co, const Ctx& c) {
-  long long st3[3] = {1, co.n[0], (long long)co.n[0] * co.n[1]};
-  int ncn = 1 << f.D;
-  for (long long cf = c.i0; cf < f.ncell; cf += c.st) {
-    uint8_t fl = f.flags[cf];
-    if (!(fl & 3)) continue;
-    int I[3];
-    ijk(f, cf, I);
-    int IC[3] = {I[0] >> 1, I[1] >> 1, f.D == 3 ? I[2] >> 1 : 0};
-    int sdir[3];
-    bool inside = true;
-    for (int a = 0; a < 3; ++a) {
-      sdir[a] = (I[a] & 1) ? 1 : -1;
-      if (a < f.D) {
-        int nb = IC[a] + sdir[a];
-        if (nb < 0 || nb >= co.n[a]) inside = false;
-      }
-    }
-    long long C = (long long)IC[0] + (long long)co.n[0] * ((long long)IC[1] + (long long)co.n[1] * IC[2]);
-    for (int p = 0; p < 2; ++p) {
-      if (!((fl >> p) & 1)) continue;
-      const T* xc = co.x[p];
-      bool lin = inside;
-      if (lin)
-        for (int k = 1; k < ncn && lin; ++k) {
-          long long n = C;
-          for (int a = 0; a < f.D; ++a)
-            if ((k >> a) & 1) n += sdir[a] * st3[a];
-          if (!((co.flags[n] >> p) & 1)) lin = false;
+  constexpr int U = 2;
+  for (long long c0 = c.i0; c0 < f.ncell; c0 += U * c.st) {
+    T add[U][2], old[U][2];
+    uint8_t fl[U];
+    long long cfs[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      long long cf = c0 + u * c.st;
+      cfs[u] = cf;
+      fl[u] = 0;
+      add[u][0] = add[u][1] = old[u][0] = old[u][1] = T(0);
+      if (cf >= f.ncell) continue;
+      fl[u] = f.flags[cf];
+      if (!(fl[u] & 3)) continue;
+      int I[3];
+      ijk(f, cf, I);
+      int IC[3] = {I[0] >> 1, I[1] >> 1, f.D == 3 ? I[2] >> 1 : 0};
+      int sdir[3];
+      bool inside = true;
+      for (int a = 0; a < 3; ++a) {
+        sdir[a] = (I[a] & 1) ? 1 : -1;
+        if (a < f.D) {
+          int nb = IC[a] + sdir[a];
+          if (nb < 0 || nb >= co.n[a]) inside = false;
         }
-      T v;
-      if (lin) {
-        T acc = T(0);
-        for (int k = 0; k < ncn; ++k) {
-          long long n = C;
-          T w = T(1);
-          for (int a = 0; a < f.D; ++a) {
-            if ((k >> a) & 1) {
-              n += sdir[a] * st3[a];
-              w *= T(0.25);
-            } else {
-              w *= T(0.75);
-            }
-          }
-          acc += w * xc[n];
-        }
-        v = acc;
-      } else {
-        v = xc[C];
       }
-      f.x[p][cf] += v;
+      long long C = (long long)IC[0] + (long long)co.n[0] * ((long long)IC[1] + (long long)co.n[1] * IC[2]);
+      for (int q = 0; q < 2; ++q)
+        if ((fl[u] >> q) & 1) {
+          add[u][q] = prolong_value(f, co, C, sdir, inside, q);
+          old[u][q] = f.x[q][cf];
+        }
     }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      for (int q = 0; q < 2; ++q)
+        if ((fl[u] >> q) & 1) f.x[q][cfs[u]] = old[u][q] + add[u][q];
   }
 }
 
-// one red-black Gauss-Seidel sweep: regular cells of a colour, then the
-// sparse rows of that colour (new values from the current iterate, then written)
+// nu red-black Gauss-Seidel sweeps.  Per colour: the regular cells relax,
+// then the sparse rows of that colour get new values from the current
+// iterate (into tmp) and are written in a second phase: rows of one colour may
+// couple through EB stencils, so none reads a value written in its own phase
+// and the result does not depend on thread timing.
 template <class T>
-__device__ bool ph_smooth(const Op<T>& o, int nu, const Ctx& c) {
+__device__ bool ph_smooth(const Op<T>& o, int nu, const Ctx& c, int l) {
   for (int s = 0; s < nu; ++s)
     for (int colour = 0; colour < 2; ++colour) {
       ph_dense(o, colour, c);
-      if (!c.sync()) return false;
+      if (!c.sync((l << 4) | (colour ? 3 : 1))) return false;
       long long rb = colour == 0 ? 0 : 2 * o.nirr_red, re = colour == 0 ? 2 * o.nirr_red : 2 * o.nirr;
-      if (re > rb) {
-        ph_rows(o, rb, re, 0, c);
-        if (!c.sync()) return false;
-        ph_write(o, rb, re, c);
-        if (!c.sync()) return false;
-      }
+      if (re <= rb) continue;
+      ph_rows(o, rb, re, 0, c);
+      if (!c.sync((l << 4) | 2)) return false;
+      ph_write(o, rb, re, c);
+      if (!c.sync((l << 4) | 4)) return false;
     }
   return true;
 }
 
 template <class T>
-__device__ bool ph_bottom(const Hier<T>& H, const Ctx& c) {
-  const Op<T>& o = H.op[H.nlev - 1];
-  if (H.bm == 0) return ph_smooth(o, H.bsweeps, c);
+__device__ bool ph_bottom(const Hier<T>& H, const Op<T>* ops, const Ctx& c) {
+  const Op<T>& o = ops[H.nlev - 1];
+  if (H.bm == 0) return ph_smooth(o, H.bsweeps, c, H.nlev - 1);
   long long nc = o.ncell;
   for (long long i = c.i0; i < H.bm; i += c.st) {
     int p = (int)(i / nc);
     long long cell = i - p * nc;
     if (!((o.flags[cell] >> p) & 1)) continue;
-    const T* row = H.binv + i * H.bm;
     T acc = T(0);
-    for (int j = 0; j < H.bm; ++j) {
+    for (int j = 0; j < H.bm; ++j) {  // binv is stored transposed: threads read consecutive entries
       int q = j / (int)nc;
       long long cj = j - q * nc;
-      acc += row[j] * o.b[q][cj];
+      acc += H.binv[(long long)j * H.bm + i] * o.b[q][cj];
     }
     o.x[p][cell] = acc;
   }
-  return c.sync();
+  return c.sync(((H.nlev - 1) << 4) | 9);
+}
+
+// levels lc.. inside CTA 0, on the shared-memory copies when H.smem
+template <class T>
+__device__ void coarse_part(const Hier<T>& H, const Op<T>* lop, const Ctx& L) {
+  const int lc = H.lc;
+  if (H.smem) {  // right-hand side of level lc in, correction zero
+    const Op<T>& g = H.op[lc];
+    const Op<T>& s = lop[lc];
+    for (long long c = L.i0; c < g.ncell; c += L.st)
+      for (int p = 0; p < 2; ++p)
+        if (g.b[p]) {
+          s.b[p][c] = g.b[p][c];
+          s.x[p][c] = g.x[p][c];  // zero below the finest level; the iterate itself when lc == 0
+        }
+    __syncthreads();
+  }
+  for (int l = lc; l < H.nlev - 1; ++l) {
+    const Op<T>& o = lop[l];
+    ph_smooth(o, H.nu1, L, l);
+    if (o.nirr) {
+      ph_rows(o, 0, 2 * o.nirr, 1, L);
+      L.sync((l << 4) | 5);
+    }
+    ph_restrict(o, lop[l + 1], L);
+    L.sync((l << 4) | 6);
+  }
+  ph_bottom(H, lop, L);
+  for (int l = H.nlev - 2; l >= lc; --l) {
+    ph_prolong(lop[l], lop[l + 1], L);
+    L.sync((l << 4) | 7);
+    ph_smooth(lop[l], H.nu2, L, l);
+  }
+  if (H.smem) {  // correction of level lc out
+    const Op<T>& g = H.op[lc];
+    const Op<T>& s = lop[lc];
+    for (long long c = L.i0; c < g.ncell; c += L.st)
+      for (int p = 0; p < 2; ++p)
+        if (g.x[p]) g.x[p][c] = s.x[p][c];
+  }
 }
 
 template <class T>
-__device__ bool vcycle_dev(const Hier<T>& H, const Ctx& G, unsigned long long* stamps) {
-  const bool stamp = stamps && blockIdx.x == 0 && threadIdx.x == 0;
-  if (stamp) stamps[0] = now_ns();
+__device__ bool vcycle_dev(const Hier<T>& H, const Op<T>* lop, const Ctx& G) {
   for (int l = 0; l < H.lc; ++l) {
     const Op<T>& o = H.op[l];
-    if (!ph_smooth(o, H.nu1, G)) return false;
+    if (!ph_smooth(o, H.nu1, G, l)) return false;
     if (o.nirr) {
       ph_rows(o, 0, 2 * o.nirr, 1, G);
-      if (!G.sync()) return false;
+      if (!G.sync((l << 4) | 5)) return false;
     }
     ph_restrict(o, H.op[l + 1], G);
-    if (!G.sync()) return false;
+    if (!G.sync((l << 4) | 6)) return false;
   }
-  if (stamp) stamps[1] = now_ns();
   if (blockIdx.x == 0) {
-    Ctx L{(long long)threadIdx.x, (long long)blockDim.x, true, G.B};
-    for (int l = H.lc; l < H.nlev - 1; ++l) {
-      const Op<T>& o = H.op[l];
-      ph_smooth(o, H.nu1, L);
-      if (o.nirr) {
-        ph_rows(o, 0, 2 * o.nirr, 1, L);
-        L.sync();
-      }
-      ph_restrict(o, H.op[l + 1], L);
-      L.sync();
-    }
-    ph_bottom(H, L);
-    for (int l = H.nlev - 2; l >= H.lc; --l) {
-      ph_prolong(H.op[l], H.op[l + 1], L);
-      L.sync();
-      ph_smooth(H.op[l], H.nu2, L);
-    }
+    Ctx L{(long long)threadIdx.x, (long long)blockDim.x, true, G.B, G.epoch, G.tr, G.tn};
+    coarse_part(H, lop, L);
   }
-  if (stamp) stamps[2] = now_ns();
-  if (!G.sync()) return false;
+  if (!G.sync((15 << 4) | 8)) return false;
   for (int l = H.lc - 1; l >= 0; --l) {
     ph_prolong(H.op[l], H.op[l + 1], G);
-    if (!G.sync()) return false;
-    if (!ph_smooth(H.op[l], H.nu2, G)) return false;
+    if (!G.sync((l << 4) | 7)) return false;
+    if (!ph_smooth(H.op[l], H.nu2, G, l)) return false;
   }
-  if (stamp) stamps[3] = now_ns();
   return true;
 }
 
@@ -311,7 +429,7 @@ __device__ bool ph_resid64(const Op<double>& o, const Hier<T>& H, int mixed, uns
                            const Ctx& G) {
   if (o.nirr) {
     ph_rows(o, 0, 2 * o.nirr, 1, G);
-    if (!G.sync()) return false;
+    if (!G.sync((14 << 4) | 10)) return false;
   }
   double mx = 0.0;
   const Op<T>& inner = H.op[0];
@@ -331,7 +449,7 @@ __device__ bool ph_resid64(const Op<double>& o, const Hier<T>& H, int mixed, uns
   }
   for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
   if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(norm, (unsigned long long)__double_as_longlong(mx));
-  return G.sync();
+  return G.sync((14 << 4) | 11);
 }
 
 template <class T>
@@ -350,10 +468,14 @@ __device__ __forceinline__ double load_norm(const unsigned long long* p) {
 
 // The solve: residual, test, (inner V-cycles, update)*, until converged or capped.
 template <class T>
-__global__ void __launch_bounds__(PT) k_solve(const Hier<T>* __restrict__ Hg, const Op<double>* __restrict__ Fg,
+__global__ void __launch_bounds__(PT, 1) k_solve(const Hier<T>* __restrict__ Hg, const Op<double>* __restrict__ Fg,
                                               SolveCtl ctl, Barrier B) {
   __shared__ Hier<T> H;
   __shared__ Op<double> F;
+  __shared__ Op<T> lop[MAXLEV];  // level views used inside CTA 0 (shared-memory data for levels lc..)
+  __shared__ unsigned epoch;
+  __shared__ unsigned tn;
+  extern __shared__ __align__(16) unsigned char dyn[];
   {
     const int* src = (const int*)Hg;
     int* dst = (int*)&H;
@@ -361,9 +483,35 @@ __global__ void __launch_bounds__(PT) k_solve(const Hier<T>* __restrict__ Hg, co
     const int* s2 = (const int*)Fg;
     int* d2 = (int*)&F;
     for (int i = threadIdx.x; i < (int)(sizeof(Op<double>) / sizeof(int)); i += blockDim.x) d2[i] = s2[i];
+    if (threadIdx.x == 0) {
+      epoch = 0u;
+      tn = 0u;
+    }
   }
   __syncthreads();
-  Ctx G{(long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x, false, B};
+  if (blockIdx.x == 0) {
+    if (threadIdx.x < MAXLEV && (int)threadIdx.x < H.nlev) {
+      int l = threadIdx.x;
+      Op<T> v = H.op[l];
+      if (H.smem && l >= H.lc) {
+        for (int p = 0; p < 2; ++p) {
+          v.x[p] = v.x[p] ? (T*)(dyn + H.off_x[l][p]) : nullptr;
+          v.b[p] = v.b[p] ? (T*)(dyn + H.off_b[l][p]) : nullptr;
+        }
+        v.flags = (const uint8_t*)(dyn + H.off_f[l]);
+        v.tmp = (T*)(dyn + H.off_t[l]);
+      }
+      lop[l] = v;
+    }
+    if (H.smem)
+      for (int l = H.lc; l < H.nlev; ++l)
+        for (long long c = threadIdx.x; c < H.op[l].ncell; c += blockDim.x) dyn[H.off_f[l] + c] = H.op[l].flags[c];
+  }
+  __syncthreads();
+  // warps of the grid interleaved over the CTAs: lanes stay on consecutive
+  // elements (coalesced) while consecutive 32-element chunks land on different SMs
+  const long long gi = ((long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
+  Ctx G{gi, (long long)gridDim.x * blockDim.x, false, B, &epoch, nullptr, &tn};
   const double bn = *ctl.bnorm;
   int it = 0, cycles = 0, status = 0;
   double r0 = 0.0, r = 0.0;
@@ -374,13 +522,11 @@ __global__ void __launch_bounds__(PT) k_solve(const Hier<T>* __restrict__ Hg, co
     }
   }
   for (; bn != 0.0;) {
-    if (it == 1 && ctl.stamps && blockIdx.x == 0 && threadIdx.x == 0) ctl.stamps[4] = now_ns();
     if (!ph_resid64(F, H, ctl.mixed, ctl.norms + it, G)) {
       status = 5;
       break;
     }
     r = load_norm(ctl.norms + it);
-    if (it == 1 && ctl.stamps && blockIdx.x == 0 && threadIdx.x == 0) ctl.stamps[5] = now_ns();
     if (it == 0) r0 = r;
     if (r <= ctl.tol * bn) break;
     if (cycles + ctl.inner > ctl.max_cycles || !(r == r) || r > 1e6 * r0) {
@@ -388,10 +534,17 @@ __global__ void __launch_bounds__(PT) k_solve(const Hier<T>* __restrict__ Hg, co
       break;
     }
     bool ok = true;
-    for (int k = 0; k < ctl.inner && ok; ++k) ok = vcycle_dev(H, G, (it == 0 && k == 0) ? ctl.stamps : nullptr);
+    for (int k = 0; k < ctl.inner && ok; ++k) {
+      Ctx Gk = G;
+      if (it == 0 && k == 0 && ctl.trace) {  // trace the first V-cycle
+        Gk.tr = ctl.trace;
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl.trace[1 + tn++] = ((unsigned long long)0xfff << 48) | (now_ns() & 0xffffffffffffULL);
+      }
+      ok = vcycle_dev(H, lop, Gk);
+    }
     if (ok && ctl.mixed) {
       ph_update64(F, H.op[0], G);
-      ok = G.sync();
+      ok = G.sync((14 << 4) | 12);
     }
     if (!ok) {
       status = 5;
@@ -401,6 +554,7 @@ __global__ void __launch_bounds__(PT) k_solve(const Hier<T>* __restrict__ Hg, co
     ++it;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (ctl.trace) ctl.trace[0] = tn;
     ctl.out[0] = status;
     ctl.out[1] = it;
     ctl.out[2] = cycles;
@@ -535,10 +689,12 @@ __global__ void k_gauss_jordan(double* A, double* Ainv, int m, int* status) {
   }
 }
 
+// transpose and convert the bottom inverse (m x m)
 template <class T>
 __global__ void k_convert(const double* a, T* b, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (T)a[i];
+  long long m = (long long)llrint(sqrt((double)n));
+  if (i < n) b[(i % m) * m + i / m] = (T)a[i];
 }
 
 }  // namespace ebp
@@ -546,7 +702,10 @@ __global__ void k_convert(const double* a, T* b, long long n) {
 namespace ebp {
 // barrier microbenchmark: reps grid barriers
 __global__ void __launch_bounds__(PT) k_barrier_bench(Barrier B, int reps) {
+  __shared__ unsigned epoch;
+  if (threadIdx.x == 0) epoch = 0u;
+  __syncthreads();
   for (int i = 0; i < reps; ++i)
-    if (!grid_sync(B)) return;
+    if (!grid_sync(B, &epoch)) return;
 }
 }  // namespace ebp

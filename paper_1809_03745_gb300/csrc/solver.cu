@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -278,6 +279,7 @@ struct eb_poisson {
   unsigned long long* d_stamps = nullptr;  // [8] first-V-cycle timestamps of the last solve
   void* d_binv = nullptr;
   int bm = 0;
+  int smem_bytes = 0;  // dynamic shared memory of the persistent kernel
   std::vector<void*> allocs;
   long long bytes = 0;
 };
@@ -301,6 +303,9 @@ static Op<T> make_op(const DevLevel& L, std::vector<void*>& owner, long long* by
   std::memset(&o, 0, sizeof(o));
   o.D = L.g.D;
   for (int k = 0; k < 3; ++k) o.n[k] = L.g.n[k];
+  o.dn0 = make_fastdiv((unsigned)L.g.n[0]);
+  o.dn1 = make_fastdiv((unsigned)L.g.n[1]);
+  o.dhx = make_fastdiv((unsigned)((L.g.n[0] + 1) / 2));
   o.ncell = L.g.ncell;
   for (int k = 0; k < 6; ++k) o.bc[k] = L.g.bc[k];
   size_t n = (size_t)L.g.ncell;
@@ -345,9 +350,9 @@ static inline void counted(int k = 1) {
 
 template <class T>
 static void smooth(const Op<T>& o, cudaStream_t s) {
-  long long half = o.ncell >> 1;
+  long long work = (o.ncell / o.n[0]) * ((o.n[0] + 1) / 2);
   for (int colour = 0; colour < 2; ++colour) {
-    k_smooth_dense<T><<<blocks(half), 256, 0, s>>>(o, colour);
+    k_smooth_dense<T><<<blocks(work), 256, 0, s>>>(o, colour);
     counted();
     long long rb = colour == 0 ? 0 : 2 * o.nirr_red, re = colour == 0 ? 2 * o.nirr_red : 2 * o.nirr;
     if (re <= rb) continue;
@@ -427,13 +432,46 @@ static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
   H.nu1 = P->o.nu1;
   H.nu2 = P->o.nu2;
   H.bsweeps = P->o.bottom_sweeps;
-  // levels of at most 4096 cells run inside one CTA
+  // levels of at most 4096 cells run inside one CTA, their data in its shared
+  // memory when it fits in SMEM_CAP bytes
+  const int SMEM_CAP = 112 * 1024;
   H.lc = P->nlev - 1;
   for (int l = 0; l < P->nlev; ++l)
     if (ops[l].ncell <= 4096) {
       H.lc = std::min(l, P->nlev - 1);
       break;
     }
+  auto layout = [&](int l0, bool write) {
+    long long off = 0;
+    auto take = [&](long long bytes) {
+      long long o = off;
+      off += (bytes + 15) / 16 * 16;
+      return (int)o;
+    };
+    for (int l = l0; l < P->nlev; ++l) {
+      long long n = ops[l].ncell;
+      for (int p = 0; p < 2; ++p) {
+        int ox = ops[l].x[p] ? take(n * (long long)sizeof(T)) : 0;
+        int ob = ops[l].b[p] ? take(n * (long long)sizeof(T)) : 0;
+        if (write) {
+          H.off_x[l][p] = ox;
+          H.off_b[l][p] = ob;
+        }
+      }
+      int of = take(n);
+      int ot = take(std::max<long long>(2 * ops[l].nirr, 1) * (long long)sizeof(T));
+      if (write) {
+        H.off_f[l] = of;
+        H.off_t[l] = ot;
+      }
+    }
+    return off;
+  };
+  while (H.lc < P->nlev - 1 && layout(H.lc, false) > SMEM_CAP) ++H.lc;
+  long long sb = layout(H.lc, false);
+  H.smem = sb <= SMEM_CAP ? 1 : 0;
+  H.smem_bytes = H.smem ? (int)sb : 0;
+  if (H.smem) layout(H.lc, true);
   for (int l = 0; l < P->nlev; ++l) H.op[l] = ops[l];
   eb_status st = EB_OK;
   // dense inverse of the coarsest operator (FP64 Gauss-Jordan on the device)
@@ -465,6 +503,7 @@ static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
   }
   if (st != EB_OK) return st;
   P->bm = H.bm;
+  P->smem_bytes = H.smem_bytes;
   P->d_hier = dev_alloc(P->allocs, sizeof(Hier<T>), &P->bytes, &st);
   if (st == EB_OK) {
     cudaError_t e = cudaMemcpy(P->d_hier, &H, sizeof(Hier<T>), cudaMemcpyHostToDevice);
@@ -486,21 +525,28 @@ static eb_status setup_persistent(eb_poisson* P) {
   P->d_out = (int*)dev_alloc(P->allocs, 4 * sizeof(int), &P->bytes, &st);
   P->d_norms = (unsigned long long*)dev_alloc(P->allocs, sizeof(unsigned long long) * (P->o.max_cycles + 2),
                                               &P->bytes, &st);
-  P->d_stamps = (unsigned long long*)dev_alloc(P->allocs, sizeof(unsigned long long) * 8, &P->bytes, &st);
-  if (st == EB_OK) cudaMemset(P->d_stamps, 0, sizeof(unsigned long long) * 8);
+  P->d_stamps = (unsigned long long*)dev_alloc(P->allocs, sizeof(unsigned long long) * (TRMAX + 1), &P->bytes, &st);
+  if (st == EB_OK) cudaMemset(P->d_stamps, 0, sizeof(unsigned long long) * (TRMAX + 1));
   if (st != EB_OK) return st;
   cudaError_t e = cudaMemcpy(P->d_fine, &P->op64[0], sizeof(Op<double>), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMallocHost(&P->h_out, 4 * sizeof(int));
   if (e != cudaSuccess) return cuda_fail(e, "persistent setup");
   if (!coop || P->o.launch_mode != 0) return EB_OK;  // per-phase kernels
   int per_sm = 0;
-  e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<float>, PT, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<double>, PT, 0);
+  const void* fn = mixed ? (const void*)k_solve<float> : (const void*)k_solve<double>;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, P->smem_bytes);
+  if (e == cudaSuccess)
+    e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<float>, PT, P->smem_bytes)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<double>, PT, P->smem_bytes);
   if (e != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return EB_OK;
   }
-  P->grid = nsm * std::min(per_sm, 2);
+  // CTAs per SM of the persistent kernel: fewer CTAs make the grid barrier
+  // cheaper, more hide memory latency on the largest levels
+  int want = 1;
+  if (const char* env = std::getenv("EBP_CTAS_PER_SM")) want = std::max(1, std::atoi(env));
+  P->grid = nsm * std::min(per_sm, want);
   P->persistent = true;
   return EB_OK;
 }
@@ -509,6 +555,7 @@ static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cyc
   cudaStream_t s = P->s;
   cudaMemsetAsync(P->d_bar, 0, 4 * sizeof(unsigned), s);
   cudaMemsetAsync(P->d_norms, 0, sizeof(unsigned long long) * (P->o.max_cycles + 2), s);
+  size_t dyn = (size_t)P->smem_bytes;
   SolveCtl ctl;
   ctl.tol = P->o.tol;
   ctl.max_cycles = P->o.max_cycles;
@@ -517,8 +564,8 @@ static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cyc
   ctl.bnorm = (const double*)(P->d_norm + 1);
   ctl.norms = P->d_norms;
   ctl.out = P->d_out;
-  ctl.stamps = P->d_stamps;
-  Barrier B{P->d_bar, P->d_bar + 1, (int*)(P->d_bar + 2)};
+  ctl.trace = P->d_stamps;
+  Barrier B{P->d_bar, (int*)(P->d_bar + 2)};
   void* args[4];
   cudaError_t e;
   if (ctl.mixed) {
@@ -528,7 +575,7 @@ static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cyc
     args[1] = (void*)&F;
     args[2] = (void*)&ctl;
     args[3] = (void*)&B;
-    e = cudaLaunchCooperativeKernel((const void*)k_solve<float>, dim3(P->grid), dim3(PT), args, 0, s);
+    e = cudaLaunchCooperativeKernel((const void*)k_solve<float>, dim3(P->grid), dim3(PT), args, dyn, s);
   } else {
     const Hier<double>* H = (const Hier<double>*)P->d_hier;
     const Op<double>* F = P->d_fine;
@@ -536,19 +583,18 @@ static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cyc
     args[1] = (void*)&F;
     args[2] = (void*)&ctl;
     args[3] = (void*)&B;
-    e = cudaLaunchCooperativeKernel((const void*)k_solve<double>, dim3(P->grid), dim3(PT), args, 0, s);
+    e = cudaLaunchCooperativeKernel((const void*)k_solve<double>, dim3(P->grid), dim3(PT), args, dyn, s);
   }
   counted();
   if (e == cudaSuccess) e = cudaMemcpyAsync(P->h_out, P->d_out, 4 * sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "persistent solve");
   int slot = P->h_out[3];
-  unsigned long long nv = 0, berr = 0;
+  unsigned long long nv = 0;
   e = cudaMemcpy(&nv, P->d_norms + slot, sizeof(nv), cudaMemcpyDeviceToHost);
   unsigned bar[3] = {0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpy(bar, P->d_bar, sizeof(bar), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "persistent readback");
-  (void)berr;
   std::memcpy(r, &nv, sizeof(double));
   *iters = P->h_out[1];
   *cycles = P->h_out[2];
@@ -814,7 +860,7 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
     }
     cudaStream_t s = (cudaStream_t)stream;
     cudaMemsetAsync(P->d_bar, 0, 4 * sizeof(unsigned), s);
-    Barrier B{P->d_bar, P->d_bar + 1, (int*)(P->d_bar + 2)};
+    Barrier B{P->d_bar, (int*)(P->d_bar + 2)};
     void* args[2] = {(void*)&B, (void*)&reps};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -850,8 +896,9 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
   cudaEventCreate(&e1);
   auto launch = [&](int i) {
     if (kernel == 0) {
-      if (mixed) k_smooth_dense<float><<<blocks(n >> 1), 256, 0, s>>>(P->op32[0], i & 1);
-      else k_smooth_dense<double><<<blocks(n >> 1), 256, 0, s>>>(P->op64[0], i & 1);
+      long long w = (n / P->op64[0].n[0]) * ((P->op64[0].n[0] + 1) / 2);
+      if (mixed) k_smooth_dense<float><<<blocks(w), 256, 0, s>>>(P->op32[0], i & 1);
+      else k_smooth_dense<double><<<blocks(w), 256, 0, s>>>(P->op64[0], i & 1);
     } else {
       if (mixed) k_resid_restrict<float><<<blocks(P->op32[1].ncell), 256, 0, s>>>(P->op32[0], P->op32[1]);
       else k_resid_restrict<double><<<blocks(P->op64[1].ncell), 256, 0, s>>>(P->op64[0], P->op64[1]);
@@ -873,19 +920,27 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
   return EB_OK;
 }
 
-extern "C" eb_status eb_poisson_trace(eb_poisson* P, double* ms, int n) {
-  if (!P || !ms || n < 1) {
+extern "C" eb_status eb_poisson_trace(eb_poisson* P, double* out, int n) {
+  if (!P || !out || n < 1) {
     set_error("invalid argument");
     return EB_ERR_INVALID;
   }
-  if (!P->d_stamps) {
+  if (!P->d_stamps || !P->persistent) {
     set_error("no trace on this path");
     return EB_ERR_UNSUPPORTED;
   }
-  unsigned long long t[8];
-  cudaError_t e = cudaMemcpy(t, P->d_stamps, sizeof(t), cudaMemcpyDeviceToHost);
+  std::vector<unsigned long long> t(TRMAX + 1);
+  cudaError_t e = cudaMemcpy(t.data(), P->d_stamps, sizeof(unsigned long long) * (TRMAX + 1), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "trace");
-  double v[4] = {(t[1] - t[0]) * 1e-6, (t[2] - t[1]) * 1e-6, (t[3] - t[2]) * 1e-6, (t[5] - t[4]) * 1e-6};
-  for (int i = 0; i < n && i < 4; ++i) ms[i] = v[i];
+  long long cnt = std::min<long long>((long long)t[0], TRMAX);
+  // entry k > 0: phase that ended at stamp k, duration since stamp k-1
+  int m = 0;
+  for (long long k = 1; k < cnt && 1 + 2 * (m + 1) <= n; ++k) {
+    unsigned long long a = t[k] & 0xffffffffffffULL, b = t[1 + k] & 0xffffffffffffULL;
+    out[1 + 2 * m] = (double)(t[1 + k] >> 48);
+    out[2 + 2 * m] = (double)(b - a) * 1e-6;
+    ++m;
+  }
+  out[0] = m;
   return EB_OK;
 }

@@ -338,10 +338,12 @@ class Poisson:
         return eb_poisson_profile(self._h, kernel, reps, stream)
 
     def trace(self):
-        """ms of the first V-cycle of the last solve: down leg, one-CTA coarse levels, up leg, FP64 residual."""
-        v = (C.c_double * 4)()
-        _check(load().eb_poisson_trace(self._h, v, 4), "eb_poisson_trace")
-        return dict(down=v[0], coarse=v[1], up=v[2], resid64=v[3])
+        """Phases of the first V-cycle of the last solve: list of (level, kind, ms)."""
+        cap = 2 * 4096 + 1
+        v = (C.c_double * cap)()
+        _check(load().eb_poisson_trace(self._h, v, cap), "eb_poisson_trace")
+        m = int(v[0])
+        return [(int(v[1 + 2 * i]) >> 4, int(v[1 + 2 * i]) & 15, v[2 + 2 * i]) for i in range(m)]
 
     def close(self):
         if getattr(self, "_h", None):
