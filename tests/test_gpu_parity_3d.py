@@ -1,0 +1,112 @@
+"""3D GPU parity against the oracle: pin-plane with a dielectric disk, charged
+concentric spheres, a 40^3 grid whose hierarchy ends on an even-odd mix, and a
+128^3 pin-plane checked against the oracle's assembled system."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1809_03745_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1809_03745_gb300 import ebpoisson as E
+
+
+def _concentric(n, sigma=0.7):
+    h = 2.0 / n
+    prims = [(W.PRIM_SPHERE, [0, 0, 0, 0.3]), (W.PRIM_SPHERE, [0, 0, 0, 0.9]), (W.PRIM_SPHERE, [0, 0, 0, 0.6])]
+    nodes = [(0, 0, 0), (0, 1, 0), (3, 1, 0), (1, 0, 2), (0, 2, 0)]
+    d = W._desc(3, (n, n, n), (-1, -1, -1), h, prims, nodes, 3, 4, (1.0, 4.0), [1] * 6, 1.0, [0] * 6,
+                electrodes=[(0, 1.0), (2, 0.0)])
+    return d, np.zeros((2, W.ncells(d))), np.full(W.ncells(d), sigma)
+
+
+def _pin(n, **kw):
+    d = W.pin_plane_3d(n, **kw)
+    x, y, z = W.cell_centres(d)
+    S = np.zeros((2, W.ncells(d)))
+    S[0] = 50.0 * np.exp(-((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.4) ** 2) / (2 * 0.05 ** 2))
+    return d, S, np.zeros(W.ncells(d))
+
+
+CASES = [("pin_disk_32", *_pin(32, radius=0.12)), ("concentric_32_sigma", *_concentric(32)),
+         ("pin_disk_40", *_pin(40, radius=0.1))]
+IDS = [c[0] for c in CASES]
+
+
+@pytest.fixture(scope="module")
+def oracles():
+    return {name: oracle.solve(d, s=S, sigma=sig) for name, d, S, sig in CASES}
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_geometry_parity_3d(case, oracles):
+    name, d, S, sig = case
+    og = oracles[name][0]
+    g = E.Geometry(d)
+    ex = g.export()
+    flags = ex["flags"].cpu().numpy()
+    dofbits = (og.dof[0] >= 0).astype(np.uint8) | ((og.dof[1] >= 0).astype(np.uint8) << 1)
+    assert np.array_equal(flags & 3, dofbits)
+    assert np.abs(ex["kappa"].cpu().numpy() - og.kappa).max() < 1e-13
+    eb = ex["eb_cell"].cpu().numpy()
+    assert np.array_equal(eb, og.eb_cells)
+    assert np.abs(ex["eb_area"].cpu().numpy() - og.eba[eb]).max() < 1e-13
+    assert np.abs(ex["eb_normal"].cpu().numpy() - og.ebn[eb]).max() < 1e-12
+    assert np.abs(ex["eb_centroid"].cpu().numpy() - og.ebx[eb]).max() < 1e-13
+    assert g.info["stencil_order"] == og.stencil_counts
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_operator_residual_parity_3d(case, oracles):
+    name, d, S, sig = case
+    og, _, A, b, data = oracles[name]
+    phi = og.to_cells(np.random.default_rng(4).normal(size=og.ndof))
+    g = E.Geometry(d)
+    P = E.Poisson(g, precision="fp64")
+    r = P.residual(torch.from_numpy(S), torch.from_numpy(sig), torch.from_numpy(phi)).cpu().numpy()
+    ro = og.to_cells(b - A @ og.to_dofs(phi))
+    scale = np.abs(b).max() + np.abs(A).max() * np.abs(phi).max()
+    assert np.abs(r - ro).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_solve_parity_3d(case, precision, oracles):
+    name, d, S, sig = case
+    og, ophi = oracles[name][:2]
+    g = E.Geometry(d)
+    P = E.Poisson(g, precision=precision, tol=1e-12, max_cycles=300)
+    phi, info = P.solve(torch.from_numpy(S), torch.from_numpy(sig))
+    assert info["status"] == 0, info
+    assert np.abs(phi.cpu().numpy() - ophi).max() <= 1e-9 * np.abs(ophi).max(), info
+
+
+@pytest.mark.parametrize("case", CASES[:2], ids=IDS[:2])
+def test_field_parity_3d(case, oracles):
+    name, d, S, sig = case
+    og, ophi, A, b, data = oracles[name]
+    Eo, Eno = og.field(data, og.to_dofs(ophi))
+    g = E.Geometry(d)
+    P = E.Poisson(g, precision="fp64")
+    Eg, Eng = P.field(torch.from_numpy(ophi), torch.from_numpy(sig))
+    scale = np.abs(Eo).max()
+    assert np.abs(Eg.cpu().numpy() - Eo).max() <= 1e-9 * scale
+    assert np.abs(Eng.cpu().numpy() - Eno[og.eb_cells]).max() <= 1e-9 * scale
+
+
+def test_pin_plane_128_solution_satisfies_oracle_system():
+    d, S, sig = _pin(128, radius=0.03)
+    og = oracle.Geometry(d)
+    A, b = og.assemble(og.data(s=S, sigma=sig))
+    g = E.Geometry(d)
+    ex = g.export()
+    dofbits = (og.dof[0] >= 0).astype(np.uint8) | ((og.dof[1] >= 0).astype(np.uint8) << 1)
+    assert np.array_equal(ex["flags"].cpu().numpy() & 3, dofbits)
+    P = E.Poisson(g, precision="mixed", tol=1e-10, max_cycles=300)
+    phi, info = P.solve(torch.from_numpy(S), torch.from_numpy(sig))
+    assert info["status"] == 0 and info["rel_res"] <= 1e-10, info
+    rel = np.abs(b - A @ og.to_dofs(phi.cpu().numpy())).max() / np.abs(b).max()
+    assert rel <= 2e-10, rel
