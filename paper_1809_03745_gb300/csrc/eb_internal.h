@@ -14,6 +14,7 @@ namespace ebp {
 // One multigrid level on the device.
 struct DevLevel {
   Grid g{};
+  int coarse = 0;               // 1 below the finest level
   uint8_t* flags = nullptr;     // [ncell]
   int* cut_of_cell = nullptr;   // [ncell]
   int* irr_of_cell = nullptr;   // [ncell]

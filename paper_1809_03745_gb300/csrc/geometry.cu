@@ -505,6 +505,7 @@ __global__ void k_export_eb(LevelGeom L, const int* eb_q, long long n_eb, const 
 static LevelGeom view(const DevLevel& L) {
   LevelGeom v;
   v.g = L.g;
+  v.coarse = L.coarse;
   v.flags = L.flags;
   v.cut_of_cell = L.cut_of_cell;
   v.R = L.R;
@@ -639,6 +640,7 @@ eb_status build_coarse_geometry(eb_geom* G, int fine, cudaStream_t s, bool* stop
   DevLevel& F = G->L[fine];
   DevLevel C;
   C.g = F.g;
+  C.coarse = 1;
   for (int k = 0; k < F.g.D; ++k) C.g.n[k] = F.g.n[k] / 2;
   C.g.h = F.g.h * 2.0;
   C.g.ncell = (long long)C.g.n[0] * C.g.n[1] * (C.g.D == 3 ? C.g.n[2] : 1);

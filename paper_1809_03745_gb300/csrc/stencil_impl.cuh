@@ -18,6 +18,7 @@ constexpr int MAXE = 192;  // entries of one operator row before the diagonal is
 // Device view of one level's geometry.
 struct LevelGeom {
   Grid g;
+  int coarse;              // 1 on multigrid levels below the finest
   const uint8_t* flags;    // [ncell]
   const int* cut_of_cell;  // [ncell], -1 when not cut
   CutRecords R;
