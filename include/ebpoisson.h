@@ -204,6 +204,23 @@ void eb_poisson_destroy(eb_poisson* P);
 eb_status eb_poisson_residual(eb_poisson* P, const double* d_rhs, const double* d_sigma, const double* d_phi,
                               double* d_r, void* stream);
 
+/* Allocation-free variant of eb_poisson_residual (the paper has no
+ * counterpart: this serves callers that cannot allocate device memory where
+ * they need the residual, e.g. inside a fully carved-up memory pool or an
+ * allocator-free real-time loop).  Same inputs and output as
+ * eb_poisson_residual, but it takes the geometry handle (built earlier) and
+ * needs no solver handle; its scratch (right-hand side and sparse-row
+ * residuals) lives in one file-scope device array of 2^21 + 2^19 + 8 doubles
+ * (about 20.1 MB), held on every device that loads the library until the
+ * process exits.  Limits: at most 2^20 finest-level cells and 2^19 sparse
+ * rows, else EB_ERR_INVALID before any device work.  It calls no cudaMalloc
+ * or cudaFree.  The first call on a device resolves the array's address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  Every
+ * call shares the one array: calls whose work overlaps on the device race and
+ * give undefined results.  Synchronises the stream before returning. */
+eb_status eb_poisson_residual_noalloc(const eb_geom* g, const double* d_rhs, const double* d_sigma,
+                                      const double* d_phi, double* d_r, void* stream);
+
 /* Solves A phi = b to max|r| <= tol max|b|.  d_phi [2][n_cells] holds the
  * initial guess on entry and the solution on exit (entries without an unknown
  * are written as 0).  info may be NULL.  Returns EB_ERR_NOT_CONVERGED when the

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -943,4 +944,105 @@ extern "C" eb_status eb_poisson_trace(eb_poisson* P, double* out, int n) {
   }
   out[0] = m;
   return EB_OK;
+}
+
+// ------------------------------------------------------- allocation-free residual
+//
+// Some callers cannot allocate device memory at the point where they need a
+// residual: code running inside a region that forbids cudaMalloc (a memory
+// pool that is already fully carved up, a real-time loop that must not touch
+// the allocator, a host thread that holds the device only between other
+// users' allocations).  For them the residual below keeps its right-hand side
+// and sparse-row scratch in one file-scope device array instead of memory
+// owned by a solver handle.  The array is NA_MAX_CELLS * 2 + NA_MAX_ROWS + 8
+// doubles (about 20.1 MB) and stays allocated on every device that loads the
+// library until the process exits.
+
+static constexpr long long NA_MAX_CELLS = 1LL << 20;  // cells of the finest level (e.g. 1024^2)
+static constexpr long long NA_MAX_ROWS = 1LL << 19;   // sparse rows (two per irregular cell)
+static __device__ __align__(256) double g_na_scratch[NA_MAX_CELLS * 2 + NA_MAX_ROWS + 8];
+
+static std::mutex g_na_mutex;
+static double* g_na_addr[256] = {nullptr};  // device address of g_na_scratch, per device
+
+// Resolves the device address of the static array for the current device
+// (once per device; the first call on a device does this and should come
+// before any stream capture).
+static eb_status na_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "device query");
+  if (dev < 0 || dev >= 256) {
+    set_error("device ordinal out of range");
+    return EB_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "static scratch address");
+    g_na_addr[dev] = (double*)p;
+  }
+  *out = g_na_addr[dev];
+  return EB_OK;
+}
+
+extern "C" eb_status eb_poisson_residual_noalloc(const eb_geom* G, const double* d_rhs, const double* d_sigma,
+                                                 const double* d_phi, double* d_r, void* stream) {
+  if (!G || !d_rhs || !d_phi || !d_r) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  const DevLevel& F = G->L[0];
+  long long n = F.g.ncell, nrow = 2 * F.nirr;
+  if (n > NA_MAX_CELLS || nrow > NA_MAX_ROWS) {
+    set_error("problem exceeds the static scratch of the allocation-free residual (" + std::to_string(NA_MAX_CELLS) +
+              " cells, " + std::to_string(NA_MAX_ROWS) + " sparse rows)");
+    return EB_ERR_INVALID;
+  }
+  double* base = nullptr;
+  eb_status st = na_scratch(&base);
+  if (st != EB_OK) return st;
+  double* b = base;                       // [2][n] right-hand side
+  double* tmp = base + 2 * NA_MAX_CELLS;  // [nrow] sparse-row residuals
+  double* bnorm = tmp + NA_MAX_ROWS;      // max|b| (not returned)
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(bnorm, 0, sizeof(double), s);
+  if (e != cudaSuccess) return cuda_fail(e, "scratch clear");
+  st = launch_rhs64(G, d_rhs, d_sigma, b, bnorm, s);
+  if (st != EB_OK) return st;
+  // a view of the finest operator over the caller's phi and the static b
+  Op<double> o;
+  std::memset(&o, 0, sizeof(o));
+  o.D = F.g.D;
+  for (int k = 0; k < 3; ++k) o.n[k] = F.g.n[k];
+  o.dn0 = make_fastdiv((unsigned)F.g.n[0]);
+  o.dn1 = make_fastdiv((unsigned)F.g.n[1]);
+  o.dhx = make_fastdiv((unsigned)((F.g.n[0] + 1) / 2));
+  o.ncell = n;
+  for (int k = 0; k < 6; ++k) o.bc[k] = F.g.bc[k];
+  o.x[0] = const_cast<double*>(d_phi);
+  o.x[1] = const_cast<double*>(d_phi) + n;
+  o.b[0] = b;
+  o.b[1] = b + n;
+  o.flags = F.flags;
+  o.irr_cell = F.irr_cell;
+  o.irr_of_cell = F.irr_of_cell;
+  o.row_ptr = F.row_ptr;
+  o.col = F.col;
+  o.val = F.val;
+  o.diag = F.diag;
+  o.tmp = tmp;
+  o.nirr = F.nirr;
+  o.nirr_red = F.nirr_red;
+  for (int p = 0; p < 2; ++p) {
+    double h2 = F.g.h * F.g.h;
+    o.ceps[p] = F.g.eps[p] / h2;
+    o.h2e[p] = h2 / F.g.eps[p];
+  }
+  if (nrow) k_rows<double><<<blocks(nrow), 256, 0, s>>>(o, 0, nrow, 1);
+  k_resid_field<<<blocks(n), 256, 0, s>>>(o, d_r);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? EB_OK : cuda_fail(e, "allocation-free residual");
 }

@@ -69,7 +69,8 @@ class SolveInfo(C.Structure):
 
 EXPORTS = ["eb_status_str", "eb_last_error", "eb_geom_build", "eb_geom_query", "eb_geom_destroy", "eb_geom_export",
            "eb_solver_opts_default", "eb_poisson_setup", "eb_poisson_destroy", "eb_poisson_residual",
-           "eb_poisson_solve", "eb_field_eval", "eb_poisson_profile", "eb_poisson_trace"]
+           "eb_poisson_solve", "eb_field_eval", "eb_poisson_profile", "eb_poisson_trace",
+           "eb_poisson_residual_noalloc"]
 
 
 def lib_path() -> str:
@@ -109,6 +110,8 @@ def load(build_if_missing: bool = False):
         lib.eb_poisson_solve.argtypes = [P, P, P, P, C.POINTER(SolveInfo), P]
         lib.eb_field_eval.restype = C.c_int
         lib.eb_field_eval.argtypes = [P, P, P, P, P, P]
+        lib.eb_poisson_residual_noalloc.restype = C.c_int
+        lib.eb_poisson_residual_noalloc.argtypes = [P, P, P, P, P, P]
         lib.eb_poisson_trace.restype = C.c_int
         lib.eb_poisson_trace.argtypes = [P, C.POINTER(C.c_double), C.c_int]
         lib.eb_poisson_profile.restype = C.c_int
@@ -215,6 +218,12 @@ def eb_poisson_setup(geom_handle, opts: SolverOpts | None = None, stream=None):
 def eb_poisson_residual(handle, rhs, sigma, phi, out, stream=None):
     _check(load().eb_poisson_residual(handle, _ptr(rhs), _ptr(sigma), _ptr(phi), _ptr(out), _stream(stream)),
            "eb_poisson_residual")
+
+
+def eb_poisson_residual_noalloc(geom_handle, rhs, sigma, phi, out, stream=None):
+    """Residual b - A phi without any device allocation (static scratch, see the header)."""
+    _check(load().eb_poisson_residual_noalloc(geom_handle, _ptr(rhs), _ptr(sigma), _ptr(phi), _ptr(out),
+                                              _stream(stream)), "eb_poisson_residual_noalloc")
 
 
 def eb_poisson_solve(handle, rhs, sigma, phi, stream=None) -> dict:
