@@ -228,6 +228,18 @@ eb_status eb_poisson_residual_noalloc(const eb_geom* g, const double* d_rhs, con
 eb_status eb_poisson_solve(eb_poisson* P, const double* d_rhs, const double* d_sigma, double* d_phi,
                            eb_solve_info* info, void* stream);
 
+/* Solves n independent problems (each with its own geometry and solver
+ * handle, all of one precision on one device) in one persistent cooperative
+ * launch: every instance gets a group of CTAs in proportion to its cell
+ * count and runs its own multigrid solve and convergence test with a barrier
+ * of its own, so instances finish independently.  P, d_rhs, d_sigma and d_phi
+ * are host arrays of n entries (d_sigma may be NULL, or hold NULL entries);
+ * infos (n entries) may be NULL.  Each result equals the single solve of the
+ * same instance up to rounding.  Returns the first non-OK instance status. */
+eb_status eb_poisson_solve_batched(eb_poisson* const* P, int n, const double* const* d_rhs,
+                                   const double* const* d_sigma, double* const* d_phi, eb_solve_info* infos,
+                                   void* stream);
+
 /* E = -grad phi (Sec. 2.1) at cell centres per phase, d_E [D][2][n_cells]:
  * centred differences where both face neighbours carry an unknown of the
  * phase across an open face, one-sided where one does, else the EB normal

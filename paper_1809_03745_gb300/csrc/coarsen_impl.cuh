@@ -11,6 +11,7 @@ namespace ebp {
 // reasons for stopping the coarsening (ORed with ST_STOP)
 constexpr int STOP_TWO_KINDS = 8;     // electrode and dielectric interface in one coarse cell
 constexpr int STOP_PHASES = 16;       // both phases without a dielectric interface
+constexpr int STOP_THIN = 32;         // a feature thinner than the coarse cell (EB areas cancel)
 
 // 0 covered, 1 regular gas, 2 regular dielectric, 3 cut
 EBP_HD uint8_t coarse_preclass(const LevelGeom& F, const Grid& gc, long long C) {
@@ -120,6 +121,10 @@ EBP_HDN int coarse_cut_geometry(const LevelGeom& F, const Grid& gc, const CutRec
     len2 += vec[a] * vec[a];
   }
   double ar = sqrt(len2);
+  // children's EB pieces facing opposite ways (both sides of a feature thinner
+  // than this cell) cancel in the coarse normal: the coarse level cannot
+  // represent the feature, so coarsening stops here
+  if (kind != EBK_NONE && ar * (double)(1 << (D - 1)) < 0.5 * wsum) return ST_STOP | STOP_THIN;
   if (kind != EBK_NONE && ar > 0.0 && wsum > 0.0) {
     Rc.ebk[q] = kind;
     Rc.eba[q] = ar;

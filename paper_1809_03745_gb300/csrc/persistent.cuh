@@ -44,6 +44,7 @@ struct SolveCtl {
   unsigned long long* norms;  // [max_cycles + 2] per-iteration residual max, zeroed by the host
   int* out;                   // [0] status, [1] outer iterations, [2] V-cycles, [3] norm slot of the final residual
   unsigned long long* trace;  // [1 + TRMAX]: count, then (code << 48 | ns) per phase of the first V-cycle
+  int max_iters;              // outer iterations allowed in this launch (0: no limit); status 7 when reached
 };
 
 __device__ __forceinline__ unsigned long long now_ns() {
@@ -65,12 +66,12 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // waits until it reaches (barriers passed) x (CTAs).  The wait is bounded by
 // the SM clock: on expiry the error word is set and every CTA falls through
 // (returns false) at this and every later barrier.
-__device__ __forceinline__ bool grid_sync(const Barrier& B, unsigned* epoch) {
+__device__ __forceinline__ bool grid_sync(const Barrier& B, unsigned* epoch, int gsize) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile int* ve = B.err;
     if (*ve == 0) {
-      unsigned target = (*epoch + 1u) * gridDim.x;
+      unsigned target = (*epoch + 1u) * (unsigned)gsize;
       *epoch += 1u;
       __threadfence();
       red_release_add(B.count, 1u);
@@ -98,14 +99,15 @@ struct Ctx {
   bool local;
   Barrier B;
   unsigned* epoch;         // shared-memory barrier count of this CTA
-  unsigned long long* tr;  // phase trace (CTA 0, first V-cycle) or null
+  unsigned long long* tr;  // phase trace (CTA 0 of the group, first V-cycle) or null
   unsigned* tn;            // shared-memory trace length
+  int gcta, gsize;         // this CTA's index in its group and the group's CTA count
   // barrier ending a phase; `code` = (level << 4) | kind names the phase for the trace
   __device__ __forceinline__ bool sync(int code) const {
     bool ok = true;
     if (local) __syncthreads();
-    else ok = grid_sync(B, epoch);
-    if (tr && blockIdx.x == 0 && threadIdx.x == 0 && *tn < TRMAX) {
+    else ok = grid_sync(B, epoch, gsize);
+    if (tr && gcta == 0 && threadIdx.x == 0 && *tn < TRMAX) {
       tr[1 + *tn] = ((unsigned long long)code << 48) | (now_ns() & 0xffffffffffffULL);
       *tn += 1;
     }
@@ -186,8 +188,8 @@ __device__ __forceinline__ void ph_rows(const Op<T>& o, long long rb, long long 
     return;
   }
   const int lane = threadIdx.x & 31;
-  const long long w0 = c.local ? (threadIdx.x >> 5) : (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-  const long long ws = c.local ? (blockDim.x >> 5) : (long long)gridDim.x * (blockDim.x >> 5);
+  const long long w0 = c.local ? (threadIdx.x >> 5) : (long long)(threadIdx.x >> 5) * c.gsize + c.gcta;
+  const long long ws = c.local ? (blockDim.x >> 5) : (long long)c.gsize * (blockDim.x >> 5);
   for (long long r = rb + w0; r < re; r += ws) {
     double d = o.diag[r];
     if (d == 0.0) continue;
@@ -409,8 +411,8 @@ __device__ bool vcycle_dev(const Hier<T>& H, const Op<T>* lop, const Ctx& G) {
     ph_restrict(o, H.op[l + 1], G);
     if (!G.sync((l << 4) | 6)) return false;
   }
-  if (blockIdx.x == 0) {
-    Ctx L{(long long)threadIdx.x, (long long)blockDim.x, true, G.B, G.epoch, G.tr, G.tn};
+  if (G.gcta == 0) {
+    Ctx L{(long long)threadIdx.x, (long long)blockDim.x, true, G.B, G.epoch, G.tr, G.tn, 0, 1};
     coarse_part(H, lop, L);
   }
   if (!G.sync((15 << 4) | 8)) return false;
@@ -468,8 +470,8 @@ __device__ __forceinline__ double load_norm(const unsigned long long* p) {
 
 // The solve: residual, test, (inner V-cycles, update)*, until converged or capped.
 template <class T>
-__global__ void __launch_bounds__(PT, 1) k_solve(const Hier<T>* __restrict__ Hg, const Op<double>* __restrict__ Fg,
-                                              SolveCtl ctl, Barrier B) {
+__device__ __forceinline__ void solve_group(const Hier<T>* __restrict__ Hg, const Op<double>* __restrict__ Fg,
+                                            const SolveCtl& ctl, const Barrier& B, int gcta, int gsize) {
   __shared__ Hier<T> H;
   __shared__ Op<double> F;
   __shared__ Op<T> lop[MAXLEV];  // level views used inside CTA 0 (shared-memory data for levels lc..)
@@ -489,7 +491,7 @@ __global__ void __launch_bounds__(PT, 1) k_solve(const Hier<T>* __restrict__ Hg,
     }
   }
   __syncthreads();
-  if (blockIdx.x == 0) {
+  if (gcta == 0) {
     if (threadIdx.x < MAXLEV && (int)threadIdx.x < H.nlev) {
       int l = threadIdx.x;
       Op<T> v = H.op[l];
@@ -510,8 +512,8 @@ __global__ void __launch_bounds__(PT, 1) k_solve(const Hier<T>* __restrict__ Hg,
   __syncthreads();
   // warps of the grid interleaved over the CTAs: lanes stay on consecutive
   // elements (coalesced) while consecutive 32-element chunks land on different SMs
-  const long long gi = ((long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
-  Ctx G{gi, (long long)gridDim.x * blockDim.x, false, B, &epoch, nullptr, &tn};
+  const long long gi = ((long long)(threadIdx.x >> 5) * gsize + gcta) * 32 + (threadIdx.x & 31);
+  Ctx G{gi, (long long)gsize * blockDim.x, false, B, &epoch, nullptr, &tn, gcta, gsize};
   const double bn = *ctl.bnorm;
   int it = 0, cycles = 0, status = 0;
   double r0 = 0.0, r = 0.0;
@@ -533,12 +535,16 @@ __global__ void __launch_bounds__(PT, 1) k_solve(const Hier<T>* __restrict__ Hg,
       status = 3;
       break;
     }
+    if (ctl.max_iters && it >= ctl.max_iters) {  // resumable: stop at a V-cycle boundary
+      status = 7;
+      break;
+    }
     bool ok = true;
     for (int k = 0; k < ctl.inner && ok; ++k) {
       Ctx Gk = G;
       if (it == 0 && k == 0 && ctl.trace) {  // trace the first V-cycle
         Gk.tr = ctl.trace;
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctl.trace[1 + tn++] = ((unsigned long long)0xfff << 48) | (now_ns() & 0xffffffffffffULL);
+        if (gcta == 0 && threadIdx.x == 0) ctl.trace[1 + tn++] = ((unsigned long long)0xfff << 48) | (now_ns() & 0xffffffffffffULL);
       }
       ok = vcycle_dev(H, lop, Gk);
     }
@@ -553,13 +559,40 @@ __global__ void __launch_bounds__(PT, 1) k_solve(const Hier<T>* __restrict__ Hg,
     cycles += ctl.inner;
     ++it;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (gcta == 0 && threadIdx.x == 0) {
     if (ctl.trace) ctl.trace[0] = tn;
+    ctl.norms[ctl.max_cycles + 1] = (unsigned long long)__double_as_longlong(r);  // final residual max
     ctl.out[0] = status;
     ctl.out[1] = it;
     ctl.out[2] = cycles;
     ctl.out[3] = it;
   }
+}
+
+template <class T>
+__global__ void __launch_bounds__(PT, 1) k_solve(const Hier<T>* __restrict__ Hg, const Op<double>* __restrict__ Fg,
+                                                 SolveCtl ctl, Barrier B) {
+  solve_group(Hg, Fg, ctl, B, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// one instance of a batched solve: its hierarchy, fine operator, controls,
+// barrier and the block of CTAs [start, start + size) that works on it
+template <class T>
+struct BatchItem {
+  const Hier<T>* H;
+  const Op<double>* F;
+  SolveCtl ctl;
+  Barrier B;
+  int start, size;
+};
+
+// Many independent solves in one cooperative launch: each CTA finds its
+// instance and runs the solve with the instance's own group barrier.
+template <class T>
+__global__ void __launch_bounds__(PT, 1) k_solve_batch(const BatchItem<T>* __restrict__ items,
+                                                       const int* __restrict__ cta_item) {
+  const BatchItem<T>& it = items[cta_item[blockIdx.x]];
+  solve_group(it.H, it.F, it.ctl, it.B, (int)blockIdx.x - it.start, it.size);
 }
 
 // ------------------------------------------------------------ bottom inverse
@@ -706,6 +739,6 @@ __global__ void __launch_bounds__(PT) k_barrier_bench(Barrier B, int reps) {
   if (threadIdx.x == 0) epoch = 0u;
   __syncthreads();
   for (int i = 0; i < reps; ++i)
-    if (!grid_sync(B, &epoch)) return;
+    if (!grid_sync(B, &epoch, (int)gridDim.x)) return;
 }
 }  // namespace ebp

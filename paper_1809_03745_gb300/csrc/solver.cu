@@ -533,9 +533,16 @@ static eb_status setup_persistent(eb_poisson* P) {
   if (e == cudaSuccess) e = cudaMallocHost(&P->h_out, 4 * sizeof(int));
   if (e != cudaSuccess) return cuda_fail(e, "persistent setup");
   if (!coop || P->o.launch_mode != 0) return EB_OK;  // per-phase kernels
-  int per_sm = 0;
+  int per_sm = 0, smax = 0;
   const void* fn = mixed ? (const void*)k_solve<float> : (const void*)k_solve<double>;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, P->smem_bytes);
+  // the attribute is per kernel, shared by every handle: allow the device maximum once
+  cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  smax -= 16 * 1024;  // headroom for the kernel's static shared memory
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  if (e == cudaSuccess) {
+    const void* fb = mixed ? (const void*)k_solve_batch<float> : (const void*)k_solve_batch<double>;
+    e = cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  }
   if (e == cudaSuccess)
     e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<float>, PT, P->smem_bytes)
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<double>, PT, P->smem_bytes);
@@ -566,6 +573,7 @@ static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cyc
   ctl.norms = P->d_norms;
   ctl.out = P->d_out;
   ctl.trace = P->d_stamps;
+  ctl.max_iters = 0;
   Barrier B{P->d_bar, (int*)(P->d_bar + 2)};
   void* args[4];
   cudaError_t e;
@@ -590,9 +598,8 @@ static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cyc
   if (e == cudaSuccess) e = cudaMemcpyAsync(P->h_out, P->d_out, 4 * sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "persistent solve");
-  int slot = P->h_out[3];
   unsigned long long nv = 0;
-  e = cudaMemcpy(&nv, P->d_norms + slot, sizeof(nv), cudaMemcpyDeviceToHost);
+  e = cudaMemcpy(&nv, P->d_norms + P->o.max_cycles + 1, sizeof(nv), cudaMemcpyDeviceToHost);
   unsigned bar[3] = {0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpy(bar, P->d_bar, sizeof(bar), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "persistent readback");
@@ -836,6 +843,190 @@ extern "C" eb_status eb_poisson_solve(eb_poisson* P, const double* d_rhs, const 
   inf.rel_res = b > 0.0 ? r / b : 0.0;
   if (info) *info = inf;
   return st;
+}
+
+
+// ------------------------------------------------------------------ batches
+
+// CTAs per instance for a batch on `total` CTAs: one each, the rest in
+// proportion to the instances' cell counts (largest remainders), at most
+// `cap` per instance.
+static std::vector<int> split_ctas(const std::vector<long long>& cells, int total, int cap) {
+  int n = (int)cells.size();
+  std::vector<int> size(n, 1);
+  long long sum = 0;
+  for (long long c : cells) sum += c;
+  int left = total - n;
+  if (left <= 0 || sum <= 0) return size;
+  std::vector<std::pair<double, int>> rem;
+  int given = 0;
+  for (int i = 0; i < n; ++i) {
+    double share = (double)left * (double)cells[i] / (double)sum;
+    int whole = std::min((int)share, cap - 1);
+    size[i] += whole;
+    given += whole;
+    rem.push_back({share - whole, i});
+  }
+  std::sort(rem.begin(), rem.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+    return a.first > b.first || (a.first == b.first && a.second < b.second);
+  });
+  for (int k = 0; k < (int)rem.size() && given < left; ++k) {
+    int i = rem[k].second;
+    if (size[i] < cap) {
+      ++size[i];
+      ++given;
+    }
+  }
+  return size;
+}
+
+template <class T>
+static eb_status launch_batch_t(eb_poisson* const* P, int n, int max_iters, int grid_total, int smem, cudaStream_t s) {
+  std::vector<long long> cells(n);
+  for (int i = 0; i < n; ++i) cells[i] = P[i]->G->L[0].g.ncell;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P[0]->G->device);
+  std::vector<int> size = split_ctas(cells, grid_total, std::max(1, nsm));
+  std::vector<BatchItem<T>> items(n);
+  std::vector<int> cta_item;
+  int start = 0;
+  for (int i = 0; i < n; ++i) {
+    eb_poisson* Q = P[i];
+    BatchItem<T>& it = items[i];
+    it.H = (const Hier<T>*)Q->d_hier;
+    it.F = Q->d_fine;
+    SolveCtl& c = it.ctl;
+    c.tol = Q->o.tol;
+    c.max_cycles = Q->o.max_cycles;
+    c.mixed = Q->o.precision == EB_PREC_MIXED;
+    c.inner = c.mixed ? Q->o.inner_cycles : 1;
+    c.bnorm = (const double*)(Q->d_norm + 1);
+    c.norms = Q->d_norms;
+    c.out = Q->d_out;
+    c.trace = Q->d_stamps;
+    c.max_iters = max_iters;
+    it.B = Barrier{Q->d_bar, (int*)(Q->d_bar + 2)};
+    it.start = start;
+    it.size = size[i];
+    for (int k = 0; k < size[i]; ++k) cta_item.push_back(i);
+    start += size[i];
+    cudaMemsetAsync(Q->d_bar, 0, 4 * sizeof(unsigned), s);
+    cudaMemsetAsync(Q->d_norms, 0, sizeof(unsigned long long) * (Q->o.max_cycles + 2), s);
+  }
+  BatchItem<T>* d_items = nullptr;
+  int* d_cta = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&d_items, sizeof(BatchItem<T>) * n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_cta, sizeof(int) * cta_item.size(), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, items.data(), sizeof(BatchItem<T>) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_cta, cta_item.data(), sizeof(int) * cta_item.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    void* args[2] = {(void*)&d_items, (void*)&d_cta};
+    e = cudaLaunchCooperativeKernel((const void*)k_solve_batch<T>, dim3(start), dim3(PT), args, (size_t)smem, s);
+    counted();
+  }
+  if (d_items) cudaFreeAsync(d_items, s);
+  if (d_cta) cudaFreeAsync(d_cta, s);
+  // the host vectors must outlive the copies above
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
+  return e == cudaSuccess ? EB_OK : cuda_fail(e, "batched solve");
+}
+
+// One cooperative launch over instances that share precision and device.
+// fresh: assemble b and copy the guess in first; max_iters: outer iterations
+// allowed (0: until convergence).  Results (status, iterations, V-cycles,
+// residual) are read into each handle's pinned h_out / h_norm.
+eb_status batch_step(eb_poisson* const* P, int n, const double* const* rhs, const double* const* sigma,
+                     double* const* phi, bool fresh, bool copy_out, int max_iters, cudaStream_t s) {
+  if (n < 1) return EB_OK;
+  bool mixed = P[0]->o.precision == EB_PREC_MIXED;
+  int smem = 0;
+  for (int i = 0; i < n; ++i) {
+    if ((P[i]->o.precision == EB_PREC_MIXED) != mixed || !P[i]->persistent || P[i]->G->device != P[0]->G->device) {
+      set_error("a batch needs persistent solvers of one precision on one device");
+      return EB_ERR_INVALID;
+    }
+    smem = std::max(smem, P[i]->smem_bytes);
+  }
+  int nsm = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P[0]->G->device);
+  cudaError_t e = cudaSuccess;
+  e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch<float>, PT, smem)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch<double>, PT, smem);
+  if (e != cudaSuccess || per_sm < 1) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e, "batch occupancy");
+  int total = nsm * std::min(per_sm, 1);
+  if (fresh)
+    for (int i = 0; i < n; ++i) {
+      const DevLevel& F = P[i]->G->L[0];
+      cudaMemsetAsync(P[i]->d_norm + 1, 0, sizeof(unsigned long long), s);
+      eb_status st = launch_rhs64(P[i]->G, rhs[i], sigma ? sigma[i] : nullptr, P[i]->b64, (double*)(P[i]->d_norm + 1), s);
+      if (st != EB_OK) return st;
+      k_copy_masked<<<blocks(F.g.ncell), 256, 0, s>>>(F.flags, F.g.ncell, phi[i], P[i]->phi64);
+      counted(2);
+    }
+  // at most `total` instances per launch
+  for (int b0 = 0; b0 < n; b0 += total) {
+    int m = std::min(total, n - b0);
+    eb_status st = mixed ? launch_batch_t<float>(P + b0, m, max_iters, total, smem, s)
+                         : launch_batch_t<double>(P + b0, m, max_iters, total, smem, s);
+    if (st != EB_OK) return st;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (copy_out) {
+      const DevLevel& F = P[i]->G->L[0];
+      k_copy_masked<<<blocks(F.g.ncell), 256, 0, s>>>(F.flags, F.g.ncell, P[i]->phi64, phi[i]);
+      counted();
+    }
+    cudaMemcpyAsync(P[i]->h_out, P[i]->d_out, 4 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(P[i]->h_norm, P[i]->d_norms + P[i]->o.max_cycles + 1, sizeof(unsigned long long),
+                    cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(P[i]->h_norm + 1, P[i]->d_norm + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? EB_OK : cuda_fail(e, "batched solve");
+}
+
+static void batch_info(eb_poisson* Q, eb_solve_info* inf) {
+  std::memset(inf, 0, sizeof(*inf));
+  double r = as_double(Q->h_norm[0]), b = as_double(Q->h_norm[1]);
+  inf->status = Q->h_out[0];
+  inf->outer_iters = Q->h_out[1];
+  inf->vcycles = Q->h_out[2];
+  inf->bnorm = b;
+  inf->rel_res = b > 0.0 ? r / b : 0.0;
+}
+
+extern "C" eb_status eb_poisson_solve_batched(eb_poisson* const* P, int n, const double* const* d_rhs,
+                                              const double* const* d_sigma, double* const* d_phi,
+                                              eb_solve_info* infos, void* stream) {
+  if (!P || n < 0 || (n && (!d_rhs || !d_phi))) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  for (int i = 0; i < n; ++i)
+    if (!P[i] || !d_rhs[i] || !d_phi[i]) {
+      set_error("null instance");
+      return EB_ERR_INVALID;
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  long long launches = 0;
+  g_count = &launches;
+  eb_status st = batch_step(P, n, d_rhs, d_sigma, d_phi, true, true, 0, s);
+  g_count = nullptr;
+  if (st != EB_OK) return st;
+  eb_status worst = EB_OK;
+  for (int i = 0; i < n; ++i) {
+    eb_solve_info inf;
+    batch_info(P[i], &inf);
+    inf.kernel_launches = launches;
+    if (infos) infos[i] = inf;
+    if (inf.status != EB_OK && worst == EB_OK) worst = (eb_status)inf.status;
+  }
+  if (worst == EB_ERR_NOT_CONVERGED) set_error("an instance reached its cycle cap");
+  if (worst == EB_ERR_TIMEOUT) set_error("a grid barrier wait gave up");
+  return worst;
 }
 
 extern "C" eb_status eb_field_eval(eb_poisson* P, const double* d_phi, const double* d_sigma, double* d_E,

@@ -70,7 +70,7 @@ class SolveInfo(C.Structure):
 EXPORTS = ["eb_status_str", "eb_last_error", "eb_geom_build", "eb_geom_query", "eb_geom_destroy", "eb_geom_export",
            "eb_solver_opts_default", "eb_poisson_setup", "eb_poisson_destroy", "eb_poisson_residual",
            "eb_poisson_solve", "eb_field_eval", "eb_poisson_profile", "eb_poisson_trace",
-           "eb_poisson_residual_noalloc"]
+           "eb_poisson_residual_noalloc", "eb_poisson_solve_batched"]
 
 
 def lib_path() -> str:
@@ -110,6 +110,8 @@ def load(build_if_missing: bool = False):
         lib.eb_poisson_solve.argtypes = [P, P, P, P, C.POINTER(SolveInfo), P]
         lib.eb_field_eval.restype = C.c_int
         lib.eb_field_eval.argtypes = [P, P, P, P, P, P]
+        lib.eb_poisson_solve_batched.restype = C.c_int
+        lib.eb_poisson_solve_batched.argtypes = [P, C.c_int, P, P, P, C.POINTER(SolveInfo), P]
         lib.eb_poisson_residual_noalloc.restype = C.c_int
         lib.eb_poisson_residual_noalloc.argtypes = [P, P, P, P, P, P]
         lib.eb_poisson_trace.restype = C.c_int
@@ -242,6 +244,25 @@ def eb_poisson_profile(handle, kernel: int, reps: int, stream=None):
     return ms.value, by.value
 
 
+def _info_dict(info):
+    return dict(status=info.status, outer_iters=info.outer_iters, vcycles=info.vcycles, rel_res=info.rel_res,
+                bnorm=info.bnorm, kernel_launches=info.kernel_launches)
+
+
+def eb_poisson_solve_batched(handles, rhs, sigma, phi, stream=None) -> list:
+    """n independent solves in one persistent launch; lists of handles and device tensors."""
+    n = len(handles)
+    arr = lambda xs: (C.c_void_p * max(n, 1))(*[(x.value if isinstance(x, C.c_void_p) else  # noqa: E731
+                                                  (x.data_ptr() if x is not None else 0)) for x in xs])
+    hs, rs, ss, ps = arr(handles), arr(rhs), arr(sigma if sigma is not None else [None] * n), arr(phi)
+    infos = (SolveInfo * max(n, 1))()
+    st = load().eb_poisson_solve_batched(C.cast(hs, C.c_void_p), n, C.cast(rs, C.c_void_p), C.cast(ss, C.c_void_p),
+                                         C.cast(ps, C.c_void_p), infos, _stream(stream))
+    if st not in (EB_OK, EB_ERR_NOT_CONVERGED):
+        _check(st, "eb_poisson_solve_batched")
+    return [_info_dict(infos[i]) for i in range(n)]
+
+
 def eb_field_eval(handle, phi, sigma, E, En, stream=None):
     _check(load().eb_field_eval(handle, _ptr(phi), _ptr(sigma), _ptr(E), _ptr(En), _stream(stream)),
            "eb_field_eval")
@@ -291,6 +312,19 @@ class Geometry:
             self.close()
         except Exception:
             pass
+
+
+def solve_batched(solvers, rhs, sigma=None, phi=None, stream=None):
+    """Batched solve over Poisson objects; returns (phis, infos)."""
+    rhs_d, sig_d, phis = [], [], []
+    for k, P in enumerate(solvers):
+        r, s = P._fields(rhs[k], None if sigma is None else sigma[k])
+        rhs_d.append(r)
+        sig_d.append(s)
+        phis.append(torch.zeros(2, P.geom.ncell, dtype=torch.float64, device=P.geom.device) if phi is None
+                    else phi[k])
+    infos = eb_poisson_solve_batched([P._h for P in solvers], rhs_d, sig_d, phis, stream)
+    return phis, infos
 
 
 class Poisson:

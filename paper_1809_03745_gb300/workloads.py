@@ -193,8 +193,9 @@ def batched_instances(count=64, seed=SEED_BASE + 4, *, n2=(64, 1024), n3=(32, 19
     """Independent solves with seeded geometry and sizes: 2D or 3D by a
     Bernoulli draw, n log-uniform in the given range rounded to a multiple of
     16, tip radius U[0.01, 0.05] clamped to >= 3h, gap U[0.3, 0.7], eps_r
-    U[2, 8], voltage U[0.5, 2] and a Gaussian blob of peak log-U[10, 1e3]
-    0.05 below the apex."""
+    U[2, 8] for a dielectric slab (2D, thickness 0.1) or disk (3D, radius 0.3,
+    thickness 0.05), each kept at least three cells thick, voltage U[0.5, 2]
+    and a Gaussian blob of peak log-U[10, 1e3] 0.05 below the apex."""
     root = np.random.SeedSequence(seed)
     out = []
     for child in root.spawn(count):
@@ -213,12 +214,13 @@ def batched_instances(count=64, seed=SEED_BASE + 4, *, n2=(64, 1024), n3=(32, 19
         V = rng.uniform(0.5, 2.0)
         peak = math.exp(rng.uniform(math.log(10.0), math.log(1e3)))
         if is3d:
+            # a disk at least three cells thick, its top off the node planes
             desc = pin_plane_3d(n, tip_z=gap, radius=tip_r, V=V, eps_d=eps_d,
-                                disk_t=min(0.05, gap - 10 * h) + 0.3 * h)
+                                disk_t=max(min(0.05, gap - 10 * h), 3 * h) + 0.3 * h)
             x, y, z = cell_centres(desc)
             s = peak * np.exp(-((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - (gap - 0.05)) ** 2) / (2 * 0.03 ** 2))
         else:
-            slab = min(0.1, gap - 10 * h) + 0.3 * h  # keep the flat slab top off the node rows
+            slab = max(min(0.1, gap - 10 * h), 3 * h) + 0.3 * h  # >= 3 cells, top off the node rows
             desc = rod_plane_2d(n, dielectric=True, tip_y=gap, half_width=tip_r, V=V, eps_d=eps_d, slab_y=slab,
                                 rough_amp=0.0)
             x, y, _ = cell_centres(desc)
