@@ -183,6 +183,8 @@ typedef struct {
   double rel_res;   /* final max|r| / max|b| in FP64 */
   double bnorm;     /* max|b| */
   long long kernel_launches; /* kernels this call launched (graph nodes counted per replay) */
+  double kernel_ms; /* device time of the persistent solve kernel(s) of this call, from CUDA
+                       events on the stream they ran on; 0 on the multi-launch paths */
 } eb_solve_info;
 
 typedef struct eb_poisson eb_poisson;
@@ -253,8 +255,9 @@ eb_status eb_field_eval(eb_poisson* P, const double* d_phi, const double* d_sigm
  * finest multigrid level `reps` times on `stream` between CUDA events and
  * reports the mean duration per launch and the algorithmic bytes one launch
  * must move.  It relaxes the solver's own work arrays (left as the last solve
- * left them); the caller's fields are not touched.  kernel 0: one colour of
- * the red-black Gauss-Seidel sweep of the inner-precision finest level
+ * left them); the caller's fields are not touched.  Both run the persistent
+ * solve kernel's own phase code in its grid shape.  kernel 0: one colour of
+ * the red-black Gauss-Seidel sweep (regular cells) of the inner-precision finest level
  * (bytes: half of read x, read b, write x, read flags per cell); kernel 1: the
  * fused residual + restriction of that level (read x, b, flags per fine cell,
  * write coarse b and x). */

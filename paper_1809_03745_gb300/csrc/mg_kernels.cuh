@@ -32,6 +32,7 @@ __device__ __forceinline__ unsigned fdiv(unsigned x, const FastDiv& f) {
 template <class T>
 struct Op {
   FastDiv dn0, dn1, dhx;  // n[0], n[1] and the cells of one colour per x row, (n[0] + 1) / 2
+  FastDiv dq;             // groups of four cells per x row, n[0] / 4 (used when n[0] % 4 == 0)
   int D;
   int n[3];
   long long ncell;

@@ -120,7 +120,7 @@ struct Ctx {
 // U cells a grid stride apart and issues all their loads before any store, so
 // that many loads are in flight per thread (the phase is latency bound).
 template <class T>
-__device__ __forceinline__ void ph_dense(const Op<T>& o, int colour, const Ctx& c) {
+__device__ __forceinline__ void ph_dense_scalar(const Op<T>& o, int colour, const Ctx& c) {
   constexpr int U = 4;
   int hx = (o.n[0] + 1) >> 1;  // cells of one colour per x row (either parity of n0)
   long long work = (o.ncell / o.n[0]) * hx;
@@ -168,6 +168,201 @@ __device__ __forceinline__ void ph_dense(const Op<T>& o, int colour, const Ctx& 
     for (int u = 0; u < U; ++u)
       if (act[u]) o.x[pp[u]][cc[u]] = val[u];
   }
+}
+
+template <class T>
+__device__ __forceinline__ void ld4(const T* p, T v[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  } else {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+  }
+}
+
+// Relaxed value of the cell at position E (0..3) of a group of four x cells,
+// from the group's loaded rows; the same terms in the same order as
+// reg_stencil, so the result is bitwise that of the scalar path.
+template <class T, int E>
+__device__ __forceinline__ T relax4(const Op<T>& o, int p, int i, int j, int k, const T xc[4], T xl, T xr,
+                                    const T ym[4], const T yp[4], const T zm[4], const T zp[4], const T bv[4]) {
+  const T third = T(1) / T(3);
+  T sum = T(0);
+  int dg = 0;
+  if (i > 0) {
+    sum += E > 0 ? xc[E > 0 ? E - 1 : 0] : xl;
+    dg += 1;
+  } else if (o.bc[0]) {
+    sum += xc[E < 3 ? E + 1 : 3] * third;
+    dg += 3;
+  }
+  if (i < o.n[0] - 1) {
+    sum += E < 3 ? xc[E < 3 ? E + 1 : 3] : xr;
+    dg += 1;
+  } else if (o.bc[1]) {
+    sum += xc[E > 0 ? E - 1 : 0] * third;
+    dg += 3;
+  }
+  if (j > 0) {
+    sum += ym[E];
+    dg += 1;
+  } else if (o.bc[2]) {
+    sum += yp[E] * third;
+    dg += 3;
+  }
+  if (j < o.n[1] - 1) {
+    sum += yp[E];
+    dg += 1;
+  } else if (o.bc[3]) {
+    sum += ym[E] * third;
+    dg += 3;
+  }
+  if (o.D == 3) {
+    if (k > 0) {
+      sum += zm[E];
+      dg += 1;
+    } else if (o.bc[4]) {
+      sum += zp[E] * third;
+      dg += 3;
+    }
+    if (k < o.n[2] - 1) {
+      sum += zp[E];
+      dg += 1;
+    } else if (o.bc[5]) {
+      sum += zm[E] * third;
+      dg += 3;
+    }
+  }
+  return (o.h2e[p] * bv[E] + sum) * inv_count(dg, T(0));
+}
+
+// Relaxed value of one regular cell by the scalar stencil (a group whose two
+// cells of the colour lie in different phases).
+template <class T>
+__device__ __noinline__ T relax1(const Op<T>& o, int q, int i, int j, int k, long long cc) {
+  int I[3] = {i, j, k};
+  T sum;
+  int dg;
+  reg_stencil(o, o.x[q], I, cc, sum, dg);
+  return (o.h2e[q] * o.b[q][cc] + sum) * inv_count(dg, T(0));
+}
+
+// One colour on regular cells, four x cells per work item (two of the
+// colour): the item's flags come in one 32-bit load and each of its rows
+// (centre, y and z neighbours, right-hand side) in one 16-byte vector load.
+// Needs n[0] % 4 == 0 and 16-byte aligned arrays.
+template <class T>
+__device__ __forceinline__ void ph_dense_vec(const Op<T>& o, int colour, const Ctx& c) {
+  constexpr int U = 2;
+  const int n0 = o.n[0], n1 = o.n[1], n2 = o.D == 3 ? o.n[2] : 1;
+  const unsigned nq = (unsigned)n0 >> 2;
+  const long long work = (o.ncell / n0) * (long long)nq;
+  const long long sy = n0, sz = (long long)n0 * n1;
+  for (long long t0 = c.i0; t0 < work; t0 += U * c.st) {
+    T xc[U][4], ym[U][4], yp[U][4], zm[U][4], zp[U][4], bv[U][4], xl[U], xr[U];
+    unsigned fw[U];
+    long long b0[U];
+    int J[U], K[U], I0[U], S[U], P[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      fw[u] = 0u;
+      b0[u] = 0;
+      J[u] = K[u] = I0[u] = S[u] = P[u] = 0;
+      xl[u] = xr[u] = T(0);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) xc[u][e] = ym[u][e] = yp[u][e] = zm[u][e] = zp[u][e] = bv[u][e] = T(0);
+      const long long t = t0 + u * c.st;
+      if (t >= work) continue;
+      const unsigned tu = (unsigned)t;
+      const unsigned row = fdiv(tu, o.dq);
+      const unsigned kq = fdiv(row, o.dn1);
+      const int j = (int)(row - kq * (unsigned)n1), k = (int)kq;
+      const int i0 = 4 * (int)(tu - row * nq);
+      const int sh = (j + k + colour) & 1;
+      const long long base = (long long)row * n0 + i0;
+      const unsigned w = *reinterpret_cast<const unsigned*>(o.flags + base);
+      const unsigned fa = (w >> (8 * sh)) & 0xffu, fb = (w >> (8 * (sh + 2))) & 0xffu;
+      const bool aa = !(fa & F_IRR) && (fa & 3), ab = !(fb & F_IRR) && (fb & 3);
+      if (!aa && !ab) continue;
+      const int p = aa ? ((fa & 1) ? 0 : 1) : ((fb & 1) ? 0 : 1);
+      fw[u] = w;
+      b0[u] = base;
+      J[u] = j;
+      K[u] = k;
+      I0[u] = i0;
+      S[u] = sh;
+      P[u] = p;
+      const T* X = o.x[p];
+      ld4(X + base, xc[u]);
+      if (sh == 0 && i0 > 0) xl[u] = X[base - 1];
+      if (sh == 1 && i0 + 4 < n0) xr[u] = X[base + 4];
+      if (j > 0) ld4(X + base - sy, ym[u]);
+      if (j < n1 - 1) ld4(X + base + sy, yp[u]);
+      if (o.D == 3) {
+        if (k > 0) ld4(X + base - sz, zm[u]);
+        if (k < n2 - 1) ld4(X + base + sz, zp[u]);
+      }
+      ld4(o.b[p] + base, bv[u]);
+    }
+    T v[U][2];
+    int q[U][2];
+    bool act[U][2];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const unsigned f = (fw[u] >> (8 * (S[u] + 2 * h))) & 0xffu;
+        act[u][h] = !(f & F_IRR) && (f & 3);
+        q[u][h] = (f & 1) ? 0 : 1;
+        v[u][h] = T(0);
+      }
+      if (!act[u][0] && !act[u][1]) continue;
+      const int i = I0[u] + S[u];
+      if (S[u] == 0) {
+        if (act[u][0] && q[u][0] == P[u])
+          v[u][0] = relax4<T, 0>(o, P[u], i, J[u], K[u], xc[u], xl[u], xr[u], ym[u], yp[u], zm[u], zp[u], bv[u]);
+        if (act[u][1] && q[u][1] == P[u])
+          v[u][1] = relax4<T, 2>(o, P[u], i + 2, J[u], K[u], xc[u], xl[u], xr[u], ym[u], yp[u], zm[u], zp[u], bv[u]);
+      } else {
+        if (act[u][0] && q[u][0] == P[u])
+          v[u][0] = relax4<T, 1>(o, P[u], i, J[u], K[u], xc[u], xl[u], xr[u], ym[u], yp[u], zm[u], zp[u], bv[u]);
+        if (act[u][1] && q[u][1] == P[u])
+          v[u][1] = relax4<T, 3>(o, P[u], i + 2, J[u], K[u], xc[u], xl[u], xr[u], ym[u], yp[u], zm[u], zp[u], bv[u]);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (act[u][h] && q[u][h] != P[u]) v[u][h] = relax1(o, q[u][h], i + 2 * h, J[u], K[u], b0[u] + S[u] + 2 * h);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (act[u][h]) o.x[q[u][h]][b0[u] + S[u] + 2 * h] = v[u][h];
+  }
+}
+
+template <class T>
+__device__ __forceinline__ bool vec_ok(const Op<T>& o) {
+  if (o.n[0] & 3) return false;
+  unsigned long long a = (unsigned long long)o.flags & 3ull;
+  for (int p = 0; p < 2; ++p) {
+    a |= (unsigned long long)o.x[p] & 15ull;
+    a |= (unsigned long long)o.b[p] & 15ull;
+  }
+  return a == 0;
+}
+
+template <class T>
+__device__ __forceinline__ void ph_dense(const Op<T>& o, int colour, const Ctx& c) {
+  if (vec_ok(o)) ph_dense_vec(o, colour, c);
+  else ph_dense_scalar(o, colour, c);
 }
 
 // sparse rows [rb, re), one warp per row (lanes over the entries, then a
@@ -318,23 +513,25 @@ __device__ __forceinline__ void ph_prolong(const Op<T>& f, const Op<T>& co, cons
   }
 }
 
-// nu red-black Gauss-Seidel sweeps.  Per colour: the regular cells relax,
-// then the sparse rows of that colour get new values from the current
-// iterate (into tmp) and are written in a second phase: rows of one colour may
-// couple through EB stencils, so none reads a value written in its own phase
-// and the result does not depend on thread timing.
+// nu red-black Gauss-Seidel sweeps.  Per colour, two phases: first the
+// sparse rows of the colour's cut cells get new values from the current
+// iterate (into tmp; rows of one colour may couple through EB stencils, so
+// none may see another's new value); then the colour's regular cells relax
+// and the cut-cell values are written.  A regular cell's stencil reaches only
+// cells of the other colour, so neither part of the second phase reads what
+// the other writes and the result does not depend on thread timing.
 template <class T>
 __device__ bool ph_smooth(const Op<T>& o, int nu, const Ctx& c, int l) {
   for (int s = 0; s < nu; ++s)
     for (int colour = 0; colour < 2; ++colour) {
+      long long rb = colour == 0 ? 0 : 2 * o.nirr_red, re = colour == 0 ? 2 * o.nirr_red : 2 * o.nirr;
+      if (re > rb) {
+        ph_rows(o, rb, re, 0, c);
+        if (!c.sync((l << 4) | 2)) return false;
+        ph_write(o, rb, re, c);
+      }
       ph_dense(o, colour, c);
       if (!c.sync((l << 4) | (colour ? 3 : 1))) return false;
-      long long rb = colour == 0 ? 0 : 2 * o.nirr_red, re = colour == 0 ? 2 * o.nirr_red : 2 * o.nirr;
-      if (re <= rb) continue;
-      ph_rows(o, rb, re, 0, c);
-      if (!c.sync((l << 4) | 2)) return false;
-      ph_write(o, rb, re, c);
-      if (!c.sync((l << 4) | 4)) return false;
     }
   return true;
 }
@@ -740,5 +937,28 @@ __global__ void __launch_bounds__(PT) k_barrier_bench(Barrier B, int reps) {
   __syncthreads();
   for (int i = 0; i < reps; ++i)
     if (!grid_sync(B, &epoch, (int)gridDim.x)) return;
+}
+
+// the persistent kernel's phases launched on their own, with its grid shape,
+// to time them on large levels: one colour of the regular-cell sweep, and the
+// residual fused with restriction (cut-cell residual rows as left in tmp)
+template <class T>
+__global__ void __launch_bounds__(PT) k_dense_phase(Op<T> o, int colour) {
+  Ctx c{};
+  c.i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  c.st = (long long)gridDim.x * blockDim.x;
+  c.gsize = (int)gridDim.x;
+  c.gcta = (int)blockIdx.x;
+  ph_dense(o, colour, c);
+}
+
+template <class T>
+__global__ void __launch_bounds__(PT) k_restrict_phase(Op<T> f, Op<T> co) {
+  Ctx c{};
+  c.i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  c.st = (long long)gridDim.x * blockDim.x;
+  c.gsize = (int)gridDim.x;
+  c.gcta = (int)blockIdx.x;
+  ph_restrict(f, co, c);
 }
 }  // namespace ebp

@@ -281,6 +281,8 @@ struct eb_poisson {
   void* d_binv = nullptr;
   int bm = 0;
   int smem_bytes = 0;  // dynamic shared memory of the persistent kernel
+  cudaEvent_t kev[2] = {nullptr, nullptr};  // bracket the persistent kernel
+  double kernel_ms = 0.0;                   // its device time in the last call
   std::vector<void*> allocs;
   long long bytes = 0;
 };
@@ -307,6 +309,7 @@ static Op<T> make_op(const DevLevel& L, std::vector<void*>& owner, long long* by
   o.dn0 = make_fastdiv((unsigned)L.g.n[0]);
   o.dn1 = make_fastdiv((unsigned)L.g.n[1]);
   o.dhx = make_fastdiv((unsigned)((L.g.n[0] + 1) / 2));
+  o.dq = make_fastdiv((unsigned)std::max(1, L.g.n[0] / 4));
   o.ncell = L.g.ncell;
   for (int k = 0; k < 6; ++k) o.bc[k] = L.g.bc[k];
   size_t n = (size_t)L.g.ncell;
@@ -559,6 +562,13 @@ static eb_status setup_persistent(eb_poisson* P) {
   return EB_OK;
 }
 
+static cudaError_t kernel_events(eb_poisson* P) {
+  cudaError_t e = cudaSuccess;
+  for (cudaEvent_t& k : P->kev)
+    if (!k && e == cudaSuccess) e = cudaEventCreate(&k);
+  return e;
+}
+
 static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cycles, int* status) {
   cudaStream_t s = P->s;
   cudaMemsetAsync(P->d_bar, 0, 4 * sizeof(unsigned), s);
@@ -576,7 +586,9 @@ static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cyc
   ctl.max_iters = 0;
   Barrier B{P->d_bar, (int*)(P->d_bar + 2)};
   void* args[4];
-  cudaError_t e;
+  cudaError_t e = kernel_events(P);
+  if (e != cudaSuccess) return cuda_fail(e, "event");
+  cudaEventRecord(P->kev[0], s);
   if (ctl.mixed) {
     const Hier<float>* H = (const Hier<float>*)P->d_hier;
     const Op<double>* F = P->d_fine;
@@ -595,9 +607,12 @@ static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cyc
     e = cudaLaunchCooperativeKernel((const void*)k_solve<double>, dim3(P->grid), dim3(PT), args, dyn, s);
   }
   counted();
+  cudaEventRecord(P->kev[1], s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(P->h_out, P->d_out, 4 * sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "persistent solve");
+  float kt = 0.0f;
+  if (cudaEventElapsedTime(&kt, P->kev[0], P->kev[1]) == cudaSuccess) P->kernel_ms = kt;
   unsigned long long nv = 0;
   e = cudaMemcpy(&nv, P->d_norms + P->o.max_cycles + 1, sizeof(nv), cudaMemcpyDeviceToHost);
   unsigned bar[3] = {0, 0, 0};
@@ -680,6 +695,8 @@ extern "C" void eb_poisson_destroy(eb_poisson* P) {
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->graph) cudaGraphDestroy(P->graph);
   if (P->ev) cudaEventDestroy(P->ev);
+  for (cudaEvent_t k : P->kev)
+    if (k) cudaEventDestroy(k);
   if (P->s) cudaStreamDestroy(P->s);
   if (P->h_norm) cudaFreeHost(P->h_norm);
   if (P->h_out) cudaFreeHost(P->h_out);
@@ -785,6 +802,7 @@ extern "C" eb_status eb_poisson_solve(eb_poisson* P, const double* d_rhs, const 
     if (e != cudaSuccess && st == EB_OK) st = cuda_fail(e, "solve");
     join_out(P, user);
     inf.kernel_launches = P->launches;
+    inf.kernel_ms = P->kernel_ms;
     inf.status = st;
     inf.outer_iters = iters;
     inf.vcycles = cycles;
@@ -881,7 +899,8 @@ static std::vector<int> split_ctas(const std::vector<long long>& cells, int tota
 }
 
 template <class T>
-static eb_status launch_batch_t(eb_poisson* const* P, int n, int max_iters, int grid_total, int smem, cudaStream_t s) {
+static eb_status launch_batch_t(eb_poisson* const* P, int n, int max_iters, int grid_total, int smem, cudaStream_t s,
+                                double* kernel_ms) {
   std::vector<long long> cells(n);
   for (int i = 0; i < n; ++i) cells[i] = P[i]->G->L[0].g.ncell;
   int nsm = 0;
@@ -920,9 +939,12 @@ static eb_status launch_batch_t(eb_poisson* const* P, int n, int max_iters, int 
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, items.data(), sizeof(BatchItem<T>) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_cta, cta_item.data(), sizeof(int) * cta_item.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = kernel_events(P[0]);
   if (e == cudaSuccess) {
     void* args[2] = {(void*)&d_items, (void*)&d_cta};
+    cudaEventRecord(P[0]->kev[0], s);
     e = cudaLaunchCooperativeKernel((const void*)k_solve_batch<T>, dim3(start), dim3(PT), args, (size_t)smem, s);
+    cudaEventRecord(P[0]->kev[1], s);
     counted();
   }
   if (d_items) cudaFreeAsync(d_items, s);
@@ -930,6 +952,9 @@ static eb_status launch_batch_t(eb_poisson* const* P, int n, int max_iters, int 
   // the host vectors must outlive the copies above
   cudaError_t e2 = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = e2;
+  float kt = 0.0f;
+  if (e == cudaSuccess && cudaEventElapsedTime(&kt, P[0]->kev[0], P[0]->kev[1]) == cudaSuccess && kernel_ms)
+    *kernel_ms += kt;
   return e == cudaSuccess ? EB_OK : cuda_fail(e, "batched solve");
 }
 
@@ -938,7 +963,8 @@ static eb_status launch_batch_t(eb_poisson* const* P, int n, int max_iters, int 
 // allowed (0: until convergence).  Results (status, iterations, V-cycles,
 // residual) are read into each handle's pinned h_out / h_norm.
 eb_status batch_step(eb_poisson* const* P, int n, const double* const* rhs, const double* const* sigma,
-                     double* const* phi, bool fresh, bool copy_out, int max_iters, cudaStream_t s) {
+                     double* const* phi, bool fresh, bool copy_out, int max_iters, cudaStream_t s,
+                     double* kernel_ms) {
   if (n < 1) return EB_OK;
   bool mixed = P[0]->o.precision == EB_PREC_MIXED;
   int smem = 0;
@@ -968,8 +994,8 @@ eb_status batch_step(eb_poisson* const* P, int n, const double* const* rhs, cons
   // at most `total` instances per launch
   for (int b0 = 0; b0 < n; b0 += total) {
     int m = std::min(total, n - b0);
-    eb_status st = mixed ? launch_batch_t<float>(P + b0, m, max_iters, total, smem, s)
-                         : launch_batch_t<double>(P + b0, m, max_iters, total, smem, s);
+    eb_status st = mixed ? launch_batch_t<float>(P + b0, m, max_iters, total, smem, s, kernel_ms)
+                         : launch_batch_t<double>(P + b0, m, max_iters, total, smem, s, kernel_ms);
     if (st != EB_OK) return st;
   }
   for (int i = 0; i < n; ++i) {
@@ -1013,7 +1039,8 @@ extern "C" eb_status eb_poisson_solve_batched(eb_poisson* const* P, int n, const
   cudaStream_t s = (cudaStream_t)stream;
   long long launches = 0;
   g_count = &launches;
-  eb_status st = batch_step(P, n, d_rhs, d_sigma, d_phi, true, true, 0, s);
+  double kms = 0.0;
+  eb_status st = batch_step(P, n, d_rhs, d_sigma, d_phi, true, true, 0, s, &kms);
   g_count = nullptr;
   if (st != EB_OK) return st;
   eb_status worst = EB_OK;
@@ -1021,6 +1048,7 @@ extern "C" eb_status eb_poisson_solve_batched(eb_poisson* const* P, int n, const
     eb_solve_info inf;
     batch_info(P[i], &inf);
     inf.kernel_launches = launches;
+    inf.kernel_ms = kms;
     if (infos) infos[i] = inf;
     if (inf.status != EB_OK && worst == EB_OK) worst = (eb_status)inf.status;
   }
@@ -1086,14 +1114,17 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // the persistent kernel's own phase code, in its grid shape when it has one
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->G->device);
+  const int grid = P->persistent ? P->grid : nsm;
   auto launch = [&](int i) {
     if (kernel == 0) {
-      long long w = (n / P->op64[0].n[0]) * ((P->op64[0].n[0] + 1) / 2);
-      if (mixed) k_smooth_dense<float><<<blocks(w), 256, 0, s>>>(P->op32[0], i & 1);
-      else k_smooth_dense<double><<<blocks(w), 256, 0, s>>>(P->op64[0], i & 1);
+      if (mixed) k_dense_phase<float><<<grid, PT, 0, s>>>(P->op32[0], i & 1);
+      else k_dense_phase<double><<<grid, PT, 0, s>>>(P->op64[0], i & 1);
     } else {
-      if (mixed) k_resid_restrict<float><<<blocks(P->op32[1].ncell), 256, 0, s>>>(P->op32[0], P->op32[1]);
-      else k_resid_restrict<double><<<blocks(P->op64[1].ncell), 256, 0, s>>>(P->op64[0], P->op64[1]);
+      if (mixed) k_restrict_phase<float><<<grid, PT, 0, s>>>(P->op32[0], P->op32[1]);
+      else k_restrict_phase<double><<<grid, PT, 0, s>>>(P->op64[0], P->op64[1]);
     }
   };
   launch(0);
@@ -1210,6 +1241,7 @@ extern "C" eb_status eb_poisson_residual_noalloc(const eb_geom* G, const double*
   o.dn0 = make_fastdiv((unsigned)F.g.n[0]);
   o.dn1 = make_fastdiv((unsigned)F.g.n[1]);
   o.dhx = make_fastdiv((unsigned)((F.g.n[0] + 1) / 2));
+  o.dq = make_fastdiv((unsigned)std::max(1, F.g.n[0] / 4));
   o.ncell = n;
   for (int k = 0; k < 6; ++k) o.bc[k] = F.g.bc[k];
   o.x[0] = const_cast<double*>(d_phi);

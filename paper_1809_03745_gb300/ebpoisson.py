@@ -64,7 +64,7 @@ class SolverOpts(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("vcycles", C.c_int), ("rel_res", C.c_double),
-                ("bnorm", C.c_double), ("kernel_launches", C.c_longlong)]
+                ("bnorm", C.c_double), ("kernel_launches", C.c_longlong), ("kernel_ms", C.c_double)]
 
 
 EXPORTS = ["eb_status_str", "eb_last_error", "eb_geom_build", "eb_geom_query", "eb_geom_destroy", "eb_geom_export",
@@ -234,7 +234,7 @@ def eb_poisson_solve(handle, rhs, sigma, phi, stream=None) -> dict:
     if st not in (EB_OK, EB_ERR_NOT_CONVERGED):
         _check(st, "eb_poisson_solve")
     return dict(status=info.status, outer_iters=info.outer_iters, vcycles=info.vcycles, rel_res=info.rel_res,
-                bnorm=info.bnorm, kernel_launches=info.kernel_launches)
+                bnorm=info.bnorm, kernel_launches=info.kernel_launches, kernel_ms=info.kernel_ms)
 
 
 def eb_poisson_profile(handle, kernel: int, reps: int, stream=None):
@@ -246,7 +246,7 @@ def eb_poisson_profile(handle, kernel: int, reps: int, stream=None):
 
 def _info_dict(info):
     return dict(status=info.status, outer_iters=info.outer_iters, vcycles=info.vcycles, rel_res=info.rel_res,
-                bnorm=info.bnorm, kernel_launches=info.kernel_launches)
+                bnorm=info.bnorm, kernel_launches=info.kernel_launches, kernel_ms=info.kernel_ms)
 
 
 def eb_poisson_solve_batched(handles, rhs, sigma, phi, stream=None) -> list:
