@@ -164,7 +164,9 @@ enum { EB_PREC_FP64 = 0, EB_PREC_MIXED = 1 };
 typedef struct {
   double tol;        /* stop when max|r| <= tol * max|b| (Sec. 3.3.2), default 1e-10 */
   int max_cycles;    /* cap on V-cycles in total, default 100 */
-  int nu1, nu2;      /* red-black Gauss-Seidel sweeps before / after the coarse correction, default 2, 2 */
+  int nu1, nu2;      /* red-black Gauss-Seidel sweeps before / after the coarse correction;
+                        -1 (the default) = by dimension: 2 in 2D, 6 in 3D, the fastest
+                        to 1e-10 on the rod-plane and pin-plane workloads */
   int precision;     /* EB_PREC_FP64: FP64 V-cycles; EB_PREC_MIXED: FP32 V-cycles inside FP64 defect correction */
   int inner_cycles;  /* FP32 V-cycles per FP64 outer iteration (mixed), default 2 */
   int bottom_sweeps; /* relaxation sweeps on the coarsest level, default 64 */
@@ -269,11 +271,68 @@ eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, double* ms_per
 /* Diagnostics (no counterpart in the paper): the phases of the first V-cycle
  * of the last persistent solve.  out[0] = number of phases m; then for each
  * phase i, out[1+2i] = its code ((level << 4) | kind; kinds 1 red regular
- * cells, 3 black regular cells, 2 sparse rows computed, 4 sparse rows
- * written, 5 sparse residual rows, 6 residual + restriction, 7 prolongation,
+ * cells, 3 black regular cells (each also writes the sparse-row values of
+ * its colour), 2 sparse rows computed, 5 sparse residual rows, 6 residual +
+ * restriction, 7 prolongation,
  * 8 end of the one-CTA levels, 9 bottom solve) and
  * out[2+2i] its duration in ms.  n is the capacity of out. */
 eb_status eb_poisson_trace(eb_poisson* P, double* out, int n);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous-batching solve server (no counterpart in the paper, whose
+ * solves run one per time step inside a plasma code).  Requests (a geometry
+ * description and host fields) are queued on submit; a worker thread admits
+ * them in arrival order while the device-memory budget and the slot count
+ * allow, builds their geometry and hierarchy on the device, and advances
+ * every admitted instance together in batched persistent launches of
+ * `step_iters` FP64 outer iterations each.  Instances join and leave at those
+ * boundaries, so a request that arrives while others run starts at the next
+ * step and a converged one frees its slot and memory at once.  An instance's
+ * iterates are those of its single solve (a resumed step recomputes the same
+ * residual), so its result equals the single solve with the same options.
+ * A request whose build or solve fails completes with that status; the
+ * others are not affected. */
+typedef struct {
+  double hbm_budget_bytes; /* device bytes the admitted instances may hold; <= 0: half the free memory */
+  int max_slots;           /* instances on the device at once, 1..1024 */
+  int queue_cap;           /* requests waiting for admission before submit returns EB_ERR_BUSY */
+  int step_iters;          /* FP64 outer iterations per batched launch (>= 1) */
+  int device;              /* CUDA device */
+  eb_solver_opts solver;   /* options of every instance (persistent path; launch_mode ignored) */
+} eb_server_opts;
+
+typedef struct {
+  long long submitted, completed, failed, queued, active;
+  double p50_ms, p99_ms;      /* latency from submit to result ready, completed requests */
+  double cells_per_s;         /* cells of completed requests / time from first admission to last completion */
+  long long cells_completed;
+  long long hbm_budget, hbm_used, hbm_peak; /* bytes accounted to admitted instances */
+  long long steps;            /* batched launches */
+  long long estimate_misses;  /* admissions whose measured bytes exceeded the pre-build estimate */
+} eb_server_stats;
+
+typedef struct eb_server eb_server;
+
+void eb_server_opts_default(eb_server_opts* o);
+/* Starts the worker thread.  Errors: EB_ERR_INVALID, EB_ERR_CUDA. */
+eb_status eb_server_create(const eb_server_opts* o, eb_server** out);
+/* Queues one solve.  desc (and its arrays), h_rhs [2][n_cells] and h_sigma
+ * [n_cells] (may be NULL) are copied before the call returns.  *ticket
+ * names the request.  EB_ERR_BUSY when the queue holds queue_cap requests;
+ * EB_ERR_INVALID for a description rejected on the host. */
+eb_status eb_server_submit(eb_server* S, const eb_geom_desc* desc, const double* h_rhs, const double* h_sigma,
+                           unsigned long long* ticket);
+/* EB_ERR_BUSY while the request is queued or running.  When it is done:
+ * copies phi [2][n_cells] into h_phi (may be NULL) and the solve's info,
+ * returns EB_OK, and forgets the ticket.  A failed request returns EB_OK
+ * with info->status holding its error.  EB_ERR_INVALID for an unknown ticket. */
+eb_status eb_server_poll(eb_server* S, unsigned long long ticket, double* h_phi, eb_solve_info* info);
+/* eb_server_poll that blocks up to timeout_s seconds (EB_ERR_BUSY after that). */
+eb_status eb_server_wait(eb_server* S, unsigned long long ticket, double timeout_s, double* h_phi,
+                         eb_solve_info* info);
+eb_status eb_server_query(eb_server* S, eb_server_stats* out);
+/* Finishes the admitted and queued requests, stops the worker, frees everything. */
+void eb_server_destroy(eb_server* S);
 
 #ifdef __cplusplus
 }

@@ -71,3 +71,13 @@ eb_status launch_rhs64(const eb_geom* G, const double* s_rhs, const double* sigm
                        cudaStream_t s);
 
 }  // namespace ebp
+
+// solver internals used by the serving loop (server.cu)
+struct eb_poisson;
+eb_status batch_prepare(eb_poisson* P, const double* rhs, const double* sigma, const double* phi, cudaStream_t s);
+eb_status batch_step(eb_poisson* const* P, int n, const double* const* rhs, const double* const* sigma,
+                     double* const* phi, bool fresh, bool copy_out, int max_iters, cudaStream_t s,
+                     double* kernel_ms);
+void batch_info(eb_poisson* Q, eb_solve_info* inf);
+eb_status batch_copy_out(eb_poisson* P, double* phi, cudaStream_t s);
+long long poisson_device_bytes(const eb_poisson* P);

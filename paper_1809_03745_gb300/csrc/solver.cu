@@ -291,8 +291,8 @@ extern "C" void eb_solver_opts_default(eb_solver_opts* o) {
   if (!o) return;
   o->tol = 1e-10;
   o->max_cycles = 100;
-  o->nu1 = 2;
-  o->nu2 = 2;
+  o->nu1 = -1;
+  o->nu2 = -1;
   o->precision = EB_PREC_MIXED;
   o->inner_cycles = 2;
   o->bottom_sweeps = 64;
@@ -636,6 +636,9 @@ extern "C" eb_status eb_poisson_setup(const eb_geom* G, const eb_solver_opts* op
   if (opts) P->o = *opts;
   else eb_solver_opts_default(&P->o);
   eb_solver_opts& o = P->o;
+  const int nu_auto = G->L[0].g.D == 3 ? 6 : 2;
+  if (o.nu1 == -1) o.nu1 = nu_auto;
+  if (o.nu2 == -1) o.nu2 = nu_auto;
   if (!(o.tol > 0.0) || o.max_cycles < 1 || o.nu1 < 0 || o.nu2 < 0 || o.inner_cycles < 1 || o.bottom_sweeps < 1 ||
       (o.precision != EB_PREC_FP64 && o.precision != EB_PREC_MIXED) || o.launch_mode < 0 || o.launch_mode > 2) {
     delete P;
@@ -958,6 +961,28 @@ static eb_status launch_batch_t(eb_poisson* const* P, int n, int max_iters, int 
   return e == cudaSuccess ? EB_OK : cuda_fail(e, "batched solve");
 }
 
+// An instance's right-hand side assembled into b and its guess copied in,
+// ready for batch_step(fresh = false).
+eb_status batch_prepare(eb_poisson* P, const double* rhs, const double* sigma, const double* phi, cudaStream_t s) {
+  const DevLevel& F = P->G->L[0];
+  cudaMemsetAsync(P->d_norm + 1, 0, sizeof(unsigned long long), s);
+  eb_status st = launch_rhs64(P->G, rhs, sigma, P->b64, (double*)(P->d_norm + 1), s);
+  if (st != EB_OK) return st;
+  k_copy_masked<<<blocks(F.g.ncell), 256, 0, s>>>(F.flags, F.g.ncell, phi, P->phi64);
+  counted(2);
+  return EB_OK;
+}
+
+// The instance's current iterate copied out (entries without an unknown = 0).
+eb_status batch_copy_out(eb_poisson* P, double* phi, cudaStream_t s) {
+  const DevLevel& F = P->G->L[0];
+  k_copy_masked<<<blocks(F.g.ncell), 256, 0, s>>>(F.flags, F.g.ncell, P->phi64, phi);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? EB_OK : cuda_fail(e, "copy out");
+}
+
+long long poisson_device_bytes(const eb_poisson* P) { return P->bytes; }
+
 // One cooperative launch over instances that share precision and device.
 // fresh: assemble b and copy the guess in first; max_iters: outer iterations
 // allowed (0: until convergence).  Results (status, iterations, V-cycles,
@@ -984,12 +1009,8 @@ eb_status batch_step(eb_poisson* const* P, int n, const double* const* rhs, cons
   int total = nsm * std::min(per_sm, 1);
   if (fresh)
     for (int i = 0; i < n; ++i) {
-      const DevLevel& F = P[i]->G->L[0];
-      cudaMemsetAsync(P[i]->d_norm + 1, 0, sizeof(unsigned long long), s);
-      eb_status st = launch_rhs64(P[i]->G, rhs[i], sigma ? sigma[i] : nullptr, P[i]->b64, (double*)(P[i]->d_norm + 1), s);
+      eb_status st = batch_prepare(P[i], rhs[i], sigma ? sigma[i] : nullptr, phi[i], s);
       if (st != EB_OK) return st;
-      k_copy_masked<<<blocks(F.g.ncell), 256, 0, s>>>(F.flags, F.g.ncell, phi[i], P[i]->phi64);
-      counted(2);
     }
   // at most `total` instances per launch
   for (int b0 = 0; b0 < n; b0 += total) {
@@ -1014,7 +1035,7 @@ eb_status batch_step(eb_poisson* const* P, int n, const double* const* rhs, cons
   return e == cudaSuccess ? EB_OK : cuda_fail(e, "batched solve");
 }
 
-static void batch_info(eb_poisson* Q, eb_solve_info* inf) {
+void batch_info(eb_poisson* Q, eb_solve_info* inf) {
   std::memset(inf, 0, sizeof(*inf));
   double r = as_double(Q->h_norm[0]), b = as_double(Q->h_norm[1]);
   inf->status = Q->h_out[0];

@@ -67,10 +67,24 @@ class SolveInfo(C.Structure):
                 ("bnorm", C.c_double), ("kernel_launches", C.c_longlong), ("kernel_ms", C.c_double)]
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_double), ("max_slots", C.c_int), ("queue_cap", C.c_int),
+                ("step_iters", C.c_int), ("device", C.c_int), ("solver", SolverOpts)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
+                ("queued", C.c_longlong), ("active", C.c_longlong), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("cells_per_s", C.c_double), ("cells_completed", C.c_longlong), ("hbm_budget", C.c_longlong),
+                ("hbm_used", C.c_longlong), ("hbm_peak", C.c_longlong), ("steps", C.c_longlong),
+                ("estimate_misses", C.c_longlong)]
+
+
 EXPORTS = ["eb_status_str", "eb_last_error", "eb_geom_build", "eb_geom_query", "eb_geom_destroy", "eb_geom_export",
            "eb_solver_opts_default", "eb_poisson_setup", "eb_poisson_destroy", "eb_poisson_residual",
            "eb_poisson_solve", "eb_field_eval", "eb_poisson_profile", "eb_poisson_trace",
-           "eb_poisson_residual_noalloc", "eb_poisson_solve_batched"]
+           "eb_poisson_residual_noalloc", "eb_poisson_solve_batched", "eb_server_opts_default", "eb_server_create",
+           "eb_server_submit", "eb_server_poll", "eb_server_wait", "eb_server_query", "eb_server_destroy"]
 
 
 def lib_path() -> str:
@@ -118,6 +132,18 @@ def load(build_if_missing: bool = False):
         lib.eb_poisson_trace.argtypes = [P, C.POINTER(C.c_double), C.c_int]
         lib.eb_poisson_profile.restype = C.c_int
         lib.eb_poisson_profile.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), P]
+        lib.eb_server_opts_default.argtypes = [C.POINTER(ServerOpts)]
+        lib.eb_server_create.restype = C.c_int
+        lib.eb_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(P)]
+        lib.eb_server_submit.restype = C.c_int
+        lib.eb_server_submit.argtypes = [P, C.POINTER(GeomDesc), P, P, C.POINTER(C.c_ulonglong)]
+        lib.eb_server_poll.restype = C.c_int
+        lib.eb_server_poll.argtypes = [P, C.c_ulonglong, P, C.POINTER(SolveInfo)]
+        lib.eb_server_wait.restype = C.c_int
+        lib.eb_server_wait.argtypes = [P, C.c_ulonglong, C.c_double, P, C.POINTER(SolveInfo)]
+        lib.eb_server_query.restype = C.c_int
+        lib.eb_server_query.argtypes = [P, C.POINTER(ServerStats)]
+        lib.eb_server_destroy.argtypes = [P]
         _lib = lib
         return lib
 
@@ -330,7 +356,7 @@ def solve_batched(solvers, rhs, sigma=None, phi=None, stream=None):
 class Poisson:
     """Multigrid solver bound to a Geometry (owns an eb_poisson)."""
 
-    def __init__(self, geom: Geometry, *, precision="mixed", tol=1e-10, max_cycles=100, nu1=2, nu2=2,
+    def __init__(self, geom: Geometry, *, precision="mixed", tol=1e-10, max_cycles=100, nu1=-1, nu2=-1,
                  inner_cycles=2, bottom_sweeps=64, launch_mode=0, stream=None):
         self.geom = geom
         o = eb_solver_opts_default()
@@ -391,6 +417,80 @@ class Poisson:
     def close(self):
         if getattr(self, "_h", None):
             load().eb_poisson_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching solve server (owns an eb_server and its worker thread).
+
+    submit() copies the request and returns a ticket at once; poll() returns
+    None until the result is ready, then (phi [2][n_cells] numpy, info)."""
+
+    def __init__(self, *, hbm_budget_bytes=0.0, max_slots=64, queue_cap=1 << 16, step_iters=1, device=0,
+                 precision="mixed", tol=1e-10, max_cycles=200, nu1=-1, nu2=-1, inner_cycles=2):
+        lib = load()
+        o = ServerOpts()
+        lib.eb_server_opts_default(C.byref(o))
+        o.hbm_budget_bytes, o.max_slots, o.queue_cap = float(hbm_budget_bytes), max_slots, queue_cap
+        o.step_iters, o.device = step_iters, device
+        o.solver.tol, o.solver.max_cycles, o.solver.nu1, o.solver.nu2 = tol, max_cycles, nu1, nu2
+        o.solver.precision = EB_PREC_MIXED if precision == "mixed" else EB_PREC_FP64
+        o.solver.inner_cycles = inner_cycles
+        h = C.c_void_p()
+        _check(lib.eb_server_create(C.byref(o), C.byref(h)), "eb_server_create")
+        self._h = h
+        self._n = {}
+
+    def submit(self, desc: dict, rhs, sigma=None):
+        """Queue one solve; rhs [2][n_cells] (or [n_cells]) and sigma [n_cells] as host arrays.
+        Raises EBError(EB_ERR_BUSY) when the queue is full."""
+        import numpy as np
+        d, keep = make_desc(desc)
+        n = int(np.prod([int(desc["n"][k]) for k in range(int(desc["dim"]))]))
+        r = np.ascontiguousarray(np.asarray(rhs, dtype=np.float64))
+        if r.ndim == 1:
+            r = np.stack([r, np.zeros_like(r)])
+        r = np.ascontiguousarray(r.reshape(2, n))
+        sg = None if sigma is None else np.ascontiguousarray(np.asarray(sigma, dtype=np.float64).reshape(n))
+        t = C.c_ulonglong()
+        _check(load().eb_server_submit(self._h, C.byref(d), C.c_void_p(r.ctypes.data),
+                                       C.c_void_p(sg.ctypes.data) if sg is not None else C.c_void_p(0),
+                                       C.byref(t)), "eb_server_submit")
+        self._n[t.value] = n
+        return t.value
+
+    def _take(self, fn, ticket, *extra):
+        import numpy as np
+        n = self._n.get(ticket, 0)  # unknown tickets: the library reports them
+        phi = np.zeros((2, n))
+        info = SolveInfo()
+        st = fn(self._h, C.c_ulonglong(ticket), *extra, C.c_void_p(phi.ctypes.data), C.byref(info))
+        if st == EB_ERR_BUSY:
+            return None
+        _check(st, "eb_server_poll")
+        self._n.pop(ticket, None)
+        return phi, _info_dict(info)
+
+    def poll(self, ticket):
+        return self._take(load().eb_server_poll, ticket)
+
+    def wait(self, ticket, timeout_s=600.0):
+        return self._take(load().eb_server_wait, ticket, C.c_double(timeout_s))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().eb_server_query(self._h, C.byref(s)), "eb_server_query")
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().eb_server_destroy(self._h)
             self._h = None
 
     def __del__(self):
