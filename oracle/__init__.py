@@ -87,6 +87,11 @@ def _load():
             lib.or_boundary_flux.restype = C.c_double
             lib.or_boundary_flux.argtypes = [P, C.POINTER(_Data), C.c_void_p]
             lib.or_field.argtypes = [P, C.POINTER(_Data), C.c_void_p, C.c_void_p, C.c_void_p]
+            lib.or_boundary_flux_masked.restype = C.c_double
+            lib.or_boundary_flux_masked.argtypes = [P, C.POINTER(_Data), C.c_void_p, C.c_void_p]
+            lib.or_face_flux.restype = C.c_long
+            lib.or_face_flux.argtypes = [P, C.POINTER(_Data), C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                                         C.c_void_p, C.c_void_p]
             lib.or_eval_implicit.restype = C.c_double
             lib.or_eval_implicit.argtypes = [C.POINTER(_Desc), C.c_int, C.c_void_p]
             _lib = lib
@@ -305,6 +310,22 @@ class Geometry:
         dt, _keep = data
         phi_dof = np.ascontiguousarray(phi_dof, dtype=np.float64)
         return _lib.or_boundary_flux(self._g, C.byref(dt), _ptr(phi_dof))
+
+    def boundary_flux_masked(self, data, phi_dof, mask):
+        dt, _keep = data
+        phi_dof = np.ascontiguousarray(phi_dof, dtype=np.float64)
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        return _lib.or_boundary_flux_masked(self._g, C.byref(dt), _ptr(phi_dof), _ptr(m))
+
+    def face_flux(self, data, a, J, p):
+        """(dof indices, weights, constant) of alpha/h x the +e_a centroid flux of face (a, J)."""
+        dt, _keep = data
+        Jv = np.array([J[0], J[1], J[2] if len(J) > 2 else 0], dtype=np.int64)
+        idx = np.zeros(512, np.int64)
+        w = np.zeros(512)
+        c = np.zeros(1)
+        n = _lib.or_face_flux(self._g, C.byref(dt), a, _ptr(Jv), p, _ptr(idx), _ptr(w), _ptr(c))
+        return idx[:n].copy(), w[:n].copy(), float(c[0])
 
     def field(self, data, phi_dof):
         """E[D][2][cell] at cell centres and En[cell][2] = -dphi/dn_in at EB centroids."""

@@ -1114,10 +1114,11 @@ long or_assemble(const or_geom* g, const or_data* dt, long* rows, long* cols, do
 
 /* total outward boundary flux, integrated: sum over wall faces and EBs of
  * alpha h^{D-1} F_out, interface EBs contributing sigma alpha h^{D-1}. */
-double or_boundary_flux(const or_geom* g, const or_data* dt, const double* phi_dof)
+static double boundary_flux(const or_geom* g, const or_data* dt, const double* phi_dof, const uint8_t* mask)
 {
   double tot = 0.0, h = g->d.h, hd1 = (g->D == 3) ? h * h : h;
   for (long c = 0; c < g->ncell; ++c) {
+    if (mask && !mask[c]) continue;
     long I[3];
     cell_ijk(g, c, I);
     for (int p = 0; p < 2; ++p) {
@@ -1148,6 +1149,41 @@ double or_boundary_flux(const or_geom* g, const or_data* dt, const double* phi_d
       tot = tot + dt->sigma[c] * g->eba[c] * hd1;
   }
   return tot;
+}
+
+double or_boundary_flux(const or_geom* g, const or_data* dt, const double* phi_dof)
+{
+  return boundary_flux(g, dt, phi_dof, NULL);
+}
+
+/* The same sum over the cells whose mask entry is non-zero (a composite grid
+ * counts the coarse cells outside a refined box only). */
+double or_boundary_flux_masked(const or_geom* g, const or_data* dt, const double* phi_dof, const uint8_t* mask)
+{
+  return boundary_flux(g, dt, phi_dof, mask);
+}
+
+/* The flux of face (a, J), phase p, as it enters the row of the cell on the
+ * face's low side: alpha/h times the centroid flux in the +e_a direction, a
+ * linear form in the dofs plus a constant.  Returns the number of terms, 0
+ * when the face carries no flux.  A composite operator uses it to take a
+ * coarse flux out of a coarse row before putting the fine fluxes through the
+ * same face in its place (refluxing). */
+long or_face_flux(const or_geom* g, const or_data* dt, int a, const long* Jin, int p, long* idx, double* w,
+                  double* c)
+{
+  long J[3] = {Jin[0], Jin[1], Jin[2]};
+  *c = 0.0;
+  double al = g->alpha[a][p][face_id(g, a, J)];
+  if (!(al > 0.0)) return 0;
+  lform F;
+  if (!centroid_flux(g, dt, a, J, p, &F)) return 0;
+  for (int k = 0; k < F.n; ++k) {
+    idx[k] = F.idx[k];
+    w[k] = F.w[k] * al / g->d.h;
+  }
+  *c = F.c * al / g->d.h;
+  return F.n;
 }
 
 /* E = -grad phi at cell centres per phase ([D][2][cell]) and the normal
