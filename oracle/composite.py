@@ -200,6 +200,21 @@ class Composite:
                             faces.append((a, s, fc, J, cc, CI, al, terms))
         self.faces = faces
 
+    def coarse_cf_faces(self):
+        """(a, s, coarse cell index triple) of every coarse cell across a CF side."""
+        out = []
+        for a in range(self.D):
+            for s in (0, 1):
+                if (s == 0 and self.box_lo[a] == 0) or (s == 1 and self.box_hi[a] == self.nc[a]):
+                    continue
+                ranges = [range(self.box_lo[k], self.box_hi[k]) if k < self.D else range(1) for k in range(3)]
+                ranges[a] = [self.box_lo[a] - 1] if s == 0 else [self.box_hi[a]]
+                for i0 in ranges[0]:
+                    for i1 in ranges[1]:
+                        for i2 in ranges[2]:
+                            out.append((a, s, [i0, i1, i2]))
+        return out
+
     @staticmethod
     def _face_index(g, a, J):
         n = list(g.n) + [1] * (3 - len(g.n))
@@ -255,7 +270,6 @@ class Composite:
         b = np.concatenate([Rc @ bc, bf])
         hf, hc = gf.h, gc.h
         # CF fluxes and refluxing
-        removed = set()
         for (a, s, fc, J, cc, CI, al, terms) in self.faces:
             eps0 = float(self.desc["eps"][0])
             # F_cf = eps0 (ghost - phi_F)/h_f as a row over the composite vector
@@ -270,24 +284,28 @@ class Composite:
             for col, w in row.items():
                 A[rf, col] -= al * w / hf                       # r_F += alpha F / h_f
                 A[rcr, col] += al * w / hc / (1 << (D - 1))     # r_C -= mean fine flux / h_c
-            if cc not in removed:
-                removed.add(cc)
-                # take the coarse operator's flux through this CF face out of C's row
-                JC = list(CI)
-                if s == 0:
-                    JC[a] += 1  # C below the box: the face is C's high face
-                sign = 1.0 if s == 0 else -1.0
-                idx, w, c0 = gc.face_flux(self.dc, a, JC, 0)
-                # r_C contains sign * (w . phi + c0); remove it
-                for i, wk in zip(idx, w):
-                    r_i = int(self.cmap[i])
-                    if r_i >= 0:
-                        A[rcr, r_i] += sign * wk
-                    else:  # a coarse dof under the box: through the averaging map
-                        mrow = M.getrow(i)
-                        for j, mv in zip(mrow.indices, mrow.data):
-                            A[rcr, self.nco + j] += sign * wk * mv
-                b[rcr] -= sign * c0
+        # every coarse row next to a CF side loses the coarse operator's own
+        # flux through that side (the box has no coarse equation to balance it)
+        for (a, s, CI) in self.coarse_cf_faces():
+            cc = self.ccell(CI)
+            if gc.dof[0][cc] < 0:
+                continue
+            rcr = int(self.cmap[gc.dof[0][cc]])
+            JC = list(CI)
+            if s == 0:
+                JC[a] += 1  # C below the box: the face is C's high face
+            sign = 1.0 if s == 0 else -1.0
+            idx, w, c0 = gc.face_flux(self.dc, a, JC, 0)
+            # r_C contains sign * (w . phi + c0); remove it
+            for i, wk in zip(idx, w):
+                r_i = int(self.cmap[i])
+                if r_i >= 0:
+                    A[rcr, r_i] += sign * wk
+                else:  # a coarse dof under the box: through the averaging map
+                    mrow = M.getrow(i)
+                    for j, mv in zip(mrow.indices, mrow.data):
+                        A[rcr, self.nco + j] += sign * wk * mv
+            b[rcr] -= sign * c0
         self.A, self.b = A.tocsr(), b
         return self.A, self.b
 
