@@ -278,6 +278,44 @@ eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, double* ms_per
  * out[2+2i] its duration in ms.  n is the capacity of out. */
 eb_status eb_poisson_trace(eb_poisson* P, double* out, int n);
 
+/* ---------------------------------------------------------------- composite grid
+ * One ratio-2 refined box over the coarse grid (Sec. 3.3.2 solves on refined
+ * levels; coarse-fine coupling by refluxing, Sec. 3.3).  The box covers
+ * coarse cells [box_lo, box_hi) per axis (sides a positive multiple of 4
+ * cells); the fine grid has 2 (box_hi - box_lo) cells per axis at h/2 and is
+ * built from the same description.  Composite operator: fine cells next to a
+ * coarse-fine (CF) side get the flux eps_gas (ghost - phi)/h_f through it,
+ * the ghost by quadratic tangential interpolation of coarse values (weights
+ * -3/32, 15/16, 5/32) and quadratic normal interpolation (-1/5, 2/3, 8/15),
+ * falling back to linear, then constant, where a needed cell is outside the
+ * domain, under the box, covered or cut; the coarse cell across a CF face
+ * has the coarse flux through it replaced by minus the mean of the fine
+ * fluxes (exact conservation); coarse cells under the box carry no equation
+ * and take the kappa-weighted mean of their children.  Only the gas phase may
+ * touch a CF side (EB_ERR_UNSUPPORTED otherwise).
+ * Fields: coarse [2][n_coarse], fine [2][n_fine] (layout as elsewhere). */
+typedef struct eb_amr eb_amr;
+eb_status eb_amr_setup(const eb_geom_desc* coarse, const int box_lo[3], const int box_hi[3],
+                       const eb_solver_opts* opts, void* stream, eb_amr** out);
+eb_status eb_amr_query(const eb_amr* A, long long* n_coarse, long long* n_fine, int fine_n[3], long long* cf_faces);
+/* Composite residual b - A phi (FP64): d_r_c is 0 under the box and where a
+ * cell has no unknown; phi_c values under the box are ignored (replaced by
+ * the fine means). */
+eb_status eb_amr_residual(eb_amr* A, const double* d_rhs_c, const double* d_sig_c, const double* d_rhs_f,
+                          const double* d_sig_f, const double* d_phi_c, const double* d_phi_f, double* d_r_c,
+                          double* d_r_f, void* stream);
+/* Composite solve to max|r| <= tol max|b| (opts of setup; max_cycles caps the
+ * composite iterations).  Each iteration: coarse correction over the domain
+ * (fine residual averaged under the box), constant per parent on the fine
+ * grid; then a fine correction on the box with zero Dirichlet data on its CF
+ * sides; both by the persistent multigrid solve to 1e-3.  d_phi_c / d_phi_f
+ * hold the guess on entry; on return d_phi_c under the box holds the fine
+ * means.  info: outer_iters = composite iterations, vcycles = V-cycles of the
+ * corrections. */
+eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double* d_sig_c, const double* d_rhs_f,
+                       const double* d_sig_f, double* d_phi_c, double* d_phi_f, eb_solve_info* info, void* stream);
+void eb_amr_destroy(eb_amr* A);
+
 /* ---------------------------------------------------------------- serving
  * Continuous-batching solve server (no counterpart in the paper, whose
  * solves run one per time step inside a plasma code).  Requests (a geometry

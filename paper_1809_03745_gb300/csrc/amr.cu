@@ -1,0 +1,499 @@
+// amr.cu -- composite two-level solve: one ratio-2 refined box over a coarse
+// grid (Sec. 3.3.2 runs its multigrid over refined levels; the coarse-fine
+// coupling follows the refluxing of Sec. 3.3).
+//
+// Composite operator (the same reading as the oracle's):
+//   * the fine box is a grid of its own whose coarse-fine (CF) sides are
+//     homogeneous Neumann walls; the CF flux eps0 (ghost - phi_F)/h_f times the
+//     fine aperture is added to each fine cell next to a CF side, the ghost by
+//     quadratic tangential then quadratic normal Lagrange steps (fallbacks to
+//     linear, then constant) precomputed per face at set-up;
+//   * a coarse cell outside the box next to a CF side loses the coarse
+//     operator's own flux through that face and gains minus the mean of the
+//     fine fluxes through it (refluxing: exact conservation);
+//   * coarse cells under the box carry no equation; where a coarse stencil
+//     reaches one, its value is the kappa-weighted mean of its children.
+// Solve: FAC-style defect correction on the device.  Each iteration forms the
+// composite FP64 residual, solves a coarse correction over the whole domain
+// (fine residuals averaged onto the coarse cells under the box) and adds it
+// (constant per parent on the fine grid), forms the residual again and
+// solves a fine correction on the box with zero Dirichlet data on its CF
+// sides.  Both corrections run the persistent multigrid kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "eb_internal.h"
+
+using namespace ebp;
+
+namespace {
+
+constexpr int TBA = 256;
+int nb(long long n) { return (int)std::max<long long>(1, (n + TBA - 1) / TBA); }
+
+struct BoxIdx {
+  int D;
+  int nc[3], nf[3], lo[3], hi[3];
+};
+
+__device__ __forceinline__ void ijk3(const int n[3], long long c, int I[3]) {
+  I[0] = (int)(c % n[0]);
+  I[1] = (int)((c / n[0]) % n[1]);
+  I[2] = (int)(c / ((long long)n[0] * n[1]));
+}
+__device__ __forceinline__ long long lin3(const int n[3], const int I[3]) {
+  return (long long)I[0] + (long long)n[0] * ((long long)I[1] + (long long)n[1] * I[2]);
+}
+__device__ __forceinline__ bool under_box(const BoxIdx& B, const int I[3]) {
+  for (int k = 0; k < B.D; ++k)
+    if (I[k] < B.lo[k] || I[k] >= B.hi[k]) return false;
+  return true;
+}
+
+// coarse values under the box: kappa-weighted mean of the children with the phase
+__global__ void k_avg_down(BoxIdx B, const uint8_t* cflags, const uint8_t* fflags, const double* kf, const double* pf,
+                           double* pc, long long ncc, long long nff) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncc) return;
+  int I[3];
+  ijk3(B.nc, c, I);
+  if (!under_box(B, I)) return;
+  for (int p = 0; p < 2; ++p) {
+    if (!((cflags[c] >> p) & 1)) {
+      pc[p * ncc + c] = 0.0;
+      continue;
+    }
+    double num = 0.0, den = 0.0;
+    for (int k = 0; k < (1 << B.D); ++k) {
+      int F[3] = {0, 0, 0};
+      for (int a = 0; a < B.D; ++a) F[a] = 2 * (I[a] - B.lo[a]) + ((k >> a) & 1);
+      long long f = lin3(B.nf, F);
+      if ((fflags[f] >> p) & 1) {
+        double w = kf[p * nff + f];
+        num += w * pf[p * nff + f];
+        den += w;
+      }
+    }
+    pc[p * ncc + c] = den > 0.0 ? num / den : 0.0;
+  }
+}
+
+// alpha_f times the CF flux out of the fine cell, per fine CF face
+__global__ void k_cf_flux(const CFFace* faces, long long nface, const double* pc, const double* pf, double eps0,
+                          double hf, double* fl) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nface) return;
+  const CFFace f = faces[t];
+  double v = 0.0;
+  if (f.al > 0.0) {
+    double tv = 0.0;
+    for (int k = 0; k < f.nc; ++k) tv += f.cw[k] * pc[f.cc[k]];
+    double ghost = f.wf * pf[f.fcell] + f.wc * tv;
+    if (f.f2 >= 0) ghost += f.wf2 * pf[f.f2];
+    v = f.al * eps0 * (ghost - pf[f.fcell]) / hf;
+  }
+  fl[t] = v;
+}
+
+// fine rows of one CF side (one face per fine cell within a side)
+__global__ void k_cf_fine_apply(const CFFace* faces, long long t0, long long t1, const double* fl, double hf,
+                                double* rf) {
+  long long t = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= t1) return;
+  const CFFace& f = faces[t];
+  if (f.al > 0.0) rf[f.fcell] += fl[t] / hf;
+}
+
+// coarse rows next to the box: take the coarse face flux out, put minus the
+// mean fine flux in
+__global__ void k_cf_coarse_apply(const CFCoarse* cf, long long n, const double* fl, const double* pc, long long ncc,
+                                  double hc, int D, double* rc) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const CFCoarse& c = cf[t];
+  if (c.ccell < 0) return;
+  double own = 0.0;
+  for (int k = 0; k < c.n; ++k) {
+    unsigned cl = (unsigned)c.col[k];
+    own += c.w[k] * pc[(long long)(cl >> 30) * ncc + (cl & 0x3fffffffu)];
+  }
+  double fsum = 0.0;
+  for (int k = 0; k < c.nfine; ++k) fsum += fl[c.fine[k]];
+  rc[c.ccell] += -own - fsum / (hc * (double)(1 << (D - 1)));
+}
+
+__global__ void k_zero_under(BoxIdx B, double* rc, long long ncc) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncc) return;
+  int I[3];
+  ijk3(B.nc, c, I);
+  if (under_box(B, I)) rc[c] = rc[ncc + c] = 0.0;
+}
+
+// coarse correction right-hand side under the box: mean fine residual of the
+// children carrying the phase
+__global__ void k_restrict_under(BoxIdx B, const uint8_t* fflags, const double* rf, double* rc, long long ncc,
+                                 long long nff) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncc) return;
+  int I[3];
+  ijk3(B.nc, c, I);
+  if (!under_box(B, I)) return;
+  for (int p = 0; p < 2; ++p) {
+    double s = 0.0;
+    int m = 0;
+    for (int k = 0; k < (1 << B.D); ++k) {
+      int F[3] = {0, 0, 0};
+      for (int a = 0; a < B.D; ++a) F[a] = 2 * (I[a] - B.lo[a]) + ((k >> a) & 1);
+      long long f = lin3(B.nf, F);
+      if ((fflags[f] >> p) & 1) {
+        s += rf[p * nff + f];
+        ++m;
+      }
+    }
+    rc[p * ncc + c] = m ? s / m : 0.0;
+  }
+}
+
+// phi_c += e_c outside the box; phi_f += e_c of the parent where the fine cell has the phase
+__global__ void k_add_coarse(BoxIdx B, const double* ec, double* pc, long long ncc) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncc) return;
+  int I[3];
+  ijk3(B.nc, c, I);
+  if (under_box(B, I)) return;
+  pc[c] += ec[c];
+  pc[ncc + c] += ec[ncc + c];
+}
+__global__ void k_prolong_const(BoxIdx B, const uint8_t* fflags, const double* ec, double* pf, long long ncc,
+                                long long nff) {
+  long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nff) return;
+  int F[3];
+  ijk3(B.nf, f, F);
+  int I[3] = {0, 0, 0};
+  for (int a = 0; a < B.D; ++a) I[a] = B.lo[a] + F[a] / 2;
+  long long c = lin3(B.nc, I);
+  for (int p = 0; p < 2; ++p)
+    if ((fflags[f] >> p) & 1) pf[p * nff + f] += ec[p * ncc + c];
+}
+__global__ void k_axpy_masked(const uint8_t* flags, long long n, const double* x, double* y) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  for (int p = 0; p < 2; ++p)
+    if ((flags[c] >> p) & 1) y[p * n + c] += x[p * n + c];
+}
+__global__ void k_absmax2(const uint8_t* flags, long long n, const double* v, unsigned long long* out) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double m = 0.0;
+  if (c < n)
+    for (int p = 0; p < 2; ++p)
+      if ((flags[c] >> p) & 1) m = fmax(m, fabs(v[p * n + c]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+}  // namespace
+
+struct eb_amr {
+  int D = 2;
+  BoxIdx B{};
+  CFBox cfb{};
+  eb_geom_desc dc{}, df{}, df0{};
+  std::vector<eb_prim> prims;
+  std::vector<eb_csg> nodes;
+  eb_geom *Gc = nullptr, *Gf = nullptr, *Gf0 = nullptr;
+  eb_poisson *Pc = nullptr, *Pf = nullptr, *Pf0 = nullptr;
+  eb_solver_opts o{};
+  long long ncc = 0, nff = 0, nface = 0, ncface = 0;
+  double hc = 0.0, hf = 0.0, eps0 = 1.0;
+  const uint8_t *cflags = nullptr, *fflags = nullptr;  // finest-level flags (owned by the geometries)
+  CFFace* faces = nullptr;
+  CFCoarse* cfaces = nullptr;
+  double *fl = nullptr, *kf = nullptr, *pcf = nullptr, *rc = nullptr, *rf = nullptr, *ec = nullptr, *ef = nullptr;
+  int* d_status = nullptr;
+  unsigned long long* d_norm = nullptr;
+  std::vector<void*> allocs;
+  long long bytes = 0;
+};
+
+static eb_status amr_fail(eb_amr* A, eb_status st) {
+  eb_amr_destroy(A);
+  return st;
+}
+
+extern "C" void eb_amr_destroy(eb_amr* A) {
+  if (!A) return;
+  cudaDeviceSynchronize();
+  eb_poisson_destroy(A->Pc);
+  eb_poisson_destroy(A->Pf);
+  eb_poisson_destroy(A->Pf0);
+  eb_geom_destroy(A->Gc);
+  eb_geom_destroy(A->Gf);
+  eb_geom_destroy(A->Gf0);
+  for (void* p : A->allocs) cudaFree(p);
+  delete A;
+}
+
+extern "C" eb_status eb_amr_setup(const eb_geom_desc* desc, const int box_lo[3], const int box_hi[3],
+                                  const eb_solver_opts* opts, void* stream, eb_amr** out) {
+  if (!desc || !box_lo || !box_hi || !out) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  eb_amr* A = new eb_amr();
+  A->D = desc->dim;
+  const int D = A->D;
+  if (D < 2 || D > 3) {
+    delete A;
+    set_error("dimension must be 2 or 3");
+    return EB_ERR_INVALID;
+  }
+  if (opts) A->o = *opts;
+  else eb_solver_opts_default(&A->o);
+  A->o.launch_mode = 0;
+  A->prims.assign(desc->prims, desc->prims + desc->n_prims);
+  A->nodes.assign(desc->nodes, desc->nodes + desc->n_nodes);
+  A->dc = *desc;
+  A->dc.prims = A->prims.data();
+  A->dc.nodes = A->nodes.data();
+  BoxIdx& B = A->B;
+  B.D = D;
+  for (int k = 0; k < 3; ++k) {
+    B.nc[k] = k < D ? desc->n[k] : 1;
+    B.lo[k] = k < D ? box_lo[k] : 0;
+    B.hi[k] = k < D ? box_hi[k] : 1;
+    B.nf[k] = k < D ? 2 * (B.hi[k] - B.lo[k]) : 1;
+    if (k < D && (B.lo[k] < 0 || B.hi[k] > B.nc[k] || B.hi[k] - B.lo[k] < 4 || (B.hi[k] - B.lo[k]) % 4)) {
+      delete A;
+      set_error("refined box must lie in the domain with sides a positive multiple of 4 coarse cells");
+      return EB_ERR_INVALID;
+    }
+  }
+  // fine grid descriptions: CF sides Neumann (operator) or zero Dirichlet (corrections)
+  A->df = A->dc;
+  for (int k = 0; k < D; ++k) {
+    A->df.n[k] = B.nf[k];
+    A->df.lo[k] = desc->lo[k] + B.lo[k] * desc->h;
+  }
+  A->df.h = desc->h / 2.0;
+  A->df0 = A->df;
+  for (int k = 0; k < D; ++k)
+    for (int s2 = 0; s2 < 2; ++s2) {
+      bool cf = s2 == 0 ? B.lo[k] > 0 : B.hi[k] < B.nc[k];
+      if (!cf) continue;
+      A->df.bc_type[2 * k + s2] = EB_BC_NEUMANN;
+      A->df.bc_value[2 * k + s2] = 0.0;
+      A->df0.bc_type[2 * k + s2] = EB_BC_DIRICHLET;
+      A->df0.bc_value[2 * k + s2] = 0.0;
+    }
+  A->df0.n_electrodes = desc->n_electrodes;
+  for (int e = 0; e < desc->n_electrodes; ++e) A->df0.electrode_phi[e] = 0.0;
+  eb_status st = eb_geom_build(&A->dc, stream, &A->Gc);
+  if (st == EB_OK) st = eb_geom_build(&A->df, stream, &A->Gf);
+  if (st == EB_OK) st = eb_geom_build(&A->df0, stream, &A->Gf0);
+  if (st != EB_OK) return amr_fail(A, st);
+  A->ncc = A->Gc->L[0].g.ncell;
+  A->nff = A->Gf->L[0].g.ncell;
+  A->hc = desc->h;
+  A->hf = desc->h / 2.0;
+  A->eps0 = desc->eps_gas;
+  A->cflags = A->Gc->L[0].flags;
+  A->fflags = A->Gf->L[0].flags;
+  // CF sides and face counts
+  CFBox& cb = A->cfb;
+  std::memset(&cb, 0, sizeof(cb));
+  for (int k = 0; k < 3; ++k) {
+    cb.lo[k] = B.lo[k];
+    cb.hi[k] = B.hi[k];
+  }
+  long long off = 0, coff = 0;
+  for (int a = 0; a < D; ++a)
+    for (int s2 = 0; s2 < 2; ++s2) {
+      bool cf = s2 == 0 ? B.lo[a] > 0 : B.hi[a] < B.nc[a];
+      if (!cf) continue;
+      long long nfa = 1, nca = 1;
+      for (int k = 0; k < D; ++k)
+        if (k != a) {
+          nfa *= B.nf[k];
+          nca *= B.hi[k] - B.lo[k];
+        }
+      cb.side_a[cb.nside] = a;
+      cb.side_s[cb.nside] = s2;
+      cb.off[cb.nside] = off;
+      cb.coff[cb.nside] = coff;
+      ++cb.nside;
+      off += nfa;
+      coff += nca;
+    }
+  cb.off[cb.nside] = off;
+  cb.coff[cb.nside] = coff;
+  A->nface = off;
+  A->ncface = coff;
+  auto alloc = [&](size_t bytes) { return dev_alloc(A->allocs, std::max<size_t>(bytes, 16), &A->bytes, &st); };
+  A->faces = (CFFace*)alloc(sizeof(CFFace) * off);
+  A->cfaces = (CFCoarse*)alloc(sizeof(CFCoarse) * coff);
+  A->fl = (double*)alloc(sizeof(double) * off);
+  A->kf = (double*)alloc(sizeof(double) * 2 * A->nff);
+  A->pcf = (double*)alloc(sizeof(double) * 2 * A->ncc);
+  A->rc = (double*)alloc(sizeof(double) * 2 * A->ncc);
+  A->ec = (double*)alloc(sizeof(double) * 2 * A->ncc);
+  A->rf = (double*)alloc(sizeof(double) * 2 * A->nff);
+  A->ef = (double*)alloc(sizeof(double) * 2 * A->nff);
+  A->d_status = (int*)alloc(sizeof(int));
+  A->d_norm = (unsigned long long*)alloc(sizeof(unsigned long long) * 2);
+  if (st != EB_OK) return amr_fail(A, st);
+  st = build_cf(A->Gf, A->Gc, cb, A->faces, A->cfaces, A->d_status, s);
+  if (st != EB_OK) return amr_fail(A, st);
+  eb_geom_arrays ga;
+  std::memset(&ga, 0, sizeof(ga));
+  ga.kappa = A->kf;
+  st = eb_geom_export(A->Gf, &ga, stream);
+  if (st == EB_OK) st = eb_poisson_setup(A->Gc, &A->o, stream, &A->Pc);
+  if (st == EB_OK) st = eb_poisson_setup(A->Gf, &A->o, stream, &A->Pf);
+  if (st == EB_OK) st = eb_poisson_setup(A->Gf0, &A->o, stream, &A->Pf0);
+  if (st != EB_OK) return amr_fail(A, st);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return amr_fail(A, cuda_fail(cudaGetLastError(), "amr setup"));
+  *out = A;
+  return EB_OK;
+}
+
+extern "C" eb_status eb_amr_query(const eb_amr* A, long long* n_coarse, long long* n_fine, int fine_n[3],
+                                  long long* cf_faces) {
+  if (!A) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  if (n_coarse) *n_coarse = A->ncc;
+  if (n_fine) *n_fine = A->nff;
+  if (fine_n)
+    for (int k = 0; k < 3; ++k) fine_n[k] = A->B.nf[k];
+  if (cf_faces) *cf_faces = A->nface;
+  return EB_OK;
+}
+
+// composite residual into A->rc / A->rf (phi_c values under the box are replaced by fine means)
+static eb_status amr_resid(eb_amr* A, const double* rhs_c, const double* sig_c, const double* rhs_f,
+                           const double* sig_f, const double* phi_c, const double* phi_f, cudaStream_t s) {
+  cudaMemcpyAsync(A->pcf, phi_c, 2 * A->ncc * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  k_avg_down<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->cflags, A->fflags, A->kf, phi_f, A->pcf, A->ncc, A->nff);
+  eb_status st = eb_poisson_residual(A->Pc, rhs_c, sig_c, A->pcf, A->rc, s);
+  if (st == EB_OK) st = eb_poisson_residual(A->Pf, rhs_f, sig_f, phi_f, A->rf, s);
+  if (st != EB_OK) return st;
+  if (A->nface) {
+    k_cf_flux<<<nb(A->nface), TBA, 0, s>>>(A->faces, A->nface, A->pcf, phi_f, A->eps0, A->hf, A->fl);
+    for (int sd = 0; sd < A->cfb.nside; ++sd) {
+      long long t0 = A->cfb.off[sd], t1 = A->cfb.off[sd + 1];
+      k_cf_fine_apply<<<nb(t1 - t0), TBA, 0, s>>>(A->faces, t0, t1, A->fl, A->hf, A->rf);
+    }
+    k_cf_coarse_apply<<<nb(A->ncface), TBA, 0, s>>>(A->cfaces, A->ncface, A->fl, A->pcf, A->ncc, A->hc, A->D,
+                                                     A->rc);
+  }
+  k_zero_under<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->rc, A->ncc);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? EB_OK : cuda_fail(e, "composite residual");
+}
+
+static eb_status amr_norm(eb_amr* A, cudaStream_t s, double* out) {
+  cudaMemsetAsync(A->d_norm, 0, sizeof(unsigned long long), s);
+  k_absmax2<<<nb(A->ncc), TBA, 0, s>>>(A->cflags, A->ncc, A->rc, A->d_norm);
+  k_absmax2<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, A->rf, A->d_norm);
+  unsigned long long v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, A->d_norm, sizeof(v), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "composite norm");
+  std::memcpy(out, &v, sizeof(double));
+  return EB_OK;
+}
+
+extern "C" eb_status eb_amr_residual(eb_amr* A, const double* d_rhs_c, const double* d_sig_c, const double* d_rhs_f,
+                                     const double* d_sig_f, const double* d_phi_c, const double* d_phi_f,
+                                     double* d_r_c, double* d_r_f, void* stream) {
+  if (!A || !d_rhs_c || !d_rhs_f || !d_phi_c || !d_phi_f || !d_r_c || !d_r_f) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  eb_status st = amr_resid(A, d_rhs_c, d_sig_c, d_rhs_f, d_sig_f, d_phi_c, d_phi_f, s);
+  if (st != EB_OK) return st;
+  cudaMemcpyAsync(d_r_c, A->rc, 2 * A->ncc * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(d_r_f, A->rf, 2 * A->nff * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? EB_OK : cuda_fail(e, "composite residual");
+}
+
+extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double* d_sig_c, const double* d_rhs_f,
+                                  const double* d_sig_f, double* d_phi_c, double* d_phi_f, eb_solve_info* info,
+                                  void* stream) {
+  if (!A || !d_rhs_c || !d_rhs_f || !d_phi_c || !d_phi_f) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  eb_solve_info inf;
+  std::memset(&inf, 0, sizeof(inf));
+  // ||b||: the composite residual at phi = 0
+  cudaMemsetAsync(A->ec, 0, 2 * A->ncc * sizeof(double), s);
+  cudaMemsetAsync(A->ef, 0, 2 * A->nff * sizeof(double), s);
+  eb_status st = amr_resid(A, d_rhs_c, d_sig_c, d_rhs_f, d_sig_f, A->ec, A->ef, s);
+  double bn = 0.0, r = 0.0;
+  if (st == EB_OK) st = amr_norm(A, s, &bn);
+  const double inner_tol = 1e-3;
+  int it = 0, cycles = 0;
+  const int max_it = std::max(1, A->o.max_cycles);
+  st = st == EB_OK ? EB_ERR_NOT_CONVERGED : st;
+  while (st == EB_ERR_NOT_CONVERGED && it < max_it) {
+    eb_status s2 = amr_resid(A, d_rhs_c, d_sig_c, d_rhs_f, d_sig_f, d_phi_c, d_phi_f, s);
+    if (s2 == EB_OK) s2 = amr_norm(A, s, &r);
+    if (s2 != EB_OK) {
+      st = s2;
+      break;
+    }
+    if (bn == 0.0 || r <= A->o.tol * bn) {
+      st = EB_OK;
+      break;
+    }
+    if (!(r == r) || r > 1e6 * bn) break;
+    // coarse correction over the whole domain
+    k_restrict_under<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->fflags, A->rf, A->rc, A->ncc, A->nff);
+    int cyc = 0;
+    s2 = poisson_solve_b(A->Pc, A->rc, A->ec, inner_tol, &cyc, s);
+    cycles += cyc;
+    if (s2 != EB_OK) {
+      st = s2;
+      break;
+    }
+    k_add_coarse<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->ec, d_phi_c, A->ncc);
+    k_prolong_const<<<nb(A->nff), TBA, 0, s>>>(A->B, A->fflags, A->ec, d_phi_f, A->ncc, A->nff);
+    // fine correction on the box
+    s2 = amr_resid(A, d_rhs_c, d_sig_c, d_rhs_f, d_sig_f, d_phi_c, d_phi_f, s);
+    if (s2 == EB_OK) s2 = poisson_solve_b(A->Pf0, A->rf, A->ef, inner_tol, &cyc, s);
+    cycles += cyc;
+    if (s2 != EB_OK) {
+      st = s2;
+      break;
+    }
+    k_axpy_masked<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, A->ef, d_phi_f);
+    ++it;
+  }
+  // report phi_c under the box as the fine means
+  if (st == EB_OK || st == EB_ERR_NOT_CONVERGED) {
+    k_avg_down<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->cflags, A->fflags, A->kf, d_phi_f, d_phi_c, A->ncc, A->nff);
+    if (st == EB_ERR_NOT_CONVERGED) set_error("composite iteration cap reached");
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess && st == EB_OK) st = cuda_fail(e, "composite solve");
+  inf.status = st;
+  inf.outer_iters = it;
+  inf.vcycles = cycles;
+  inf.bnorm = bn;
+  inf.rel_res = bn > 0.0 ? r / bn : 0.0;
+  if (info) *info = inf;
+  return st;
+}

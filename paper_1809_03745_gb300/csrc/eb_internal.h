@@ -52,6 +52,46 @@ struct eb_geom {
 
 namespace ebp {
 
+// ------------------------------------------------- composite (one refined box)
+// Box of coarse cells [lo, hi) refined by 2 and its coarse-fine (CF) sides.
+struct CFBox {
+  int lo[3], hi[3];
+  int nside;
+  int side_a[6], side_s[6];  // normal axis, 0 = low side / 1 = high side of the box
+  long long off[7];          // first fine CF face of each side
+  long long coff[7];         // first coarse CF face of each side
+};
+
+// One fine face on a CF side: the ghost value behind it is
+// wf phi_F + wf2 phi_F2 + wc sum_k cw_k phi_coarse(cc_k); al = 0 marks a face
+// without flux.
+struct CFFace {
+  int fcell, f2;  // fine cell, fine cell 3/2 h_f inside (-1: linear normal step)
+  int ccell;      // coarse cell across the face
+  int nc;
+  int cc[5];
+  double cw[5];
+  double wf, wf2, wc, al;
+};
+
+// One coarse face on a CF side: the coarse cell outside the box (-1 when it
+// has no gas unknown), its fine faces, and the coarse operator's own flux
+// through the face as it enters the cell's row (sum w phi[col], cols encoded
+// (phase << 30 | cell)).
+struct CFCoarse {
+  int ccell;
+  int nfine;
+  int fine[4];
+  int n;
+  int col[24];
+  double w[24];
+};
+
+// Builds the CF face lists on the device from the fine (box) and coarse
+// finest levels; EB_ERR_UNSUPPORTED when a dielectric unknown touches a CF side.
+eb_status build_cf(const eb_geom* Gf, const eb_geom* Gc, const CFBox& B, CFFace* faces, CFCoarse* cfaces,
+                   int* d_status, cudaStream_t s);
+
 // error reporting
 void set_error(const std::string& msg);
 eb_status cuda_fail(cudaError_t e, const char* what);
@@ -81,3 +121,4 @@ eb_status batch_step(eb_poisson* const* P, int n, const double* const* rhs, cons
 void batch_info(eb_poisson* Q, eb_solve_info* inf);
 eb_status batch_copy_out(eb_poisson* P, double* phi, cudaStream_t s);
 long long poisson_device_bytes(const eb_poisson* P);
+eb_status poisson_solve_b(eb_poisson* P, const double* d_b, double* d_x, double tol, int* cycles, cudaStream_t user);

@@ -500,6 +500,158 @@ __global__ void k_export_eb(LevelGeom L, const int* eb_q, long long n_eb, const 
     for (int p = 0; p < 2; ++p) ord[2 * i + p] = ((L.flags[L.R.cell[q]] >> p) & 1) ? order[p * nq + q] : 0;
 }
 
+// ------------------------------------------------- composite CF faces
+
+__device__ void cf_side_of(const CFBox& B, const long long* off, long long t, int& side, long long& local) {
+  side = 0;
+  while (side + 1 < B.nside && t >= off[side + 1]) ++side;
+  local = t - off[side];
+}
+
+__device__ void cf_tangential(int D, int a, int t[2]) {
+  int k = 0;
+  for (int d = 0; d < D; ++d)
+    if (d != a) t[k++] = d;
+  if (D == 2) t[1] = 2;
+}
+
+// a coarse cell the tangential interpolation may use (gas unknown, not cut,
+// inside the domain and outside the box)
+__device__ bool cf_coarse_ok(const LevelGeom& Lc, const CFBox& B, const int I[3]) {
+  const Grid& g = Lc.g;
+  bool under = true;
+  for (int k = 0; k < g.D; ++k) {
+    if (I[k] < 0 || I[k] >= g.n[k]) return false;
+    if (I[k] < B.lo[k] || I[k] >= B.hi[k]) under = false;
+  }
+  if (under) return false;
+  long long c = cell_index(g, I[0], I[1], I[2]);
+  return (Lc.flags[c] & 1) && Lc.cut_of_cell[c] < 0;
+}
+
+__device__ bool cf_fine_ok(const LevelGeom& Lf, const int I[3]) {
+  const Grid& g = Lf.g;
+  for (int k = 0; k < g.D; ++k)
+    if (I[k] < 0 || I[k] >= g.n[k]) return false;
+  long long c = cell_index(g, I[0], I[1], I[2]);
+  return (Lf.flags[c] & 1) && Lf.cut_of_cell[c] < 0;
+}
+
+__global__ void k_cf_fine(LevelGeom Lf, LevelGeom Lc, CFBox B, CFFace* faces, int* status) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B.off[B.nside]) return;
+  int side;
+  long long loc;
+  cf_side_of(B, B.off, t, side, loc);
+  const int D = Lf.g.D, a = B.side_a[side], s = B.side_s[side];
+  int tg[2];
+  cf_tangential(D, a, tg);
+  int FI[3] = {0, 0, 0};
+  FI[a] = s ? Lf.g.n[a] - 1 : 0;
+  FI[tg[0]] = (int)(loc % Lf.g.n[tg[0]]);
+  if (D == 3) FI[tg[1]] = (int)(loc / Lf.g.n[tg[0]]);
+  int CI[3] = {0, 0, 0};
+  for (int k = 0; k < D; ++k) CI[k] = B.lo[k] + FI[k] / 2;
+  CI[a] += s ? 1 : -1;
+  CFFace f;
+  f.fcell = (int)cell_index(Lf.g, FI[0], FI[1], FI[2]);
+  f.ccell = (int)cell_index(Lc.g, CI[0], CI[1], CI[2]);
+  f.f2 = -1;
+  f.nc = 0;
+  f.wf = f.wf2 = f.wc = f.al = 0.0;
+  const uint8_t ff = Lf.flags[f.fcell], fcf = Lc.flags[f.ccell];
+  if ((ff & 2) || (fcf & 2)) atomicExch(status, 1);  // a dielectric unknown at a CF side
+  FaceInfo fi;
+  int J[3] = {FI[0], FI[1], FI[2]};
+  J[a] += s;
+  if ((ff & 1) && (fcf & 1) && face_open(Lf, a, J, 0, fi)) {
+    f.al = fi.al;
+    // tangential value: phi_C plus one 1-D correction per tangential axis
+    f.nc = 1;
+    f.cc[0] = f.ccell;
+    f.cw[0] = 1.0;
+    for (int q = 0; q < D - 1; ++q) {
+      const int k = tg[q];
+      const double o = (FI[k] % 2 == 0) ? -0.25 : 0.25;
+      int lo_I[3] = {CI[0], CI[1], CI[2]}, hi_I[3] = {CI[0], CI[1], CI[2]};
+      lo_I[k] -= 1;
+      hi_I[k] += 1;
+      if (cf_coarse_ok(Lc, B, lo_I) && cf_coarse_ok(Lc, B, hi_I)) {
+        f.cc[f.nc] = (int)cell_index(Lc.g, lo_I[0], lo_I[1], lo_I[2]);
+        f.cw[f.nc++] = o * (o - 1.0) / 2.0;
+        f.cw[0] = f.cw[0] + ((1.0 - o * o) - 1.0);
+        f.cc[f.nc] = (int)cell_index(Lc.g, hi_I[0], hi_I[1], hi_I[2]);
+        f.cw[f.nc++] = o * (o + 1.0) / 2.0;
+      } else {
+        const int* sd = o > 0.0 ? hi_I : lo_I;
+        if (cf_coarse_ok(Lc, B, sd)) {
+          f.cw[0] = f.cw[0] + (-0.25);
+          f.cc[f.nc] = (int)cell_index(Lc.g, sd[0], sd[1], sd[2]);
+          f.cw[f.nc++] = 0.25;
+        }
+      }
+    }
+    int F2[3] = {FI[0], FI[1], FI[2]};
+    F2[a] += s ? -1 : 1;
+    if (cf_fine_ok(Lf, F2)) {
+      f.f2 = (int)cell_index(Lf.g, F2[0], F2[1], F2[2]);
+      f.wf = 2.0 / 3.0;
+      f.wf2 = -1.0 / 5.0;
+      f.wc = 8.0 / 15.0;
+    } else {
+      f.wf = 1.0 / 3.0;
+      f.wc = 2.0 / 3.0;
+    }
+  }
+  faces[t] = f;
+}
+
+__global__ void k_cf_coarse2(LevelGeom Lc, CFBox B, int nf0, int nf1, int nf2, CFCoarse* out, int* status) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B.coff[B.nside]) return;
+  int side;
+  long long loc;
+  cf_side_of(B, B.coff, t, side, loc);
+  const int D = Lc.g.D, a = B.side_a[side], s = B.side_s[side];
+  const int nf[3] = {nf0, nf1, nf2};
+  int tg[2];
+  cf_tangential(D, a, tg);
+  const int w0 = B.hi[tg[0]] - B.lo[tg[0]];
+  const int U = (int)(loc % w0), V = D == 3 ? (int)(loc / w0) : 0;
+  int CI[3] = {0, 0, 0};
+  CI[a] = s ? B.hi[a] : B.lo[a] - 1;
+  CI[tg[0]] = B.lo[tg[0]] + U;
+  if (D == 3) CI[tg[1]] = B.lo[tg[1]] + V;
+  CFCoarse c;
+  c.ccell = -1;
+  c.nfine = 0;
+  c.n = 0;
+  const long long cc = cell_index(Lc.g, CI[0], CI[1], CI[2]);
+  for (int j = 0; j < (D == 3 ? 2 : 1); ++j)
+    for (int i = 0; i < 2; ++i) {
+      long long u = 2 * U + i, v = 2 * V + j;
+      c.fine[c.nfine++] = (int)(B.off[side] + u + (D == 3 ? (long long)nf[tg[0]] * v : 0));
+    }
+  if (Lc.flags[cc] & 1) {
+    c.ccell = (int)cc;
+    int JC[3] = {CI[0], CI[1], CI[2]};
+    if (s == 0) JC[a] += 1;  // the cell below the box: its high face
+    FaceInfo fi;
+    if (face_open(Lc, a, JC, 0, fi)) {
+      Form<24> R;
+      R.zero();
+      add_centroid_flux(Lc, a, JC, 0, (s == 0 ? 1.0 : -1.0) * fi.al / Lc.g.h, R);
+      if (R.overflow) atomicExch(status, 2);
+      c.n = R.n;
+      for (int k = 0; k < R.n; ++k) {
+        c.col[k] = R.col[k];
+        c.w[k] = R.w[k];
+      }
+    }
+  }
+  out[t] = c;
+}
+
 // ------------------------------------------------------------------ host
 
 static LevelGeom view(const DevLevel& L) {
@@ -746,6 +898,31 @@ eb_status launch_field(const eb_geom* G, const double* phi, const double* sigma,
   if (En && L.n_eb) k_field_eb<<<nblk(L.n_eb, 64), 64, 0, s>>>(v, L.eb_q, L.n_eb, phi, sigma, En);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? EB_OK : cuda_fail(e, "field");
+}
+
+eb_status build_cf(const eb_geom* Gf, const eb_geom* Gc, const CFBox& B, CFFace* faces, CFCoarse* cfaces,
+                   int* d_status, cudaStream_t s) {
+  const DevLevel& F = Gf->L[0];
+  const DevLevel& C = Gc->L[0];
+  cudaMemsetAsync(d_status, 0, sizeof(int), s);
+  if (B.off[B.nside] > 0)
+    k_cf_fine<<<nblk(B.off[B.nside]), TB, 0, s>>>(view(F), view(C), B, faces, d_status);
+  if (B.coff[B.nside] > 0)
+    k_cf_coarse2<<<nblk(B.coff[B.nside], 64), 64, 0, s>>>(view(C), B, F.g.n[0], F.g.n[1], F.g.n[2], cfaces,
+                                                          d_status);
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "coarse-fine faces");
+  if (h == 1) {
+    set_error("a dielectric unknown touches a coarse-fine side of the refined box");
+    return EB_ERR_UNSUPPORTED;
+  }
+  if (h == 2) {
+    set_error("coarse face flux stencil too long");
+    return EB_ERR_UNSUPPORTED;
+  }
+  return check(s, "coarse-fine faces");
 }
 
 eb_status export_geometry(const eb_geom* G, eb_geom_arrays* out, cudaStream_t s) {

@@ -371,6 +371,20 @@ __global__ void k_update64(Op<double> o, const float* e0, const float* e1) {
 }
 
 // masked copy of a [2][ncell] field: entries without an unknown become 0
+// max |v| over the entries that carry an unknown, into *out (bit pattern of a
+// non-negative double, so an integer atomicMax orders it)
+__global__ void k_absmax_masked(const uint8_t* flags, long long ncell, const double* v, unsigned long long* out) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double m = 0.0;
+  if (c < ncell) {
+    uint8_t f = flags[c];
+    for (int p = 0; p < 2; ++p)
+      if ((f >> p) & 1) m = fmax(m, fabs(v[p * ncell + c]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
 __global__ void k_copy_masked(const uint8_t* flags, long long ncell, const double* src, double* dst) {
   long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;

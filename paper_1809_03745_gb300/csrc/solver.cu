@@ -983,6 +983,36 @@ eb_status batch_copy_out(eb_poisson* P, double* phi, cudaStream_t s) {
 
 long long poisson_device_bytes(const eb_poisson* P) { return P->bytes; }
 
+// A x = b for a right-hand side given in integrated form (boundary data not
+// added: a correction equation with homogeneous data), from x = 0, to
+// max|r| <= tol max|b|.  d_b and d_x are [2][ncell] on `user`'s stream.
+eb_status poisson_solve_b(eb_poisson* P, const double* d_b, double* d_x, double tol, int* cycles, cudaStream_t user) {
+  if (!P->persistent) {
+    set_error("correction solves need the persistent path");
+    return EB_ERR_UNSUPPORTED;
+  }
+  const DevLevel& F = P->G->L[0];
+  long long n = F.g.ncell;
+  join_in(P, user);
+  k_copy_masked<<<blocks(n), 256, 0, P->s>>>(F.flags, n, d_b, P->b64);
+  cudaMemsetAsync(P->d_norm + 1, 0, sizeof(unsigned long long), P->s);
+  k_absmax_masked<<<blocks(n), 256, 0, P->s>>>(F.flags, n, P->b64, P->d_norm + 1);
+  cudaMemsetAsync(P->phi64, 0, 2 * n * sizeof(double), P->s);
+  double keep = P->o.tol;
+  P->o.tol = tol;
+  double r = 0.0;
+  int iters = 0, cyc = 0, status = 0;
+  eb_status st = solve_persistent(P, &r, &iters, &cyc, &status);
+  P->o.tol = keep;
+  if (st == EB_OK && status != EB_OK && status != EB_ERR_NOT_CONVERGED) st = (eb_status)status;
+  k_copy_masked<<<blocks(n), 256, 0, P->s>>>(F.flags, n, P->phi64, d_x);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess && st == EB_OK) st = cuda_fail(e, "correction solve");
+  join_out(P, user);
+  if (cycles) *cycles = cyc;
+  return st;
+}
+
 // One cooperative launch over instances that share precision and device.
 // fresh: assemble b and copy the guess in first; max_iters: outer iterations
 // allowed (0: until convergence).  Results (status, iterations, V-cycles,

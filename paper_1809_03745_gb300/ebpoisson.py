@@ -84,7 +84,8 @@ EXPORTS = ["eb_status_str", "eb_last_error", "eb_geom_build", "eb_geom_query", "
            "eb_solver_opts_default", "eb_poisson_setup", "eb_poisson_destroy", "eb_poisson_residual",
            "eb_poisson_solve", "eb_field_eval", "eb_poisson_profile", "eb_poisson_trace",
            "eb_poisson_residual_noalloc", "eb_poisson_solve_batched", "eb_server_opts_default", "eb_server_create",
-           "eb_server_submit", "eb_server_poll", "eb_server_wait", "eb_server_query", "eb_server_destroy"]
+           "eb_server_submit", "eb_server_poll", "eb_server_wait", "eb_server_query", "eb_server_destroy",
+           "eb_amr_setup", "eb_amr_query", "eb_amr_residual", "eb_amr_solve", "eb_amr_destroy"]
 
 
 def lib_path() -> str:
@@ -132,6 +133,17 @@ def load(build_if_missing: bool = False):
         lib.eb_poisson_trace.argtypes = [P, C.POINTER(C.c_double), C.c_int]
         lib.eb_poisson_profile.restype = C.c_int
         lib.eb_poisson_profile.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), P]
+        lib.eb_amr_setup.restype = C.c_int
+        lib.eb_amr_setup.argtypes = [C.POINTER(GeomDesc), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.POINTER(SolverOpts), P, C.POINTER(P)]
+        lib.eb_amr_query.restype = C.c_int
+        lib.eb_amr_query.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_longlong)]
+        lib.eb_amr_residual.restype = C.c_int
+        lib.eb_amr_residual.argtypes = [P] + [P] * 8 + [P]
+        lib.eb_amr_solve.restype = C.c_int
+        lib.eb_amr_solve.argtypes = [P] + [P] * 6 + [C.POINTER(SolveInfo), P]
+        lib.eb_amr_destroy.argtypes = [P]
         lib.eb_server_opts_default.argtypes = [C.POINTER(ServerOpts)]
         lib.eb_server_create.restype = C.c_int
         lib.eb_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(P)]
@@ -491,6 +503,71 @@ class Server:
     def close(self):
         if getattr(self, "_h", None):
             load().eb_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Composite:
+    """Composite grid: one ratio-2 refined box over coarse cells [box_lo, box_hi) (owns an eb_amr)."""
+
+    def __init__(self, desc: dict, box_lo, box_hi, *, precision="mixed", tol=1e-10, max_cycles=100, nu1=-1, nu2=-1,
+                 inner_cycles=2, device=None, stream=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        d, keep = make_desc(desc)
+        o = eb_solver_opts_default()
+        o.tol, o.max_cycles, o.nu1, o.nu2 = tol, max_cycles, nu1, nu2
+        o.precision = EB_PREC_MIXED if precision == "mixed" else EB_PREC_FP64
+        o.inner_cycles = inner_cycles
+        lo = (C.c_int * 3)(*[int(v) for v in (list(box_lo) + [0] * 3)[:3]])
+        hi = (C.c_int * 3)(*[int(v) for v in (list(box_hi) + [1] * 3)[:3]])
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(load().eb_amr_setup(C.byref(d), lo, hi, C.byref(o), _stream(stream), C.byref(h)), "eb_amr_setup")
+        self._h = h
+        nc, nf, nfa = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        fn = (C.c_int * 3)()
+        _check(load().eb_amr_query(h, C.byref(nc), C.byref(nf), fn, C.byref(nfa)), "eb_amr_query")
+        self.n_coarse, self.n_fine, self.fine_n, self.cf_faces = nc.value, nf.value, tuple(fn), nfa.value
+
+    def _f(self, x, n):
+        if x is None:
+            return None
+        x = _dev(x, torch.float64, self.device)
+        if x.dim() == 1 and x.numel() == n:
+            return x.contiguous()
+        return x.reshape(2, n).contiguous()
+
+    def residual(self, rhs_c, sig_c, rhs_f, sig_f, phi_c, phi_f, stream=None):
+        nc, nf = self.n_coarse, self.n_fine
+        args = [self._f(rhs_c, nc), self._f(sig_c, nc), self._f(rhs_f, nf), self._f(sig_f, nf),
+                self._f(phi_c, nc), self._f(phi_f, nf)]
+        rc = torch.empty(2, nc, dtype=torch.float64, device=self.device)
+        rf = torch.empty(2, nf, dtype=torch.float64, device=self.device)
+        _check(load().eb_amr_residual(self._h, *[_ptr(a) for a in args], _ptr(rc), _ptr(rf), _stream(stream)),
+               "eb_amr_residual")
+        return rc, rf
+
+    def solve(self, rhs_c, rhs_f, sig_c=None, sig_f=None, phi_c=None, phi_f=None, stream=None):
+        nc, nf = self.n_coarse, self.n_fine
+        pc = torch.zeros(2, nc, dtype=torch.float64, device=self.device) if phi_c is None else self._f(phi_c, nc)
+        pf = torch.zeros(2, nf, dtype=torch.float64, device=self.device) if phi_f is None else self._f(phi_f, nf)
+        info = SolveInfo()
+        # keep the converted inputs alive until the call returns
+        ins = [self._f(rhs_c, nc), self._f(sig_c, nc), self._f(rhs_f, nf), self._f(sig_f, nf)]
+        st = load().eb_amr_solve(self._h, *[_ptr(a) for a in ins], _ptr(pc), _ptr(pf), C.byref(info),
+                                 _stream(stream))
+        if st not in (EB_OK, EB_ERR_NOT_CONVERGED):
+            _check(st, "eb_amr_solve")
+        return pc, pf, _info_dict(info)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().eb_amr_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -176,15 +176,44 @@ def pin_plane_3d(n=256, *, tip_z=0.5, radius=0.02, V=1.0, disk=True, eps_d=3.0, 
                  [0.0, 0.0, 0.0, 0.0, 0.0, V])
 
 
+def line_charge(x, y, z, peak=1e3):
+    """Gaussian line charge of radius 0.02 along the pin axis for z in [0.05, 0.5]."""
+    r2 = (x - 0.5) ** 2 + (y - 0.5) ** 2
+    dz = np.where(z < 0.05, 0.05 - z, np.where(z > 0.5, z - 0.5, 0.0))
+    return peak * np.exp(-r2 / (2 * 0.02 ** 2)) * np.exp(-dz ** 2 / (2 * 0.02 ** 2))
+
+
 def c3_inputs(n=256, seed=SEED_BASE + 3, peak=1e3):
     desc = pin_plane_3d(n)
     x, y, z = cell_centres(desc)
-    r2 = (x - 0.5) ** 2 + (y - 0.5) ** 2
-    dz = np.where(z < 0.05, 0.05 - z, np.where(z > 0.5, z - 0.5, 0.0))
-    s = peak * np.exp(-r2 / (2 * 0.02 ** 2)) * np.exp(-dz ** 2 / (2 * 0.02 ** 2))
+    s = line_charge(x, y, z, peak)
     S = np.zeros((2, s.size))
     S[0] = s
     return desc, S, np.zeros(s.size)
+
+
+def refined_box_desc(desc, box_lo, box_hi):
+    """The fine grid of a ratio-2 box over coarse cells [box_lo, box_hi) (for cell centres)."""
+    D = desc["dim"]
+    n = [2 * (box_hi[k] - box_lo[k]) if k < D else 1 for k in range(3)]
+    lo = [desc["lo"][k] + box_lo[k] * desc["h"] if k < D else 0.0 for k in range(3)]
+    return dict(desc, n=tuple(n), lo=tuple(lo), h=desc["h"] / 2.0)
+
+
+def c3_amr_inputs(n=256, peak=1e3, box_frac=(0.375, 0.625)):
+    """The 3D pin-plane workload with a ratio-2 refined box around the tip:
+    coarse cells [3n/8, 5n/8)^3 (physical [0.375, 0.625]^3), so 256^3 + 128^3.
+    Returns (desc, box_lo, box_hi, S_c, sig_c, S_f, sig_f)."""
+    desc = pin_plane_3d(n)
+    lo = [int(round(box_frac[0] * n))] * 3
+    hi = [int(round(box_frac[1] * n))] * 3
+    x, y, z = cell_centres(desc)
+    Sc = np.zeros((2, x.size))
+    Sc[0] = line_charge(x, y, z, peak)
+    xf, yf, zf = cell_centres(refined_box_desc(desc, lo, hi))
+    Sf = np.zeros((2, xf.size))
+    Sf[0] = line_charge(xf, yf, zf, peak)
+    return desc, lo, hi, Sc, np.zeros(x.size), Sf, np.zeros(xf.size)
 
 
 # --------------------------------------------------------------- batched instances
