@@ -266,7 +266,11 @@ eb_status eb_field_eval(eb_poisson* P, const double* d_phi, const double* d_sigm
 eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, double* ms_per_launch, double* bytes_per_launch,
                              void* stream);
 /* kernel 2 of eb_poisson_profile times `reps` grid barriers of the persistent
- * solve kernel (bytes_per_launch receives the number of CTAs). */
+ * solve kernel (bytes_per_launch receives the number of CTAs).  kernel 3 is
+ * the bounded-wait self-test: two CTAs wait at a grid barrier sized for
+ * three, so the wait ends only by its clock bound (about 2 s); the call then
+ * returns EB_ERR_TIMEOUT with ms_per_launch the kernel's duration, and the
+ * context stays usable. */
 
 /* Diagnostics (no counterpart in the paper): the phases of the first V-cycle
  * of the last persistent solve.  out[0] = number of phases m; then for each

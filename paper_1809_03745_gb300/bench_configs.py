@@ -1,0 +1,124 @@
+"""Measures every workload configuration on one GPU and prints one JSON line each.
+
+  C1  2D rod-plane 128^2, single phase: FP64 V-cycles and mixed precision
+  C2  2D multi-material 1024^2: FP64 V-cycles against FP32 V-cycles in FP64
+      defect correction, and the plain multi-launch FP64 path
+  C3  3D pin-plane 256^3 with a ratio-2 128^3 box around the tip (composite
+      solve), and the 256^3 single level
+  C4  64 seeded instances (2D 64^2..1024^2, 3D 32^3..192^3): one batched
+      persistent launch (mixed) against one-at-a-time solves, plain FP64
+      multi-launch and mixed persistent
+
+Times are wall-clock around the solve calls after warm-up (device work
+synchronised on both sides); inputs are resident on the device; all solves
+run to max|r| <= 1e-10 max|b|.
+
+Usage: python -m paper_1809_03745_gb300.bench_configs [--only C1 C2 C3 C4]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import ebpoisson as E
+from . import workloads as W
+
+
+def _timed(fn, reps=3):
+    fn()
+    best, out = float("inf"), None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        best = min(best, time.perf_counter() - t)
+    return best, out
+
+
+def single(name, desc, S, sig, **kw):
+    g = E.Geometry(desc)
+    P = E.Poisson(g, **kw)
+    rhs, sg = torch.from_numpy(S).cuda(), torch.from_numpy(sig).cuda()
+    dt, (phi, info) = _timed(lambda: P.solve(rhs, sg))
+    n = W.ncells(desc)
+    return {"config": name, "cells": n, "ms": dt * 1e3, "cells_per_s": n / dt, "vcycles": info["vcycles"],
+            "outer": info["outer_iters"], "rel_res": info["rel_res"], "status": info["status"],
+            "opts": {k: v for k, v in kw.items()}}
+
+
+def c1():
+    d, S, sig = W.c1_inputs(128)
+    yield single("C1 128^2 FP64", d, S, sig, precision="fp64", tol=1e-10, max_cycles=200)
+    yield single("C1 128^2 mixed", d, S, sig, precision="mixed", tol=1e-10, max_cycles=200)
+
+
+def c2():
+    d, S, sig = W.c2_inputs(1024)
+    yield single("C2 1024^2 FP64 V-cycles (persistent)", d, S, sig, precision="fp64", tol=1e-10, max_cycles=200)
+    yield single("C2 1024^2 FP32 V-cycles in FP64 defect correction (persistent)", d, S, sig, precision="mixed",
+                 tol=1e-10, max_cycles=200)
+    yield single("C2 1024^2 FP64 plain multi-launch", d, S, sig, precision="fp64", tol=1e-10, max_cycles=200,
+                 launch_mode=2)
+
+
+def c3():
+    d, lo, hi, Sc, sc, Sf, sf = W.c3_amr_inputs(256)
+    t = time.perf_counter()
+    G = E.Composite(d, lo, hi, precision="mixed", tol=1e-10, max_cycles=200)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t
+    args = [torch.from_numpy(a).cuda() for a in (Sc, Sf, sc, sf)]
+    dt, (pc, pf, info) = _timed(lambda: G.solve(*args), reps=2)
+    n = 256 ** 3 - 64 ** 3 + 128 ** 3
+    yield {"config": "C3 256^3 + 128^3 box composite, mixed", "cells": n, "ms": dt * 1e3, "cells_per_s": n / dt,
+           "composite_iters": info["outer_iters"], "vcycles": info["vcycles"], "rel_res": info["rel_res"],
+           "status": info["status"], "setup_s": setup}
+    del G, args
+    dd, S, sig = W.c3_inputs(256)
+    yield single("C3 256^3 single level, mixed", dd, S, sig, precision="mixed", tol=1e-10, max_cycles=400)
+
+
+def c4(count=64):
+    inst = W.batched_instances(count=count)
+    cells = sum(W.ncells(d) for d, _, _ in inst)
+    geoms = [E.Geometry(d) for d, _, _ in inst]
+    rhs = [torch.from_numpy(S).cuda() for _, S, _ in inst]
+    sig = [torch.from_numpy(s).cuda() for _, _, s in inst]
+    Pb = [E.Poisson(g, precision="mixed", tol=1e-10, max_cycles=600) for g in geoms]
+    dt, (phis, infos) = _timed(lambda: E.solve_batched(Pb, rhs, sig), reps=2)
+    yield {"config": f"C4 {count} instances, one batched persistent launch, mixed", "cells": cells,
+           "ms": dt * 1e3, "cells_per_s": cells / dt, "statuses": sorted(set(i["status"] for i in infos)),
+           "max_vcycles": max(i["vcycles"] for i in infos), "kernel_ms": infos[0]["kernel_ms"],
+           "n_2d": sum(d["dim"] == 2 for d, _, _ in inst)}
+
+    def one_by_one(Ps):
+        return [P.solve(rhs[k], sig[k])[1] for k, P in enumerate(Ps)]
+    dt1, inf1 = _timed(lambda: one_by_one(Pb), reps=1)
+    yield {"config": f"C4 {count} instances one at a time, mixed persistent", "cells": cells, "ms": dt1 * 1e3,
+           "cells_per_s": cells / dt1, "statuses": sorted(set(i["status"] for i in inf1))}
+    del Pb
+    torch.cuda.empty_cache()
+    Pp = [E.Poisson(g, precision="fp64", tol=1e-10, max_cycles=600, launch_mode=2) for g in geoms]
+    dt2, inf2 = _timed(lambda: one_by_one(Pp), reps=1)
+    yield {"config": f"C4 {count} instances one at a time, plain FP64 multi-launch", "cells": cells,
+           "ms": dt2 * 1e3, "cells_per_s": cells / dt2, "statuses": sorted(set(i["status"] for i in inf2))}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--only", nargs="+", default=["C1", "C2", "C3", "C4"])
+    args = ap.parse_args()
+    E.load()
+    for name, fn in (("C1", c1), ("C2", c2), ("C3", c3), ("C4", c4)):
+        if name in args.only:
+            for line in fn():
+                print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

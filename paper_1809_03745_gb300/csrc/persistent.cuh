@@ -939,6 +939,16 @@ __global__ void __launch_bounds__(PT) k_barrier_bench(Barrier B, int reps) {
     if (!grid_sync(B, &epoch, (int)gridDim.x)) return;
 }
 
+// bounded-wait self-test: the CTAs wait at a grid barrier sized for one more
+// CTA than was launched, so the wait can only end by its clock bound; the
+// kernel then returns with the error word set
+__global__ void __launch_bounds__(PT) k_barrier_expiry(Barrier B) {
+  __shared__ unsigned epoch;
+  if (threadIdx.x == 0) epoch = 0u;
+  __syncthreads();
+  grid_sync(B, &epoch, (int)gridDim.x + 1);
+}
+
 // the persistent kernel's phases launched on their own, with its grid shape,
 // to time them on large levels: one colour of the regular-cell sweep, and the
 // residual fused with restriction (cut-cell residual rows as left in tmp)

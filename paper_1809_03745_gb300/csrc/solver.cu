@@ -1149,6 +1149,34 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
     *bytes = (double)P->grid;
     return EB_OK;
   }
+  if (P && kernel == 3 && ms && bytes) {
+    // a grid barrier that nobody completes: the bounded wait must expire and
+    // report EB_ERR_TIMEOUT with the context still usable
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(P->d_bar, 0, 4 * sizeof(unsigned), s);
+    Barrier B{P->d_bar, (int*)(P->d_bar + 2)};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    k_barrier_expiry<<<2, PT, 0, s>>>(B);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    unsigned bar[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(bar, P->d_bar, sizeof(bar), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "barrier expiry test");
+    *ms = (double)t;
+    *bytes = 0.0;
+    if (bar[2]) {
+      set_error("a grid barrier wait gave up");
+      return EB_ERR_TIMEOUT;
+    }
+    return EB_OK;
+  }
   if (!P || reps < 1 || (kernel != 0 && kernel != 1) || !ms || !bytes) {
     set_error("invalid argument");
     return EB_ERR_INVALID;

@@ -181,3 +181,16 @@ def test_no_boundary_pure_dirichlet_box():
     P = E.Poisson(g, precision="fp64", tol=1e-13)
     phi, info = P.solve(torch.from_numpy(S))
     assert np.abs(phi.cpu().numpy() - ophi).max() <= 1e-9 * np.abs(ophi).max()
+
+
+def test_bounded_barrier_wait_expires_with_timeout_status():
+    """A grid barrier nobody completes (a flag nothing sets): the kernel's
+    bounded wait gives up, the call reports EB_ERR_TIMEOUT, and the same
+    context then solves normally."""
+    d, S, sig = W.c1_inputs(64)
+    P = E.Poisson(E.Geometry(d), precision="mixed", tol=1e-10)
+    with pytest.raises(E.EBError) as ei:
+        P.profile(3, 1)
+    assert ei.value.status == E.EB_ERR_TIMEOUT
+    phi, info = P.solve(torch.from_numpy(S), torch.from_numpy(sig))
+    assert info["status"] == 0 and info["rel_res"] <= 1e-10
