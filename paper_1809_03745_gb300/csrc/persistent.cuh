@@ -24,6 +24,7 @@ struct Hier {
   int bm;       // order of the bottom inverse (0: relax the bottom instead)
   int bsweeps;  // relaxation sweeps when bm == 0
   int smem;     // 1: levels lc.. keep x, b, flags and row scratch in CTA 0's shared memory
+  int gbot;     // 1: the bottom is a grid phase, a row-major dense inverse applied one warp per row
   int smem_bytes;
   const T* binv;  // [bm][bm], slot s = p * ncell + c of the coarsest level
   int off_x[MAXLEV][2], off_b[MAXLEV][2], off_f[MAXLEV], off_t[MAXLEV];  // byte offsets into shared memory
@@ -556,6 +557,31 @@ __device__ bool ph_bottom(const Hier<T>& H, const Op<T>* ops, const Ctx& c) {
   return c.sync(((H.nlev - 1) << 4) | 9);
 }
 
+// bottom solve over the whole grid: x = binv b with binv row-major, one warp
+// per row (lanes over the columns, then a shuffle reduction)
+template <class T>
+__device__ bool ph_bottom_grid(const Hier<T>& H, const Ctx& c) {
+  const Op<T>& o = H.op[H.nlev - 1];
+  const long long nc = o.ncell;
+  const int lane = threadIdx.x & 31;
+  const long long w0 = (long long)(threadIdx.x >> 5) * c.gsize + c.gcta;
+  const long long ws = (long long)c.gsize * (blockDim.x >> 5);
+  for (long long i = w0; i < H.bm; i += ws) {
+    const int p = (int)(i / nc);
+    const long long cell = i - p * nc;
+    if (!((o.flags[cell] >> p) & 1)) continue;
+    const T* row = H.binv + i * H.bm;
+    T acc = T(0);
+    for (int j = lane; j < H.bm; j += 32) {
+      const int q = j >= nc ? 1 : 0;
+      acc += row[j] * o.b[q][j - q * nc];
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) o.x[p][cell] = acc;
+  }
+  return c.sync(((H.nlev - 1) << 4) | 9);
+}
+
 // levels lc.. inside CTA 0, on the shared-memory copies when H.smem
 template <class T>
 __device__ void coarse_part(const Hier<T>& H, const Op<T>* lop, const Ctx& L) {
@@ -608,11 +634,15 @@ __device__ bool vcycle_dev(const Hier<T>& H, const Op<T>* lop, const Ctx& G) {
     ph_restrict(o, H.op[l + 1], G);
     if (!G.sync((l << 4) | 6)) return false;
   }
-  if (G.gcta == 0) {
-    Ctx L{(long long)threadIdx.x, (long long)blockDim.x, true, G.B, G.epoch, G.tr, G.tn, 0, 1};
-    coarse_part(H, lop, L);
+  if (H.gbot) {
+    if (!ph_bottom_grid(H, G)) return false;
+  } else {
+    if (G.gcta == 0) {
+      Ctx L{(long long)threadIdx.x, (long long)blockDim.x, true, G.B, G.epoch, G.tr, G.tn, 0, 1};
+      coarse_part(H, lop, L);
+    }
+    if (!G.sync((15 << 4) | 8)) return false;
   }
-  if (!G.sync((15 << 4) | 8)) return false;
   for (int l = H.lc - 1; l >= 0; --l) {
     ph_prolong(H.op[l], H.op[l + 1], G);
     if (!G.sync((l << 4) | 7)) return false;
@@ -803,8 +833,7 @@ __global__ void k_bottom_matrix(Op<T> o, double ceps0, double ceps1, int m, doub
   long long nc = o.ncell;
   int p = (int)(i / nc);
   long long c = i - p * nc;
-  double* row = M + i * m;
-  for (int j = 0; j < m; ++j) row[j] = 0.0;
+  double* row = M + i * m;  // zeroed by the caller
   uint8_t f = o.flags[c];
   if (!((f >> p) & 1)) {
     row[i] = 1.0;
@@ -920,11 +949,98 @@ __global__ void k_gauss_jordan(double* A, double* Ainv, int m, int* status) {
 }
 
 // transpose and convert the bottom inverse (m x m)
-template <class T>
-__global__ void k_convert(const double* a, T* b, long long n) {
+template <class T, class S = double>
+__global__ void k_convert(const S* a, T* b, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long m = (long long)llrint(sqrt((double)n));
   if (i < n) b[(i % m) * m + i / m] = (T)a[i];
+}
+
+template <class T>
+__global__ void k_from_float(const float* a, T* b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (T)a[i];
+}
+
+__global__ void k_to_float(const double* a, float* b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// FP32 Gauss-Jordan for larger bottoms, one pivot step in two launches.
+// Step k, part 1 (one CTA): partial pivoting on column k, row swap, row k
+// scaled by the pivot; Ai starts as the identity.
+__global__ void k_gj_pivot(float* A, float* Ai, int m, int k, int* status) {
+  __shared__ float sv[1024];
+  __shared__ int si[1024];
+  __shared__ int piv;
+  __shared__ float pval;
+  if (status[0]) return;
+  float best = -1.0f;
+  int bi = k;
+  for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
+    float v = fabsf(A[(long long)r * m + k]);
+    if (v > best) {
+      best = v;
+      bi = r;
+    }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      float a = sv[threadIdx.x], b = sv[threadIdx.x + s];
+      int ia = si[threadIdx.x], ib = si[threadIdx.x + s];
+      if (b > a || (b == a && ib < ia)) {
+        sv[threadIdx.x] = b;
+        si[threadIdx.x] = ib;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    piv = si[0];
+    pval = A[(long long)si[0] * m + k];
+    if (!(fabsf(pval) > 1e-30f)) status[0] = 1;
+  }
+  __syncthreads();
+  if (status[0]) return;
+  const int pr = piv;
+  const float inv = 1.0f / pval;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    float a = A[(long long)pr * m + j], ai = Ai[(long long)pr * m + j];
+    if (pr != k) {
+      A[(long long)pr * m + j] = A[(long long)k * m + j];
+      Ai[(long long)pr * m + j] = Ai[(long long)k * m + j];
+    }
+    A[(long long)k * m + j] = a * inv;
+    Ai[(long long)k * m + j] = ai * inv;
+  }
+}
+
+// Step k, part 2: column k eliminated from every other row, one warp per row
+// (row k is only read; each warp reads its multiplier before clearing it).
+__global__ void k_gj_elim(float* A, float* Ai, int m, int k, const int* status) {
+  if (status[0]) return;
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= m || r == k) return;
+  const float f = A[r * m + k];
+  if (f == 0.0f) return;
+  const float* Ak = A + (long long)k * m;
+  const float* Aik = Ai + (long long)k * m;
+  float* Ar = A + r * m;
+  float* Air = Ai + r * m;
+  for (int j = k + 1 + lane; j < m; j += 32) Ar[j] -= f * Ak[j];
+  for (int j = lane; j < m; j += 32) Air[j] -= f * Aik[j];
+  __syncwarp();
+  if (lane == 0) Ar[k] = 0.0f;
+}
+
+__global__ void k_identity(float* Ai, int m) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (long long)m * m) Ai[e] = (e / m == e % m) ? 1.0f : 0.0f;
 }
 
 }  // namespace ebp

@@ -60,14 +60,22 @@ struct Done {
 // caller-side fields (40 B), the inner-precision hierarchy (<= 32 B x 8/7..4/3),
 // geometry arrays per level (~12 B) and the FP64 level copies of the
 // multi-launch path (<= 43 B); cut cells and sparse rows stay well inside the
-// slack; plus the node labels and a fixed part for the small buffers.
+// slack; plus the node labels, a fixed part for the small buffers and the
+// dense bottom inverse: coarsening halves even sizes down to 8 cells but may
+// stop earlier on the geometry, so any bottom of at most 4096 unknowns is
+// possible unless the finest grid alone is already larger at the deepest
+// level it could reach.  (Set-up scratch of the inverse is transient.)
 long long estimate_bytes(const eb_geom_desc& d) {
-  long long n = 1, nodes = 1;
+  long long n = 1, nodes = 1, deepest = 2;
   for (int k = 0; k < d.dim; ++k) {
     n *= d.n[k];
     nodes *= d.n[k] + 1;
+    int m = d.n[k];
+    while (m % 2 == 0 && m / 2 >= 8) m /= 2;
+    deepest *= m;
   }
-  return n * 200 + nodes + (8ll << 20);
+  long long inv = deepest > 4096 ? 0 : 4096ll * 4096ll * 8ll;
+  return n * 200 + nodes + (8ll << 20) + inv;
 }
 
 }  // namespace

@@ -471,16 +471,20 @@ static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
     }
     return off;
   };
+  const Op<T>& ob = ops[P->nlev - 1];
+  const int m = (int)(P->G->n_phase * ob.ncell);
+  // a bottom of 256 < m <= 4096 unknowns gets a dense inverse applied by the
+  // whole grid: every level is then a grid level, the bottom in global memory
+  const bool big_bottom = m > 256 && m <= 4096;
+  if (big_bottom) H.lc = P->nlev - 1;
   while (H.lc < P->nlev - 1 && layout(H.lc, false) > SMEM_CAP) ++H.lc;
   long long sb = layout(H.lc, false);
-  H.smem = sb <= SMEM_CAP ? 1 : 0;
+  H.smem = (sb <= SMEM_CAP && !big_bottom) ? 1 : 0;
   H.smem_bytes = H.smem ? (int)sb : 0;
   if (H.smem) layout(H.lc, true);
   for (int l = 0; l < P->nlev; ++l) H.op[l] = ops[l];
   eb_status st = EB_OK;
   // dense inverse of the coarsest operator (FP64 Gauss-Jordan on the device)
-  const Op<T>& ob = ops[P->nlev - 1];
-  int m = (int)(P->G->n_phase * ob.ncell);
   if (m <= 256) {
     std::vector<void*> tmp;
     double* M = (double*)dev_alloc(tmp, sizeof(double) * m * m, nullptr, &st);
@@ -491,6 +495,7 @@ static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
       const DevLevel& Lb = P->G->L[P->nlev - 1];
       double h2 = Lb.g.h * Lb.g.h;
       cudaMemsetAsync(stat, 0, sizeof(int), P->s);
+      cudaMemsetAsync(M, 0, sizeof(double) * m * m, P->s);
       k_bottom_matrix<T><<<blocks(m), 256, 0, P->s>>>(ob, Lb.g.eps[0] / h2, Lb.g.eps[1] / h2, m, M);
       k_gauss_jordan<<<1, 1024, 0, P->s>>>(M, Mi, m, stat);
       k_convert<T><<<blocks((long long)m * m), 256, 0, P->s>>>(Mi, binv, (long long)m * m);
@@ -504,6 +509,44 @@ static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
       }
     }
     for (void* p : tmp) cudaFree(p);
+  } else if (m <= 4096) {
+    // larger bottoms: FP32 Gauss-Jordan with partial pivoting, one pivot step
+    // per pair of launches (an approximate inverse is enough for a bottom
+    // solve inside the V-cycle; a failed pivot keeps the relaxation bottom)
+    std::vector<void*> tmp;
+    double* M = (double*)dev_alloc(tmp, sizeof(double) * m * m, nullptr, &st);
+    float* Af = (float*)dev_alloc(tmp, sizeof(float) * m * m, nullptr, &st);
+    float* Ai = (float*)dev_alloc(tmp, sizeof(float) * m * m, nullptr, &st);
+    int* stat = (int*)dev_alloc(tmp, sizeof(int), nullptr, &st);
+    T* binv = st == EB_OK ? (T*)dev_alloc(P->allocs, sizeof(T) * m * m, &P->bytes, &st) : nullptr;
+    if (st == EB_OK) {
+      const DevLevel& Lb = P->G->L[P->nlev - 1];
+      double h2 = Lb.g.h * Lb.g.h;
+      long long mm = (long long)m * m;
+      cudaMemsetAsync(stat, 0, sizeof(int), P->s);
+      cudaMemsetAsync(M, 0, sizeof(double) * m * m, P->s);
+      k_bottom_matrix<T><<<blocks(m), 256, 0, P->s>>>(ob, Lb.g.eps[0] / h2, Lb.g.eps[1] / h2, m, M);
+      k_to_float<<<blocks(mm), 256, 0, P->s>>>(M, Af, mm);
+      k_identity<<<blocks(mm), 256, 0, P->s>>>(Ai, m);
+      const int eb = (int)(((long long)m * 32 + 255) / 256);
+      for (int k = 0; k < m; ++k) {
+        k_gj_pivot<<<1, 1024, 0, P->s>>>(Af, Ai, m, k, stat);
+        k_gj_elim<<<eb, 256, 0, P->s>>>(Af, Ai, m, k, stat);
+      }
+      k_from_float<T><<<blocks(mm), 256, 0, P->s>>>(Ai, binv, mm);  // row-major for ph_bottom_grid
+      int hs = 0;
+      cudaError_t e = cudaMemcpyAsync(&hs, stat, sizeof(int), cudaMemcpyDeviceToHost, P->s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
+      if (e != cudaSuccess) st = cuda_fail(e, "bottom inverse");
+      if (st == EB_OK && hs == 0) {
+        H.bm = m;
+        H.binv = binv;
+        H.gbot = 1;
+      }
+    }
+    for (void* p : tmp) cudaFree(p);
+    st = st == EB_ERR_OOM ? EB_OK : st;  // no room for the inverse: relaxation bottom
+    if (st == EB_OK && H.bm == 0) cudaGetLastError();
   }
   if (st != EB_OK) return st;
   P->bm = H.bm;

@@ -68,10 +68,10 @@ def test_small_results_match_oracle():
 
 def test_admission_respects_memory_budget():
     inst = W.batched_instances(count=6, seed=1809 + 52, n2=(256, 256), n3=(32, 32), p3d=0.0)
-    # the server's pre-build estimate of one 256^2 instance; an admitted
-    # instance is then accounted at its measured size, so with 1.2 estimates
-    # of budget a second one fits only if the first holds under 0.2 of one
-    per = 256 * 256 * 200 + 257 * 257 + (8 << 20)
+    # the server's pre-build estimate of one 256^2 instance (including the
+    # bound on a dense bottom inverse); an admitted instance is then accounted
+    # at its measured size, so 1.2 estimates of budget hold a few at a time
+    per = 256 * 256 * 200 + 257 * 257 + (8 << 20) + 4096 * 4096 * 8
     srv = E.Server(max_slots=16, hbm_budget_bytes=1.2 * per, tol=1e-10, max_cycles=400)
     try:
         tickets = [srv.submit(d, S, s) for d, S, s in inst]
@@ -89,7 +89,7 @@ def test_admission_respects_memory_budget():
     assert all(r[1]["status"] == 0 for r in res)
     assert st["hbm_peak"] <= st["hbm_budget"], st
     assert st["estimate_misses"] == 0
-    assert peak_active <= 2
+    assert peak_active < len(inst)  # the budget, not the slot count, limited admission
     assert st["hbm_used"] == 0
 
 
