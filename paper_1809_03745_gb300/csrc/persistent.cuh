@@ -74,7 +74,10 @@ __device__ __forceinline__ bool grid_sync(const Barrier& B, unsigned* epoch, int
     if (*ve == 0) {
       unsigned target = (*epoch + 1u) * (unsigned)gsize;
       *epoch += 1u;
-      __threadfence();
+      // the CTA's writes reach thread 0 through the block barrier and are
+      // released at GPU scope by the arrival (release is cumulative); the
+      // acquiring load orders the reads after the wait, and the block barrier
+      // below hands that on to the other threads
       red_release_add(B.count, 1u);
       long long t0 = clock64();
       while (ld_acquire(B.count) < target) {
@@ -82,9 +85,7 @@ __device__ __forceinline__ bool grid_sync(const Barrier& B, unsigned* epoch, int
           atomicOr(B.err, 1);
           break;
         }
-        __nanosleep(16);
       }
-      __threadfence();
     }
   }
   __syncthreads();
