@@ -261,17 +261,35 @@ __device__ __noinline__ T relax1(const Op<T>& o, int q, int i, int j, int k, lon
 // (centre, y and z neighbours, right-hand side) in one 16-byte vector load.
 // Needs n[0] % 4 == 0 and 16-byte aligned arrays.
 template <class T>
+__device__ __forceinline__ unsigned quad_flags(const Op<T>& o, long long t, long long work, unsigned nq) {
+  if (t >= work) return 0u;
+  const unsigned row = fdiv((unsigned)t, o.dq);
+  const long long base = (long long)row * o.n[0] + 4 * (long long)((unsigned)t - row * nq);
+  return *reinterpret_cast<const unsigned*>(o.flags + base);
+}
+
+template <class T>
 __device__ __forceinline__ void ph_dense_vec(const Op<T>& o, int colour, const Ctx& c) {
   constexpr int U = 2;
   const int n0 = o.n[0], n1 = o.n[1], n2 = o.D == 3 ? o.n[2] : 1;
   const unsigned nq = (unsigned)n0 >> 2;
   const long long work = (o.ncell / n0) * (long long)nq;
   const long long sy = n0, sz = (long long)n0 * n1;
+  // the flags of the next work items are loaded one iteration ahead, so an
+  // item's rows are requested without waiting for its flags
+  unsigned wnext[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) wnext[u] = quad_flags(o, c.i0 + u * c.st, work, nq);
   for (long long t0 = c.i0; t0 < work; t0 += U * c.st) {
     T xc[U][4], ym[U][4], yp[U][4], zm[U][4], zp[U][4], bv[U][4], xl[U], xr[U];
-    unsigned fw[U];
+    unsigned fw[U], wcur[U];
     long long b0[U];
     int J[U], K[U], I0[U], S[U], P[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      wcur[u] = wnext[u];
+      wnext[u] = quad_flags(o, t0 + (U + u) * c.st, work, nq);
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       fw[u] = 0u;
@@ -289,7 +307,7 @@ __device__ __forceinline__ void ph_dense_vec(const Op<T>& o, int colour, const C
       const int i0 = 4 * (int)(tu - row * nq);
       const int sh = (j + k + colour) & 1;
       const long long base = (long long)row * n0 + i0;
-      const unsigned w = *reinterpret_cast<const unsigned*>(o.flags + base);
+      const unsigned w = wcur[u];
       const unsigned fa = (w >> (8 * sh)) & 0xffu, fb = (w >> (8 * (sh + 2))) & 0xffu;
       const bool aa = !(fa & F_IRR) && (fa & 3), ab = !(fb & F_IRR) && (fb & 3);
       if (!aa && !ab) continue;
