@@ -309,13 +309,14 @@ eb_status eb_amr_residual(eb_amr* A, const double* d_rhs_c, const double* d_sig_
                           const double* d_sig_f, const double* d_phi_c, const double* d_phi_f, double* d_r_c,
                           double* d_r_f, void* stream);
 /* Composite solve to max|r| <= tol max|b| (opts of setup; max_cycles caps the
- * composite iterations).  Each iteration: coarse correction over the domain
- * (fine residual averaged under the box), constant per parent on the fine
- * grid; then a fine correction on the box with zero Dirichlet data on its CF
- * sides; both by the persistent multigrid solve to 1e-3.  d_phi_c / d_phi_f
- * hold the guess on entry; on return d_phi_c under the box holds the fine
- * means.  info: outer_iters = composite iterations, vcycles = V-cycles of the
- * corrections. */
+ * composite iterations): restarted FGMRES (restart 12, FP64) preconditioned
+ * by one FAC step: a coarse correction over the domain (fine part averaged
+ * under the box), constant per parent on the fine grid, then a fine
+ * correction on the box with zero Dirichlet data on its CF sides, both by the
+ * persistent multigrid solve to 1e-2.  d_phi_c / d_phi_f hold the guess on
+ * entry; on return d_phi_c under the box holds the fine means.  info:
+ * outer_iters = FGMRES iterations, vcycles = V-cycles of the corrections.
+ * The work space (27 composite vectors) is allocated at the first call. */
 eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double* d_sig_c, const double* d_rhs_f,
                        const double* d_sig_f, double* d_phi_c, double* d_phi_f, eb_solve_info* info, void* stream);
 void eb_amr_destroy(eb_amr* A);
