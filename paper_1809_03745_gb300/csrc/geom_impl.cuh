@@ -237,7 +237,7 @@ EBP_HDN void edge_point_local(const Csg& c, const Grid& g, const uint8_t* lab, c
 
 // EB centroid in local coordinates.  2D: midpoint of the two crossings.  3D:
 // the crossings ordered into one loop through the cell faces, area centroid
-// of the fan of triangles from the lowest-numbered cut edge.
+// of the fan of triangles about the vertex mean of the loop.
 EBP_HDN int eb_centroid_local(const Csg& c, const Grid& g, const uint8_t* lab, const int I[3], double u[3]) {
   u[0] = u[1] = u[2] = 0.0;
   if (g.D == 2) {
@@ -318,31 +318,35 @@ EBP_HDN int eb_centroid_local(const Csg& c, const Grid& g, const uint8_t* lab, c
     if (cur == start || len > 12) break;
   }
   if (len != ncut) return ST_UNSUPPORTED;
+  // area centroid of the fan of triangles about the loop's vertex mean: for a
+  // planar (convex) loop the polygon's centroid; for a curved boundary it does
+  // not depend on where the loop starts or which way it runs
+  double vm[3];
+  for (int q = 0; q < 3; ++q) {
+    double t = 0.0;
+    for (int k = 0; k < len; ++k) t = t + P[loop[k]][q];
+    vm[q] = t / (double)len;
+  }
   double W = 0.0, S[3] = {0.0, 0.0, 0.0};
-  const double* v0 = P[loop[0]];
-  for (int k = 1; k + 1 < len; ++k) {
+  for (int k = 0; k < len; ++k) {
     const double* v1 = P[loop[k]];
-    const double* v2 = P[loop[k + 1]];
+    const double* v2 = P[loop[(k + 1) % len]];
     double e1[3], e2[3], cr[3];
     for (int q = 0; q < 3; ++q) {
-      e1[q] = v1[q] - v0[q];
-      e2[q] = v2[q] - v0[q];
+      e1[q] = v1[q] - vm[q];
+      e2[q] = v2[q] - vm[q];
     }
     cr[0] = e1[1] * e2[2] - e1[2] * e2[1];
     cr[1] = e1[2] * e2[0] - e1[0] * e2[2];
     cr[2] = e1[0] * e2[1] - e1[1] * e2[0];
     double ar = 0.5 * sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
     W = W + ar;
-    for (int q = 0; q < 3; ++q) S[q] = S[q] + ar * ((v0[q] + v1[q] + v2[q]) / 3.0);
+    for (int q = 0; q < 3; ++q) S[q] = S[q] + ar * ((vm[q] + v1[q] + v2[q]) / 3.0);
   }
   if (W > 0.0) {
     for (int q = 0; q < 3; ++q) u[q] = S[q] / W;
   } else {  // all crossings on one line or point: their mean
-    for (int q = 0; q < 3; ++q) {
-      double t = 0.0;
-      for (int k = 0; k < len; ++k) t = t + P[loop[k]][q];
-      u[q] = t / (double)len;
-    }
+    for (int q = 0; q < 3; ++q) u[q] = vm[q];
   }
   return 0;
 }
