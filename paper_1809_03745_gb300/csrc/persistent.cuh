@@ -406,9 +406,14 @@ __device__ __forceinline__ void ph_rows(const Op<T>& o, long long rb, long long 
   const long long w0 = c.local ? (threadIdx.x >> 5) : (long long)(threadIdx.x >> 5) * c.gsize + c.gcta;
   const long long ws = c.local ? (blockDim.x >> 5) : (long long)c.gsize * (blockDim.x >> 5);
   for (long long r = rb + w0; r < re; r += ws) {
-    double d = o.diag[r];
-    if (d == 0.0) continue;
+    // the row's descriptors in one round of independent loads, then its
+    // entries together with the cell's own b and x, then the gathered x
+    const double d = o.diag[r];
     const int e0 = o.row_ptr[r], e1 = o.row_ptr[r + 1];
+    const long long cell = o.irr_cell[r >> 1];
+    if (d == 0.0) continue;
+    const int p = (int)(r & 1);
+    const double bc = (double)o.b[p][cell], xc = (double)o.x[p][cell];
     double s = 0.0;
     for (int e = e0 + lane; e < e1; e += 32) {
       unsigned cl = (unsigned)o.col[e];
@@ -416,10 +421,8 @@ __device__ __forceinline__ void ph_rows(const Op<T>& o, long long rb, long long 
     }
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) {
-      long long cell = o.irr_cell[r >> 1];
-      int p = (int)(r & 1);
-      double v = (double)o.b[p][cell] - s;
-      o.tmp[r] = mode == 0 ? (T)(v / d) : (T)(v - d * (double)o.x[p][cell]);
+      double v = bc - s;
+      o.tmp[r] = mode == 0 ? (T)(v / d) : (T)(v - d * xc);
     }
   }
 }
@@ -427,8 +430,10 @@ __device__ __forceinline__ void ph_rows(const Op<T>& o, long long rb, long long 
 template <class T>
 __device__ __forceinline__ void ph_write(const Op<T>& o, long long rb, long long re, const Ctx& c) {
   for (long long r = rb + c.i0; r < re; r += c.st) {
-    if (o.diag[r] == 0.0) continue;
-    o.x[r & 1][o.irr_cell[r >> 1]] = o.tmp[r];
+    const double d = o.diag[r];
+    const long long cell = o.irr_cell[r >> 1];
+    const T v = o.tmp[r];
+    if (d != 0.0) o.x[r & 1][cell] = v;
   }
 }
 
@@ -491,8 +496,101 @@ __device__ __forceinline__ T prolong_value(const Op<T>& f, const Op<T>& co, long
   return acc;
 }
 
+// Prolongation by blocks: one coarse cell and its 2^D children per work item.
+// The coarse 3^D neighbourhood (flags, values of the phases the children
+// carry) and the children's flags and values are loaded in one round; each
+// child then gets the (bi/tri)linear value of prolong_value, same weights in
+// the same order, or the constant one.  Needs fine n = 2 coarse n per axis.
+template <class T, int D>
+__device__ __forceinline__ void ph_prolong_blk(const Op<T>& f, const Op<T>& co, const Ctx& c) {
+  constexpr int NB = D == 3 ? 27 : 9, NCH = 1 << D;
+  const long long stc[3] = {1, co.n[0], (long long)co.n[0] * co.n[1]};
+  const long long stf[3] = {1, f.n[0], (long long)f.n[0] * f.n[1]};
+  for (long long C = c.i0; C < co.ncell; C += c.st) {
+    int IC[3];
+    ijk(co, C, IC);
+    if (D == 2) IC[2] = 0;
+    // children's flags and the coarse neighbourhood's, as one bit mask per phase
+    long long cf[NCH];
+    unsigned fm[2] = {0u, 0u}, cm[2] = {0u, 0u};
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+      cf[k] = (long long)(2 * IC[0] + (k & 1)) + stf[1] * (2 * IC[1] + ((k >> 1) & 1)) +
+              (D == 3 ? stf[2] * (2 * IC[2] + ((k >> 2) & 1)) : 0);
+      const unsigned v = f.flags[cf[k]];
+      fm[0] |= (v & 1u) << k;
+      fm[1] |= ((v >> 1) & 1u) << k;
+    }
+#pragma unroll
+    for (int m = 0; m < NB; ++m) {
+      const int o0 = m % 3 - 1, o1 = (m / 3) % 3 - 1, o2 = D == 3 ? m / 9 - 1 : 0;
+      const bool in = IC[0] + o0 >= 0 && IC[0] + o0 < co.n[0] && IC[1] + o1 >= 0 && IC[1] + o1 < co.n[1] &&
+                      (D == 2 || (IC[2] + o2 >= 0 && IC[2] + o2 < co.n[2]));
+      const unsigned v = in ? co.flags[C + o0 * stc[0] + o1 * stc[1] + o2 * stc[2]] : 0u;
+      cm[0] |= (v & 1u) << m;
+      cm[1] |= ((v >> 1) & 1u) << m;
+    }
+    for (int q = 0; q < 2; ++q) {
+      if (!fm[q]) continue;
+      T cx[NB], xo[NCH];
+#pragma unroll
+      for (int m = 0; m < NB; ++m) {
+        const int o0 = m % 3 - 1, o1 = (m / 3) % 3 - 1, o2 = D == 3 ? m / 9 - 1 : 0;
+        cx[m] = ((cm[q] >> m) & 1u) ? co.x[q][C + o0 * stc[0] + o1 * stc[1] + o2 * stc[2]] : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < NCH; ++k) xo[k] = ((fm[q] >> k) & 1u) ? f.x[q][cf[k]] : T(0);
+#pragma unroll
+      for (int k = 0; k < NCH; ++k) {
+        if (!((fm[q] >> k) & 1u)) continue;
+        const int sd0 = (k & 1) ? 1 : -1, sd1 = ((k >> 1) & 1) ? 1 : -1, sd2 = ((k >> 2) & 1) ? 1 : -1;
+        bool lin = IC[0] + sd0 >= 0 && IC[0] + sd0 < co.n[0] && IC[1] + sd1 >= 0 && IC[1] + sd1 < co.n[1] &&
+                   (D == 2 || (IC[2] + sd2 >= 0 && IC[2] + sd2 < co.n[2]));
+        // neighbourhood slot of the corner whose offset bits j step sd along each axis
+        const int centre = D == 3 ? 13 : 4;
+#define EBP_SLOT(j) (centre + (((j) & 1) ? sd0 : 0) + ((((j) >> 1) & 1) ? 3 * sd1 : 0) + \
+                     ((D == 3 && (((j) >> 2) & 1)) ? 9 * sd2 : 0))
+#pragma unroll
+        for (int j = 1; j < NCH; ++j)
+          if (!((cm[q] >> EBP_SLOT(j)) & 1u)) lin = false;
+        T add;
+        if (!lin) {
+          add = cx[centre];
+        } else {
+          T acc = T(0);
+#pragma unroll
+          for (int j = 0; j < NCH; ++j) {
+            T w = T(1);
+            for (int a = 0; a < D; ++a) w *= ((j >> a) & 1) ? T(0.25) : T(0.75);
+            acc += w * cx[EBP_SLOT(j)];
+          }
+          add = acc;
+        }
+#undef EBP_SLOT
+        f.x[q][cf[k]] = xo[k] + add;
+      }
+    }
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void ph_prolong_pt(const Op<T>& f, const Op<T>& co, const Ctx& c);
+
 template <class T>
 __device__ __forceinline__ void ph_prolong(const Op<T>& f, const Op<T>& co, const Ctx& c) {
+  bool blk = true;
+  for (int a = 0; a < f.D; ++a)
+    if (f.n[a] != 2 * co.n[a]) blk = false;
+  if (blk) {
+    if (f.D == 3) ph_prolong_blk<T, 3>(f, co, c);
+    else ph_prolong_blk<T, 2>(f, co, c);
+    return;
+  }
+  ph_prolong_pt(f, co, c);
+}
+
+template <class T>
+__device__ __forceinline__ void ph_prolong_pt(const Op<T>& f, const Op<T>& co, const Ctx& c) {
   constexpr int U = 2;
   for (long long c0 = c.i0; c0 < f.ncell; c0 += U * c.st) {
     T add[U][2], old[U][2];
