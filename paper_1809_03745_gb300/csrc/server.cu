@@ -62,7 +62,7 @@ struct Done {
 // multi-launch path (<= 43 B); cut cells and sparse rows stay well inside the
 // slack; plus the node labels, a fixed part for the small buffers and the
 // dense bottom inverse: coarsening halves even sizes down to 8 cells but may
-// stop earlier on the geometry, so any bottom of at most 4096 unknowns is
+// stop earlier on the geometry, so any bottom of at most 1024 unknowns is
 // possible unless the finest grid alone is already larger at the deepest
 // level it could reach.  (Set-up scratch of the inverse is transient.)
 long long estimate_bytes(const eb_geom_desc& d) {
@@ -74,7 +74,7 @@ long long estimate_bytes(const eb_geom_desc& d) {
     while (m % 2 == 0 && m / 2 >= 8) m /= 2;
     deepest *= m;
   }
-  long long inv = deepest > 4096 ? 0 : 4096ll * 4096ll * 8ll;
+  long long inv = deepest > 1024 ? 0 : 1024ll * 1024ll * 8ll;
   return n * 200 + nodes + (8ll << 20) + inv;
 }
 

@@ -473,9 +473,11 @@ static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
   };
   const Op<T>& ob = ops[P->nlev - 1];
   const int m = (int)(P->G->n_phase * ob.ncell);
-  // a bottom of 256 < m <= 4096 unknowns gets a dense inverse applied by the
-  // whole grid: every level is then a grid level, the bottom in global memory
-  const bool big_bottom = m > 256 && m <= 4096;
+  // a bottom of 256 < m <= 1024 unknowns gets a dense inverse applied by the
+  // whole grid: every level is then a grid level, the bottom in global memory.
+  // (Set-up costs ~2 m^3 flops through L2: ~7 ms at m = 1024, ~260 ms at
+  // m = 3500, which a serving loop pays per admitted request.)
+  const bool big_bottom = m > 256 && m <= 1024;
   if (big_bottom) H.lc = P->nlev - 1;
   while (H.lc < P->nlev - 1 && layout(H.lc, false) > SMEM_CAP) ++H.lc;
   long long sb = layout(H.lc, false);
@@ -509,7 +511,7 @@ static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
       }
     }
     for (void* p : tmp) cudaFree(p);
-  } else if (m <= 4096) {
+  } else if (m <= 1024) {
     // larger bottoms: FP32 Gauss-Jordan with partial pivoting, one pivot step
     // per pair of launches (an approximate inverse is enough for a bottom
     // solve inside the V-cycle; a failed pivot keeps the relaxation bottom)

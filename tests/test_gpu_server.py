@@ -71,7 +71,7 @@ def test_admission_respects_memory_budget():
     # the server's pre-build estimate of one 256^2 instance (including the
     # bound on a dense bottom inverse); an admitted instance is then accounted
     # at its measured size, so 1.2 estimates of budget hold a few at a time
-    per = 256 * 256 * 200 + 257 * 257 + (8 << 20) + 4096 * 4096 * 8
+    per = 256 * 256 * 200 + 257 * 257 + (8 << 20) + 1024 * 1024 * 8
     srv = E.Server(max_slots=16, hbm_budget_bytes=1.2 * per, tol=1e-10, max_cycles=400)
     try:
         tickets = [srv.submit(d, S, s) for d, S, s in inst]
