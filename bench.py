@@ -240,12 +240,9 @@ def run_gpu(args):
     kms = statistics.mean(i["kernel_ms"] for i in infos)
     kbytes = solve_bytes(ncell, 2, True, infos[-1]["vcycles"], infos[-1]["outer_iters"])
     scale = kernels_at_scale(dev, E, W, args.scale_n) if (rank == 0 and not args.no_scale) else None
-    ms = sum(ms_steps) / len(ms_steps)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * ncell / (ms / 1000.0)
+    from paper_1809_03745_gb300.shard import job_time, throughput
+    ms = job_time(sum(ms_steps) / len(ms_steps))
+    value = throughput(ncell, world, ms)
 
     # end to end through the public API with host buffers
     h_rhs = torch.from_numpy(S).pin_memory()
@@ -264,7 +261,7 @@ def run_gpu(args):
         b.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-    e2e = world * ncell / (sum(e2e_ms) / len(e2e_ms) / 1000.0)
+    e2e = throughput(ncell, world, job_time(sum(e2e_ms) / len(e2e_ms)))
 
     if rank != 0:
         return
