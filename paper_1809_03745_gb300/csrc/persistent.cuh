@@ -437,8 +437,119 @@ __device__ __forceinline__ void ph_write(const Op<T>& o, long long rb, long long
   }
 }
 
+// Residual + restriction by blocks: one coarse cell per work item; the
+// children and their face neighbours (4 x 4 without corners in 2D, the 2^3
+// block and its 24 face neighbours in 3D) are loaded in one round for each
+// phase the children carry, then every regular child's residual is formed with
+// the terms and order of cell_residual; cut children take their sparse
+// residual.  Needs fine n = 2 coarse n per axis.
+template <class T, int D>
+__device__ __forceinline__ void ph_restrict_blk(const Op<T>& f, const Op<T>& co, const Ctx& c) {
+  constexpr int NCH = 1 << D, NP = D == 3 ? 64 : 16;
+  const long long st[3] = {1, f.n[0], (long long)f.n[0] * f.n[1]};
+  const T scale = T(1) / T(NCH), third = T(1) / T(3);
+  for (long long C = c.i0; C < co.ncell; C += c.st) {
+    int IC[3];
+    ijk(co, C, IC);
+    if (D == 2) IC[2] = 0;
+    const int O[3] = {2 * IC[0], 2 * IC[1], 2 * IC[2]};
+    const long long c0 = O[0] + st[1] * O[1] + st[2] * O[2];
+    unsigned fl[NCH];
+    unsigned any = 0u;
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+      fl[k] = f.flags[c0 + (k & 1) + st[1] * ((k >> 1) & 1) + (D == 3 ? st[2] * ((k >> 2) & 1) : 0)];
+      any |= fl[k];
+    }
+    const unsigned cfl = co.flags[C];
+    T acc[2] = {T(0), T(0)};
+    for (int q = 0; q < 2; ++q) {
+      if (!((any >> q) & 1u)) continue;
+      const T* x = f.x[q];
+      // patch value at local offset (u, v, w) in -1..2, loaded where it lies in the grid
+      T P[NP];
+      T bv[NCH];
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        const int u = m % 4 - 1, v = (m / 4) % 4 - 1, w = D == 3 ? m / 16 - 1 : 0;
+        const int out = (u < 0 || u > 1) + (v < 0 || v > 1) + (w < 0 || w > 1);
+        P[m] = T(0);
+        if (out > 1) continue;  // corners and edges are never needed
+        const bool in = O[0] + u >= 0 && O[0] + u < f.n[0] && O[1] + v >= 0 && O[1] + v < f.n[1] &&
+                        (D == 2 || (O[2] + w >= 0 && O[2] + w < f.n[2]));
+        if (in) P[m] = x[c0 + u + st[1] * v + st[2] * w];
+      }
+#pragma unroll
+      for (int k = 0; k < NCH; ++k) {
+        const long long cc = c0 + (k & 1) + st[1] * ((k >> 1) & 1) + (D == 3 ? st[2] * ((k >> 2) & 1) : 0);
+        bv[k] = (((fl[k] >> q) & 1u) && !(fl[k] & F_IRR)) ? f.b[q][cc] : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < NCH; ++k) {
+        if (!((fl[k] >> q) & 1u)) continue;
+        const int ku = k & 1, kv = (k >> 1) & 1, kw = (k >> 2) & 1;
+        const int I[3] = {O[0] + ku, O[1] + kv, O[2] + kw};
+        const int loc[3] = {ku, kv, kw};
+        if (fl[k] & F_IRR) {
+          const long long cc = c0 + ku + st[1] * kv + (D == 3 ? st[2] * kw : 0);
+          acc[q] += f.tmp[2 * (long long)f.irr_of_cell[cc] + q];
+          continue;
+        }
+#define EBP_PIX(du, dv, dw) (((ku) + (du) + 1) + 4 * ((kv) + (dv) + 1) + 16 * ((kw) + (dw) + 1))
+        T sum = T(0);
+        int dg = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const int e0 = a == 0, e1 = a == 1, e2 = a == 2;
+          const T lo = P[D == 3 ? EBP_PIX(-e0, -e1, -e2) : EBP_PIX(-e0, -e1, 0) - 16];
+          const T hi = P[D == 3 ? EBP_PIX(e0, e1, e2) : EBP_PIX(e0, e1, 0) - 16];
+          if (I[a] > 0) {
+            sum += lo;
+            dg += 1;
+          } else if (f.bc[2 * a]) {
+            sum += hi * third;
+            dg += 3;
+          }
+          if (I[a] < f.n[a] - 1) {
+            sum += hi;
+            dg += 1;
+          } else if (f.bc[2 * a + 1]) {
+            sum += lo * third;
+            dg += 3;
+          }
+        }
+        const T xc = P[D == 3 ? EBP_PIX(0, 0, 0) : EBP_PIX(0, 0, 0) - 16];
+#undef EBP_PIX
+        (void)loc;
+        acc[q] += bv[k] - f.ceps[q] * ((T)dg * xc - sum);
+      }
+    }
+    for (int p = 0; p < 2; ++p) {
+      if (co.b[p] == nullptr) continue;
+      co.b[p][C] = ((cfl >> p) & 1u) ? acc[p] * scale : T(0);
+      co.x[p][C] = T(0);
+    }
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void ph_restrict_pt(const Op<T>& f, const Op<T>& co, const Ctx& c);
+
 template <class T>
 __device__ __forceinline__ void ph_restrict(const Op<T>& f, const Op<T>& co, const Ctx& c) {
+  bool blk = true;
+  for (int a = 0; a < f.D; ++a)
+    if (f.n[a] != 2 * co.n[a]) blk = false;
+  if (blk) {
+    if (f.D == 3) ph_restrict_blk<T, 3>(f, co, c);
+    else ph_restrict_blk<T, 2>(f, co, c);
+    return;
+  }
+  ph_restrict_pt(f, co, c);
+}
+
+template <class T>
+__device__ __forceinline__ void ph_restrict_pt(const Op<T>& f, const Op<T>& co, const Ctx& c) {
   int nch = 1 << f.D;
   T scale = T(1) / T(nch);
   for (long long C = c.i0; C < co.ncell; C += c.st) {
