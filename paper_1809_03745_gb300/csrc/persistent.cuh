@@ -25,6 +25,10 @@ struct Hier {
   int bsweeps;  // relaxation sweeps when bm == 0
   int smem;     // 1: levels lc.. keep x, b, flags and row scratch in CTA 0's shared memory
   int gbot;     // 1: the bottom is a grid phase, a row-major dense inverse applied one warp per row
+  int gkry;     // 1: the bottom is a grid phase, BiCGStab over the whole grid (no inverse, > 4096 cells)
+  int kry_iters;     // its iteration cap
+  T* kry;            // its vectors: 6 x [2][ncell] of the bottom level
+  double* kpart;     // its per-CTA partial sums: [2 buffers][CTAs][2]
   int smem_bytes;
   const T* binv;  // [bm][bm], slot s = p * ncell + c of the coarsest level
   int off_x[MAXLEV][2], off_b[MAXLEV][2], off_f[MAXLEV], off_t[MAXLEV];  // byte offsets into shared memory
@@ -850,6 +854,170 @@ __device__ void coarse_part(const Hier<T>& H, const Op<T>* lop, const Ctx& L) {
   }
 }
 
+// ---------------------------------------------------------------- Krylov bottom
+// Sum over the CTA in a fixed order (tree over warps): deterministic.
+__device__ __forceinline__ double cta_sum(double v) {
+  __shared__ double part[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) part[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < nw; ++k) t += part[k];
+  return t;
+}
+
+// Two grid-wide sums at once: each CTA stores its partials in buffer `buf`,
+// the grid barrier follows, then every thread adds the partials in CTA order
+// (deterministic).  Consecutive reductions alternate buffers, so a CTA never
+// overwrites partials another CTA may still be reading.
+__device__ __forceinline__ bool grid_sum2(double* kpart, int buf, double a, double b, const Ctx& c, int code,
+                                          double& sa, double& sb) {
+  a = cta_sum(a);
+  b = cta_sum(b);
+  double* pb = kpart + (long long)buf * 2 * c.gsize;
+  if (threadIdx.x == 0) {
+    pb[2 * c.gcta] = a;
+    pb[2 * c.gcta + 1] = b;
+  }
+  if (!c.sync(code)) return false;
+  // warp 0 reads the partials through L2 (lane j takes CTAs j, j + 32, ...)
+  // and reduces them by a fixed shuffle tree: the same sums in every CTA
+  __shared__ double res[2];
+  if (threadIdx.x < 32) {
+    double ta = 0.0, tb = 0.0;
+    for (int k = threadIdx.x; k < c.gsize; k += 32) {
+      ta += __ldcg(pb + 2 * k);
+      tb += __ldcg(pb + 2 * k + 1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ta += __shfl_xor_sync(0xffffffffu, ta, o);
+      tb += __shfl_xor_sync(0xffffffffu, tb, o);
+    }
+    if (threadIdx.x == 0) {
+      res[0] = ta;
+      res[1] = tb;
+    }
+  }
+  __syncthreads();
+  sa = res[0];
+  sb = res[1];
+  __syncthreads();
+  return true;
+}
+
+// z = A y on the bottom level (its own operator: implicit regular stencil,
+// sparse cut-cell rows; entries without an unknown 0), grid-stride over cells;
+// returns this thread's partial of (w, z) and (z, z) when w is given
+template <class T>
+__device__ __forceinline__ void bot_matvec_grid(const Op<T>& o, const T* y, T* z, const Ctx& c) {
+  const long long n = o.ncell;
+  for (long long cc = c.i0; cc < n; cc += c.st) {
+    const uint8_t f = o.flags[cc];
+    for (int p = 0; p < 2; ++p) {
+      T acc = T(0);
+      if ((f >> p) & 1) {
+        if (f & F_IRR) {
+          const long long r = 2 * (long long)o.irr_of_cell[cc] + p;
+          double a = o.diag[r] * (double)y[p * n + cc];
+          for (int e = o.row_ptr[r]; e < o.row_ptr[r + 1]; ++e) {
+            const unsigned cl = (unsigned)o.col[e];
+            a += o.val[e] * (double)y[(long long)(cl >> 30) * n + (cl & 0x3fffffffu)];
+          }
+          acc = (T)a;
+        } else {
+          int I[3];
+          ijk(o, cc, I);
+          T sum;
+          int dg;
+          reg_stencil(o, y + p * n, I, cc, sum, dg);
+          acc = o.ceps[p] * ((T)dg * y[p * n + cc] - sum);
+        }
+      }
+      z[p * n + cc] = acc;
+    }
+  }
+}
+
+// BiCGStab on the bottom level over the whole grid, from x = 0, until
+// |r|_2 <= 1e-3 |b|_2 or kry_iters iterations.  Every thread computes the same
+// scalars from the same ordered sums, so all CTAs take the same path through
+// the five grid barriers of an iteration.
+template <class T>
+__device__ bool ph_bicgstab_grid(const Hier<T>& H, const Ctx& c) {
+  const int code = ((H.nlev - 1) << 4) | 9;
+  const Op<T>& o = H.op[H.nlev - 1];
+  if (c.gsize > 1024) return ph_smooth(o, H.bsweeps, c, H.nlev - 1);  // partial sums sized for 1024 CTAs
+  const long long n = o.ncell, m = 2 * n;
+  T *r = H.kry, *r0 = r + m, *pv = r0 + m, *v = pv + m, *sv = v + m, *t = sv + m;
+  int buf = 0;
+  double la = 0.0, lb = 0.0;
+  for (long long cc = c.i0; cc < n; cc += c.st) {
+    const uint8_t f = o.flags[cc];
+    for (int p = 0; p < 2; ++p) {
+      const long long i = p * n + cc;
+      const T bi = (((f >> p) & 1) && o.b[p]) ? o.b[p][cc] : T(0);
+      r[i] = r0[i] = bi;
+      pv[i] = v[i] = T(0);
+      if (o.x[p]) o.x[p][cc] = T(0);
+      la += (double)bi * (double)bi;
+    }
+  }
+  double bb = 0.0, rho1 = 0.0;
+  if (!grid_sum2(H.kpart, buf, la, la, c, code, bb, rho1)) return false;
+  buf ^= 1;
+  if (!(bb > 0.0)) return true;
+  double rho = 1.0, alpha = 1.0, omega = 1.0;
+  for (int it = 0; it < H.kry_iters; ++it) {
+    if (rho1 == 0.0 || omega == 0.0) break;
+    const double beta = (rho1 / rho) * (alpha / omega);
+    for (long long i = c.i0; i < m; i += c.st) pv[i] = (T)((double)r[i] + beta * ((double)pv[i] - omega * (double)v[i]));
+    if (!c.sync(code)) return false;
+    bot_matvec_grid(o, pv, v, c);
+    la = 0.0;
+    for (long long cc = c.i0; cc < n; cc += c.st)
+      for (int p = 0; p < 2; ++p) la += (double)r0[p * n + cc] * (double)v[p * n + cc];
+    double rv = 0.0, dummy = 0.0;
+    if (!grid_sum2(H.kpart, buf, la, 0.0, c, code, rv, dummy)) return false;
+    buf ^= 1;
+    if (rv == 0.0) break;
+    alpha = rho1 / rv;
+    for (long long i = c.i0; i < m; i += c.st) sv[i] = (T)((double)r[i] - alpha * (double)v[i]);
+    if (!c.sync(code)) return false;
+    bot_matvec_grid(o, sv, t, c);
+    la = lb = 0.0;
+    for (long long cc = c.i0; cc < n; cc += c.st)
+      for (int p = 0; p < 2; ++p) {
+        const double tv = (double)t[p * n + cc];
+        la += tv * (double)sv[p * n + cc];
+        lb += tv * tv;
+      }
+    double ts = 0.0, tt = 0.0;
+    if (!grid_sum2(H.kpart, buf, la, lb, c, code, ts, tt)) return false;
+    buf ^= 1;
+    omega = tt > 0.0 ? ts / tt : 0.0;
+    la = lb = 0.0;
+    for (long long i = c.i0; i < m; i += c.st) {
+      const int p = (int)(i / n);
+      const long long cc = i - p * n;
+      if (o.x[p] && ((o.flags[cc] >> p) & 1))
+        o.x[p][cc] = (T)((double)o.x[p][cc] + alpha * (double)pv[i] + omega * (double)sv[i]);
+      const double ri = (double)sv[i] - omega * (double)t[i];
+      r[i] = (T)ri;
+      la += (double)r0[i] * ri;
+      lb += ri * ri;
+    }
+    double rho_next = 0.0, rr = 0.0;
+    if (!grid_sum2(H.kpart, buf, la, lb, c, code, rho_next, rr)) return false;
+    buf ^= 1;
+    rho = rho1;
+    rho1 = rho_next;
+    if (rr <= 1e-6 * bb) break;
+  }
+  return true;
+}
+
 template <class T>
 __device__ bool vcycle_dev(const Hier<T>& H, const Op<T>* lop, const Ctx& G) {
   for (int l = 0; l < H.lc; ++l) {
@@ -864,6 +1032,9 @@ __device__ bool vcycle_dev(const Hier<T>& H, const Op<T>* lop, const Ctx& G) {
   }
   if (H.gbot) {
     if (!ph_bottom_grid(H, G)) return false;
+  } else if (H.gkry) {
+    if (!ph_bicgstab_grid(H, G)) return false;
+    if (!G.sync(((H.nlev - 1) << 4) | 9)) return false;
   } else {
     if (G.gcta == 0) {
       Ctx L{(long long)threadIdx.x, (long long)blockDim.x, true, G.B, G.epoch, G.tr, G.tn, 0, 1};

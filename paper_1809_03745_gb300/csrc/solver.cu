@@ -478,10 +478,13 @@ static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
   // (Set-up costs ~2 m^3 flops through L2: ~7 ms at m = 1024, ~260 ms at
   // m = 3500, which a serving loop pays per admitted request.)
   const bool big_bottom = m > 256 && m <= 1024;
-  if (big_bottom) H.lc = P->nlev - 1;
+  // a bottom of more than 4096 cells (coarsening stopped early) and no inverse
+  // is solved by BiCGStab over the whole grid
+  const bool krylov_bottom = m > 1024 && ob.ncell > 4096;
+  if (big_bottom || krylov_bottom) H.lc = P->nlev - 1;
   while (H.lc < P->nlev - 1 && layout(H.lc, false) > SMEM_CAP) ++H.lc;
   long long sb = layout(H.lc, false);
-  H.smem = (sb <= SMEM_CAP && !big_bottom) ? 1 : 0;
+  H.smem = (sb <= SMEM_CAP && !big_bottom && !krylov_bottom) ? 1 : 0;
   H.smem_bytes = H.smem ? (int)sb : 0;
   if (H.smem) layout(H.lc, true);
   for (int l = 0; l < P->nlev; ++l) H.op[l] = ops[l];
@@ -551,6 +554,13 @@ static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
     if (st == EB_OK && H.bm == 0) cudaGetLastError();
   }
   if (st != EB_OK) return st;
+  if (krylov_bottom && H.bm == 0) {
+    H.kry = (T*)dev_alloc(P->allocs, sizeof(T) * 12 * (size_t)ob.ncell, &P->bytes, &st);
+    H.kpart = (double*)dev_alloc(P->allocs, sizeof(double) * 2 * 2 * 1024, &P->bytes, &st);  // up to 1024 CTAs
+    H.kry_iters = std::max(16, P->o.bottom_sweeps);
+    H.gkry = st == EB_OK ? 1 : 0;
+    if (st != EB_OK) return st;
+  }
   P->bm = H.bm;
   P->smem_bytes = H.smem_bytes;
   P->d_hier = dev_alloc(P->allocs, sizeof(Hier<T>), &P->bytes, &st);
