@@ -194,3 +194,17 @@ def test_bounded_barrier_wait_expires_with_timeout_status():
     assert ei.value.status == E.EB_ERR_TIMEOUT
     phi, info = P.solve(torch.from_numpy(S), torch.from_numpy(sig))
     assert info["status"] == 0 and info["rel_res"] <= 1e-10
+
+
+@pytest.mark.parametrize("launch_mode", [1, 2])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multi_launch_paths_match_oracle(launch_mode, precision, oracles):
+    """The captured-graph (1) and plain (2) multi-launch paths, used as the
+    one-launch-per-phase baselines, solve the same system as the oracle."""
+    name, d, S, sig = CASES[1]  # 200^2: odd coarse sizes and a relaxation bottom
+    og, ophi = oracles[name][:2]
+    P = E.Poisson(E.Geometry(d), precision=precision, tol=1e-12, max_cycles=400, launch_mode=launch_mode)
+    phi, info = P.solve(torch.from_numpy(S), torch.from_numpy(sig))
+    assert info["status"] == 0, info
+    assert info["kernel_launches"] > 4  # many launches: not the persistent kernel
+    assert np.abs(phi.cpu().numpy() - ophi).max() <= 1e-9 * np.abs(ophi).max(), info
