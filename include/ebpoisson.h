@@ -312,8 +312,8 @@ eb_status eb_amr_residual(eb_amr* A, const double* d_rhs_c, const double* d_sig_
  * composite iterations): restarted FGMRES (restart 12, FP64) preconditioned
  * by one FAC step: a coarse correction over the domain (fine part averaged
  * under the box), constant per parent on the fine grid, then a fine
- * correction on the box with zero Dirichlet data on its CF sides, both by the
- * persistent multigrid solve to 1e-2.  d_phi_c / d_phi_f hold the guess on
+ * correction on the box with zero Dirichlet data on its CF sides, each one V-cycle
+ * of the persistent multigrid solve.  d_phi_c / d_phi_f hold the guess on
  * entry; on return d_phi_c under the box holds the fine means.  info:
  * outer_iters = FGMRES iterations, vcycles = V-cycles of the corrections.
  * The work space (27 composite vectors) is allocated at the first call. */
