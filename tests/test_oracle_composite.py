@@ -120,3 +120,22 @@ def test_dielectric_at_cf_side_rejected():
     d = W.coaxial_2d(64)
     with pytest.raises(oracle.OracleError):
         Composite(d, [40, 28], [48, 36])  # crosses the dielectric shell
+
+
+def test_planted_linear_tangential_interpolation_breaks_exactness(monkeypatch):
+    """Plant a mistake in the oracle: linear instead of quadratic tangential
+    weights.  The quadratic-exactness pin must then fail, so it does test the
+    coarse-fine interpolation."""
+    import oracle.composite as OC
+    monkeypatch.setattr(OC, "_tangential_weights", lambda off: (-off if off < 0 else 0.0, 1.0 - abs(off),
+                                                                off if off > 0 else 0.0))
+    n = 32
+    d = W._desc(2, (n, n), (0, 0), 1.0 / n, [(W.PRIM_SPHERE, [0.2, 0.2, 0.0, 0.1])], [(0, 0, 0)], 0, -1,
+                (1.0, 1.0), [1] * 4 + [0, 0], 0.0, [0] * 6)
+    C = OC.Composite(d, [16, 16], [24, 24])
+    c = np.array([0.3, -0.7, 0.4, 1.1, -0.6, 0.9])
+
+    def phi(x, y, z):
+        return c[0] + c[1] * x + c[2] * y + c[3] * x * x + c[4] * y * y + c[5] * x * y
+    rel, *_ = _quadratic_truncation(C, phi, 2 * (c[3] + c[4]))
+    assert rel > 1e-8

@@ -161,3 +161,20 @@ def test_sphere_volume_second_order():
         vol = g.kappa[0].sum() * g.h ** 3
         errs.append(abs(vol - (1.0 - 4.0 / 3.0 * math.pi * 0.31 ** 3)))
     assert math.log2(errs[0] / errs[1]) > 1.8, errs
+
+
+def test_pin_plane_solution_mirror_symmetric():
+    """The pin-plane geometry and line charge are symmetric under x -> 1-x,
+    y -> 1-y and x <-> y; so is the discrete solution (the EB centroid of a
+    curved cut is fanned about the crossing loop's vertex mean, independent of
+    where the loop starts)."""
+    n = 24
+    d, S, s = W.c3_inputs(n)
+    g, phi, A, b, data = oracle.solve(d, s=S, sigma=s)
+    f = phi[0].reshape(n, n, n)
+    m = np.abs(f).max()
+    assert np.abs(f - f[:, :, ::-1]).max() <= 1e-12 * m
+    assert np.abs(f - f[:, ::-1, :]).max() <= 1e-12 * m
+    assert np.abs(f - f.transpose(0, 2, 1)).max() <= 1e-12 * m
+    k = g.kappa[0].reshape(n, n, n)
+    assert np.abs(k - k[:, :, ::-1]).max() <= 1e-13
