@@ -1,0 +1,59 @@
+"""Host-side logic on the CPU: the bench's algorithmic-bytes model, the
+serving trace's FIFO baseline and percentiles, and the batched-instance
+sampler's stated readings (sizes, seeds, thickness clamps)."""
+import math
+
+import numpy as np
+import pytest
+
+import bench
+from paper_1809_03745_gb300 import serve_trace as T
+from paper_1809_03745_gb300 import workloads as W
+
+
+def test_solve_bytes_model():
+    # per fine cell and V-cycle: 4 sweeps x 12 B + residual/restriction 9 B + prolongation 9 B = 66 B
+    # in 2D FP32, times the level sum 4/3 = 88 B; FP64 doubles it; 3D uses 8/7 and 2^3 children
+    assert bench.solve_bytes(1, 2, True, 1, 0) == pytest.approx(88.0 + 24.0)
+    assert bench.solve_bytes(1, 2, False, 1, 0) == pytest.approx(176.0 + 24.0)
+    per3 = (48 + 8 + 0.5 + 0.5 + 8) * 8 / 7
+    assert bench.solve_bytes(1, 3, True, 1, 0) == pytest.approx(per3 + 24.0)
+    # outer iterations add the FP64 residual (24 B) and update (20 B); linear in cells
+    assert bench.solve_bytes(1000, 2, True, 14, 7) == pytest.approx(1000 * (14 * 88 + 7 * 44 + 24))
+
+
+def test_fifo_latency_and_percentiles():
+    # arrivals (s) and service times (ms): a single FIFO server
+    lat = T.fifo_latency([0.0, 0.001, 0.5], [10.0, 10.0, 10.0])
+    assert lat == pytest.approx([10.0, 19.0, 10.0])
+    x = list(range(1, 101))
+    assert T.pct(x, 0.5) == 50 and T.pct(x, 0.99) == 99 and T.pct(x, 1.0) == 100
+    assert T.pct([7.0], 0.99) == 7.0
+
+
+def test_batched_instances_follow_their_readings():
+    inst = W.batched_instances(count=40)
+    again = W.batched_instances(count=40)
+    dims = set()
+    for (d, S, s), (d2, S2, s2) in zip(inst, again):
+        assert d == d2 and np.array_equal(S, S2)  # seeded: identical on every call
+        n, D = d["n"][0], d["dim"]
+        dims.add(D)
+        assert n % 16 == 0 and all(d["n"][k] == n for k in range(D))
+        lo, hi = (32, 192) if D == 3 else (64, 1024)
+        assert lo - 8 <= n <= hi + 8
+        h = d["h"]
+        assert math.isclose(h, 1.0 / n)
+        tip_r = d["prims"][0][1][-1]
+        assert tip_r >= 3 * h - 1e-12  # tip radius clamped to at least 3 cells
+        assert S.shape == (2, W.ncells(d)) and np.all(S[1] == 0.0) and S[0].max() > 0.0
+    assert dims == {2, 3}
+    small = W.batched_instances(count=20, max_cells=40000)
+    assert all(W.ncells(d) <= 40000 for d, _, _ in small)
+
+
+def test_refined_box_description():
+    d = W.pin_plane_3d(64)
+    f = W.refined_box_desc(d, [24, 24, 24], [40, 40, 40])
+    assert f["n"] == (32, 32, 32) and f["h"] == d["h"] / 2
+    assert f["lo"] == pytest.approx((24 / 64, 24 / 64, 24 / 64))
