@@ -35,6 +35,23 @@ N_CELLS_SIDE = 1024
 REF_SIDE = 256   # oracle sample size per step
 
 
+
+KERNEL_SOURCES = ("persistent.cuh", "mg_kernels.cuh", "eb_common.cuh", "solver.cu")
+
+
+def kernel_sources_sha256(read=None) -> str:
+    """SHA-256 over the sources the persistent solve kernel and its launch are
+    built from; `read(name)` returns a file's bytes (default: the working tree)."""
+    import hashlib
+    if read is None:
+        def read(name):
+            with open(os.path.join(ROOT, "paper_1809_03745_gb300", "csrc", name), "rb") as f:
+                return f.read()
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update(name.encode() + b"\0" + read(name))
+    return h.hexdigest()
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -272,7 +289,10 @@ def run_gpu(args):
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         try:
-            traffic = json.load(open(prof)).get("k_solve_fp32_c2_1024", None)
+            rec = json.load(open(prof))
+            # counters taken on another version of the kernel's sources do not count
+            if rec.get("sources_sha256") == kernel_sources_sha256():
+                traffic = rec.get("k_solve_fp32_c2_1024", None)
         except Exception:
             traffic = None
     cpu = None

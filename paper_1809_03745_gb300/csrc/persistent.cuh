@@ -32,6 +32,10 @@ struct Hier {
   int smem_bytes;
   const T* binv;  // [bm][bm], slot s = p * ncell + c of the coarsest level
   int off_x[MAXLEV][2], off_b[MAXLEV][2], off_f[MAXLEV], off_t[MAXLEV];  // byte offsets into shared memory
+  // levels lc.. whose sparse rows are staged in shared memory too (srows = 1):
+  // offsets of row_ptr, col, val, diag, irr_cell, irr_of_cell, and the entry count
+  int srows[MAXLEV], off_rp[MAXLEV], off_col[MAXLEV], off_val[MAXLEV], off_dg[MAXLEV], off_ic[MAXLEV],
+      off_io[MAXLEV], rnnz[MAXLEV];
   Op<T> op[MAXLEV];
 };
 
@@ -1095,6 +1099,13 @@ __device__ __forceinline__ double load_norm(const unsigned long long* p) {
 }
 
 // The solve: residual, test, (inner V-cycles, update)*, until converged or capped.
+// copy of `words` 4-byte words from global into shared memory by the whole CTA
+__device__ __forceinline__ void stage_words(unsigned char* dst, const void* src, long long words) {
+  const int* s = (const int*)src;
+  int* d = (int*)dst;
+  for (long long i = threadIdx.x; i < words; i += blockDim.x) d[i] = s[i];
+}
+
 template <class T>
 __device__ __forceinline__ void solve_group(const Hier<T>* __restrict__ Hg, const Op<double>* __restrict__ Fg,
                                             const SolveCtl& ctl, const Barrier& B, int gcta, int gsize) {
@@ -1128,12 +1139,31 @@ __device__ __forceinline__ void solve_group(const Hier<T>* __restrict__ Hg, cons
         }
         v.flags = (const uint8_t*)(dyn + H.off_f[l]);
         v.tmp = (T*)(dyn + H.off_t[l]);
+        if (H.srows[l]) {
+          v.row_ptr = (const int*)(dyn + H.off_rp[l]);
+          v.col = (const int*)(dyn + H.off_col[l]);
+          v.val = (const double*)(dyn + H.off_val[l]);
+          v.diag = (const double*)(dyn + H.off_dg[l]);
+          v.irr_cell = (const int*)(dyn + H.off_ic[l]);
+          v.irr_of_cell = (const int*)(dyn + H.off_io[l]);
+        }
       }
       lop[l] = v;
     }
     if (H.smem)
-      for (int l = H.lc; l < H.nlev; ++l)
-        for (long long c = threadIdx.x; c < H.op[l].ncell; c += blockDim.x) dyn[H.off_f[l] + c] = H.op[l].flags[c];
+      for (int l = H.lc; l < H.nlev; ++l) {
+        const Op<T>& g = H.op[l];
+        for (long long c = threadIdx.x; c < g.ncell; c += blockDim.x) dyn[H.off_f[l] + c] = g.flags[c];
+        if (H.srows[l]) {  // the level's rows are constant over the launch: staged once
+          const long long nr = 2 * g.nirr;
+          stage_words(dyn + H.off_rp[l], g.row_ptr, nr + 1);
+          stage_words(dyn + H.off_col[l], g.col, H.rnnz[l]);
+          stage_words(dyn + H.off_val[l], g.val, 2 * (long long)H.rnnz[l]);
+          stage_words(dyn + H.off_dg[l], g.diag, 2 * nr);
+          stage_words(dyn + H.off_ic[l], g.irr_cell, g.nirr);
+          stage_words(dyn + H.off_io[l], g.irr_of_cell, g.ncell);
+        }
+      }
   }
   __syncthreads();
   // warps of the grid interleaved over the CTAs: lanes stay on consecutive

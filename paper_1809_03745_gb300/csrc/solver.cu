@@ -487,6 +487,30 @@ static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
   H.smem = (sb <= SMEM_CAP && !big_bottom && !krylov_bottom) ? 1 : 0;
   H.smem_bytes = H.smem ? (int)sb : 0;
   if (H.smem) layout(H.lc, true);
+  // the sparse rows of those levels (constant over a solve) join them while
+  // the total stays under ROWS_CAP, level by level from the finest of them:
+  // the row phases inside CTA 0 then make no L2 round trip
+  if (H.smem) {
+    const long long ROWS_CAP = 200 * 1024;
+    auto al = [](long long b) { return (b + 15) / 16 * 16; };
+    long long off = sb;
+    for (int l = H.lc; l < P->nlev; ++l) {
+      const long long nirr = ops[l].nirr, nr = 2 * nirr, nnz = P->G->L[l].nnz, nc = ops[l].ncell;
+      if (nr == 0) continue;
+      const long long need = al(4 * (nr + 1)) + al(4 * nnz) + al(8 * nnz) + al(8 * nr) + al(4 * nirr) + al(4 * nc);
+      if (off + need > ROWS_CAP) continue;
+      H.off_rp[l] = (int)off;
+      H.off_col[l] = (int)(off += al(4 * (nr + 1)));
+      H.off_val[l] = (int)(off += al(4 * nnz));
+      H.off_dg[l] = (int)(off += al(8 * nnz));
+      H.off_ic[l] = (int)(off += al(8 * nr));
+      H.off_io[l] = (int)(off += al(4 * nirr));
+      off += al(4 * nc);
+      H.rnnz[l] = (int)nnz;
+      H.srows[l] = 1;
+    }
+    H.smem_bytes = (int)off;
+  }
   for (int l = 0; l < P->nlev; ++l) H.op[l] = ops[l];
   eb_status st = EB_OK;
   // dense inverse of the coarsest operator (FP64 Gauss-Jordan on the device)

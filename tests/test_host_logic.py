@@ -1,7 +1,9 @@
 """Host-side logic on the CPU: the bench's algorithmic-bytes model, the
 serving trace's FIFO baseline and percentiles, and the batched-instance
 sampler's stated readings (sizes, seeds, thickness clamps)."""
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -57,3 +59,17 @@ def test_refined_box_description():
     f = W.refined_box_desc(d, [24, 24, 24], [40, 40, 40])
     assert f["n"] == (32, 32, 32) and f["h"] == d["h"] / 2
     assert f["lo"] == pytest.approx((24 / 64, 24 / 64, 24 / 64))
+
+
+def test_traffic_record_is_tied_to_kernel_sources():
+    """The DRAM traffic of profiles/traffic.json counts only for the sources it
+    was captured on: the hash changes with any one of them."""
+    import bench
+    files = {n: n.encode() * 3 for n in bench.KERNEL_SOURCES}
+    h0 = bench.kernel_sources_sha256(lambda n: files[n])
+    assert h0 == bench.kernel_sources_sha256(lambda n: files[n])
+    for n in bench.KERNEL_SOURCES:
+        changed = dict(files, **{n: files[n] + b" "})
+        assert bench.kernel_sources_sha256(lambda m: changed[m]) != h0
+    rec = json.load(open(os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")))
+    assert len(rec["sources_sha256"]) == 64 and rec["k_solve_fp32_c2_1024"] > 0
