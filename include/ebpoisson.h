@@ -239,7 +239,8 @@ eb_status eb_poisson_solve(eb_poisson* P, const double* d_rhs, const double* d_s
  * of its own, so instances finish independently.  P, d_rhs, d_sigma and d_phi
  * are host arrays of n entries (d_sigma may be NULL, or hold NULL entries);
  * infos (n entries) may be NULL.  Each result equals the single solve of the
- * same instance up to rounding.  Returns the first non-OK instance status. */
+ * same instance up to rounding.  A handle may appear once per batch
+ * (EB_ERR_INVALID otherwise).  Returns the first non-OK instance status. */
 eb_status eb_poisson_solve_batched(eb_poisson* const* P, int n, const double* const* d_rhs,
                                    const double* const* d_sigma, double* const* d_phi, eb_solve_info* infos,
                                    void* stream);

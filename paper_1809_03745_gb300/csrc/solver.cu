@@ -1166,6 +1166,14 @@ extern "C" eb_status eb_poisson_solve_batched(eb_poisson* const* P, int n, const
       set_error("null instance");
       return EB_ERR_INVALID;
     }
+  {  // a handle twice in one batch would have two CTA groups share its work arrays and barrier
+    std::vector<eb_poisson*> h(P, P + n);
+    std::sort(h.begin(), h.end());
+    if (std::adjacent_find(h.begin(), h.end()) != h.end()) {
+      set_error("a solver handle appears twice in the batch");
+      return EB_ERR_INVALID;
+    }
+  }
   cudaStream_t s = (cudaStream_t)stream;
   long long launches = 0;
   g_count = &launches;

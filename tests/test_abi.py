@@ -50,6 +50,13 @@ def test_status_strings_and_validation_without_gpu():
     assert st == E.EB_ERR_INVALID
     assert b"multiple of 8" in lib.eb_last_error()
     assert not h.value
+    # a handle twice in one batch is refused before any handle is read
+    fake = ctypes.c_void_p(0x1000)
+    hs = (ctypes.c_void_p * 2)(fake, fake)
+    ptrs = (ctypes.c_void_p * 2)(0x2000, 0x3000)
+    st = lib.eb_poisson_solve_batched(hs, 2, ptrs, None, ptrs, None, None)
+    assert st == E.EB_ERR_INVALID
+    assert b"twice" in lib.eb_last_error()
 
 
 def test_binding_refuses_to_run_without_library(monkeypatch, tmp_path):
