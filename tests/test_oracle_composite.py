@@ -7,7 +7,8 @@
   adds the two 1-D corrections, no cross term);
 - exact conservation for arbitrary phi with the rod crossing the box sides
   (cut CF faces): the fine fluxes through every CF face enter the coarse row
-  with the opposite sign;
+  with the opposite sign; the same in 3D with a pin through the top side, and
+  a planted mistake (the coarse operator's own CF-side flux kept) breaks it;
 - second-order convergence of the coaxial closed form (Sec. 4.2) with a box
   in the gas shell;
 - a box covering the whole domain reduces to the plain fine-grid problem;
@@ -139,3 +140,32 @@ def test_planted_linear_tangential_interpolation_breaks_exactness(monkeypatch):
         return c[0] + c[1] * x + c[2] * y + c[3] * x * x + c[4] * y * y + c[5] * x * y
     rel, *_ = _quadratic_truncation(C, phi, 2 * (c[3] + c[4]))
     assert rel > 1e-8
+
+
+def _conservation_gap_3d(C):
+    gc, gf = C.gc, C.gf
+    A, b = C.assemble(sc=np.zeros((2, gc.ncell)), sf=np.zeros((2, gf.ncell)))
+    x = np.random.default_rng(2).normal(size=C.n)
+    vol = np.concatenate([np.full(C.nco, gc.h ** 3), np.full(gf.ndof, gf.h ** 3)])
+    terms = vol * (b - A @ x)
+    return abs(terms.sum() - C.boundary_flux(x)) / np.abs(terms).sum()
+
+
+def test_composite_conservation_3d_pin_crossing_cf_side():
+    """3D: a pin of radius 0.1 through the top side of the box [4, 12)^3 of a
+    16^3 grid cuts CF faces; for arbitrary phi the volume-weighted residuals
+    still sum to the wall and EB fluxes alone."""
+    d = W.pin_plane_3d(16, radius=0.1, disk=False)
+    C = Composite(d, [4, 4, 4], [12, 12, 12])
+    assert any(C.gf.cut[f[2]] for f in C.faces)
+    assert _conservation_gap_3d(C) <= 1e-12
+
+
+def test_planted_missing_coarse_flux_removal_breaks_conservation(monkeypatch):
+    """Plant a mistake in the oracle: keep the coarse operator's own flux
+    through the CF sides next to the box.  The conservation pin must then fail."""
+    import oracle.composite as OC
+    monkeypatch.setattr(OC.Composite, "coarse_cf_faces", lambda self: [])
+    d = W.pin_plane_3d(16, radius=0.1, disk=False)
+    C = OC.Composite(d, [4, 4, 4], [12, 12, 12])
+    assert _conservation_gap_3d(C) > 1e-6
