@@ -36,15 +36,18 @@ OK, INVALID, UNSUPPORTED = 0, 1, 6
 EB_NONE, EB_ELECTRODE, EB_INTERFACE = 0, 1, 2
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/_build/libeb_oracle.so (gcc, no FMA contraction)."""
+def build(force: bool = False, plant: int = 0) -> str:
+    """Compile the oracle into oracle/_build/libeb_oracle.so (gcc, no FMA contraction).
+    plant = k > 0 builds the variant with planted mistake k (see eb_oracle.c) into
+    its own library, for the tests that show the pins catch it."""
     os.makedirs(_LIB_DIR, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+    lib = _LIB if plant == 0 else os.path.join(_LIB_DIR, f"libeb_oracle_plant{int(plant)}.so")
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               f"-DOR_PLANT={int(plant)}", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, lib)
+    return lib
 
 
 class _Desc(C.Structure):
@@ -60,42 +63,50 @@ class _Data(C.Structure):
                 ("phidom", C.POINTER(C.c_double)), ("s", C.POINTER(C.c_double))]
 
 
+def planted(k: int):
+    """The oracle library with planted mistake k, bound like the real one (tests only)."""
+    return _bind(C.CDLL(build(plant=k)))
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = C.CDLL(build())
-            P = C.c_void_p
-            lib.or_geom_build.restype = P
-            lib.or_geom_build.argtypes = [C.POINTER(_Desc), C.POINTER(C.c_int)]
-            lib.or_geom_free.argtypes = [P]
-            for name in ("or_ndof", "or_ncell", "or_n_eb", "or_wall_total", "or_bad_cell"):
-                getattr(lib, name).restype = C.c_long
-                getattr(lib, name).argtypes = [P]
-            lib.or_status.restype = C.c_int
-            lib.or_status.argtypes = [P]
-            lib.or_nface.restype = C.c_long
-            lib.or_nface.argtypes = [P, C.c_int]
-            lib.or_counts.argtypes = [P, C.c_void_p]
-            lib.or_cells.argtypes = [P] + [C.c_void_p] * 7
-            lib.or_faces.argtypes = [P, C.c_int, C.c_void_p, C.c_void_p]
-            lib.or_labels.argtypes = [P, C.c_void_p]
-            lib.or_stencil_order.argtypes = [P, C.c_void_p]
-            lib.or_assemble.restype = C.c_long
-            lib.or_assemble.argtypes = [P, C.POINTER(_Data), C.c_void_p, C.c_void_p, C.c_void_p, C.c_long,
-                                        C.c_void_p]
-            lib.or_boundary_flux.restype = C.c_double
-            lib.or_boundary_flux.argtypes = [P, C.POINTER(_Data), C.c_void_p]
-            lib.or_field.argtypes = [P, C.POINTER(_Data), C.c_void_p, C.c_void_p, C.c_void_p]
-            lib.or_boundary_flux_masked.restype = C.c_double
-            lib.or_boundary_flux_masked.argtypes = [P, C.POINTER(_Data), C.c_void_p, C.c_void_p]
-            lib.or_face_flux.restype = C.c_long
-            lib.or_face_flux.argtypes = [P, C.POINTER(_Data), C.c_int, C.c_void_p, C.c_int, C.c_void_p,
-                                         C.c_void_p, C.c_void_p]
-            lib.or_eval_implicit.restype = C.c_double
-            lib.or_eval_implicit.argtypes = [C.POINTER(_Desc), C.c_int, C.c_void_p]
-            _lib = lib
+            _lib = _bind(C.CDLL(build()))
     return _lib
+
+
+def _bind(lib):
+    P = C.c_void_p
+    lib.or_geom_build.restype = P
+    lib.or_geom_build.argtypes = [C.POINTER(_Desc), C.POINTER(C.c_int)]
+    lib.or_geom_free.argtypes = [P]
+    for name in ("or_ndof", "or_ncell", "or_n_eb", "or_wall_total", "or_bad_cell"):
+        getattr(lib, name).restype = C.c_long
+        getattr(lib, name).argtypes = [P]
+    lib.or_status.restype = C.c_int
+    lib.or_status.argtypes = [P]
+    lib.or_nface.restype = C.c_long
+    lib.or_nface.argtypes = [P, C.c_int]
+    lib.or_counts.argtypes = [P, C.c_void_p]
+    lib.or_cells.argtypes = [P] + [C.c_void_p] * 7
+    lib.or_faces.argtypes = [P, C.c_int, C.c_void_p, C.c_void_p]
+    lib.or_labels.argtypes = [P, C.c_void_p]
+    lib.or_stencil_order.argtypes = [P, C.c_void_p]
+    lib.or_assemble.restype = C.c_long
+    lib.or_assemble.argtypes = [P, C.POINTER(_Data), C.c_void_p, C.c_void_p, C.c_void_p, C.c_long,
+                                C.c_void_p]
+    lib.or_boundary_flux.restype = C.c_double
+    lib.or_boundary_flux.argtypes = [P, C.POINTER(_Data), C.c_void_p]
+    lib.or_field.argtypes = [P, C.POINTER(_Data), C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.or_boundary_flux_masked.restype = C.c_double
+    lib.or_boundary_flux_masked.argtypes = [P, C.POINTER(_Data), C.c_void_p, C.c_void_p]
+    lib.or_face_flux.restype = C.c_long
+    lib.or_face_flux.argtypes = [P, C.POINTER(_Data), C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]
+    lib.or_eval_implicit.restype = C.c_double
+    lib.or_eval_implicit.argtypes = [C.POINTER(_Desc), C.c_int, C.c_void_p]
+    return lib
 
 
 def _ptr(a):
@@ -113,7 +124,7 @@ class Geometry:
     """Cut-cell geometry, dofs and EB stencils of one problem (Sec. 3.1, 3.3.1)."""
 
     def __init__(self, desc: dict):
-        lib = _load()
+        lib = self._lib = _load()  # kept: the geometry lives in this library's memory
         self.desc = desc
         self.dim = int(desc["dim"])
         n = list(desc["n"]) + [1] * (3 - len(desc["n"]))
@@ -179,28 +190,28 @@ class Geometry:
         self.eb_cells = np.nonzero(self.cut.astype(bool) & ((self.dof[0] >= 0) | (self.dof[1] >= 0)))[0]
 
     def __del__(self):
-        if getattr(self, "_g", None) is not None and _lib is not None:
-            _lib.or_geom_free(self._g)
+        if getattr(self, "_g", None) is not None and getattr(self, "_lib", None) is not None:
+            self._lib.or_geom_free(self._g)
             self._g = None
 
     # -- geometry queries ------------------------------------------------
     def faces(self, a: int):
         """(alpha[2][faces], centroid offsets[2][faces][2]) for faces normal to axis a."""
-        nf = _lib.or_nface(self._g, a)
+        nf = self._lib.or_nface(self._g, a)
         al = np.zeros((2, nf))
         fc = np.zeros((2, nf, 2))
-        _lib.or_faces(self._g, a, _ptr(al), _ptr(fc))
+        self._lib.or_faces(self._g, a, _ptr(al), _ptr(fc))
         return al, fc
 
     def labels(self):
         nn = [self.n[k] + 1 if k < self.dim else 1 for k in range(3)]
         lab = np.zeros(nn[0] * nn[1] * nn[2], np.uint8)
-        _lib.or_labels(self._g, _ptr(lab))
+        self._lib.or_labels(self._g, _ptr(lab))
         return lab
 
     def stencil_order(self):
         o = np.zeros((2, self.ncell), np.int32)
-        _lib.or_stencil_order(self._g, _ptr(o))
+        self._lib.or_stencil_order(self._g, _ptr(o))
         return o
 
     def cell_centres(self):
@@ -299,7 +310,7 @@ class Geometry:
         cols = np.zeros(cap, np.int64)
         vals = np.zeros(cap)
         b = np.zeros(self.ndof)
-        nnz = _lib.or_assemble(self._g, C.byref(dt), _ptr(rows), _ptr(cols), _ptr(vals), cap, _ptr(b))
+        nnz = self._lib.or_assemble(self._g, C.byref(dt), _ptr(rows), _ptr(cols), _ptr(vals), cap, _ptr(b))
         if nnz > cap:
             raise RuntimeError("triplet capacity exceeded")
         A = sp.coo_matrix((vals[:nnz], (rows[:nnz], cols[:nnz])), shape=(self.ndof, self.ndof)).tocsr()
@@ -309,13 +320,13 @@ class Geometry:
     def boundary_flux(self, data, phi_dof):
         dt, _keep = data
         phi_dof = np.ascontiguousarray(phi_dof, dtype=np.float64)
-        return _lib.or_boundary_flux(self._g, C.byref(dt), _ptr(phi_dof))
+        return self._lib.or_boundary_flux(self._g, C.byref(dt), _ptr(phi_dof))
 
     def boundary_flux_masked(self, data, phi_dof, mask):
         dt, _keep = data
         phi_dof = np.ascontiguousarray(phi_dof, dtype=np.float64)
         m = np.ascontiguousarray(mask, dtype=np.uint8)
-        return _lib.or_boundary_flux_masked(self._g, C.byref(dt), _ptr(phi_dof), _ptr(m))
+        return self._lib.or_boundary_flux_masked(self._g, C.byref(dt), _ptr(phi_dof), _ptr(m))
 
     def face_flux(self, data, a, J, p):
         """(dof indices, weights, constant) of alpha/h x the +e_a centroid flux of face (a, J)."""
@@ -324,7 +335,7 @@ class Geometry:
         idx = np.zeros(512, np.int64)
         w = np.zeros(512)
         c = np.zeros(1)
-        n = _lib.or_face_flux(self._g, C.byref(dt), a, _ptr(Jv), p, _ptr(idx), _ptr(w), _ptr(c))
+        n = self._lib.or_face_flux(self._g, C.byref(dt), a, _ptr(Jv), p, _ptr(idx), _ptr(w), _ptr(c))
         return idx[:n].copy(), w[:n].copy(), float(c[0])
 
     def field(self, data, phi_dof):
@@ -333,7 +344,7 @@ class Geometry:
         phi_dof = np.ascontiguousarray(phi_dof, dtype=np.float64)
         E = np.zeros((self.dim, 2, self.ncell))
         En = np.zeros((self.ncell, 2))
-        _lib.or_field(self._g, C.byref(dt), _ptr(phi_dof), _ptr(E), _ptr(En))
+        self._lib.or_field(self._g, C.byref(dt), _ptr(phi_dof), _ptr(E), _ptr(En))
         return E, En
 
     # -- layout helpers --------------------------------------------------------

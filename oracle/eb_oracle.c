@@ -31,6 +31,15 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Planted mistakes, for the tests that show each pin catches one: a separate
+ * build with -DOR_PLANT=k (the oracle itself is built with 0, no plant).
+ *   1  the first-order Dirichlet wall flux even where the second-order one applies
+ *   2  face-centre fluxes instead of their interpolation to the face centroid
+ *   3  right-hand side s instead of kappa s in cut cells */
+#ifndef OR_PLANT
+#define OR_PLANT 0
+#endif
+
 /* ---------------------------------------------------------------- inputs */
 
 enum { PR_SPHERE = 0, PR_CAPSULE = 1, PR_HALFSPACE = 2, PR_SINE = 3, PR_CYLINDER = 4, PR_BOX = 5 };
@@ -967,7 +976,7 @@ static int centred_flux(const or_geom* g, const or_data* dt, int a, const long J
   double phi0 = dt->phidom[(long)p * wall_total(g) + wall_index(g, a, hi, C)];
   lform O;
   lf_zero(&O);
-  if (d2 >= 0) {
+  if (d2 >= 0 && OR_PLANT != 1) {
     lf_add(&O, d1, -9.0 * eps / (3.0 * h));
     lf_add(&O, d2, eps / (3.0 * h));
     O.c = 8.0 * eps * phi0 / (3.0 * h);
@@ -988,6 +997,7 @@ static int centroid_flux(const or_geom* g, const or_data* dt, int a, const long 
 {
   lform F00, F10, F01, F11;
   if (!centred_flux(g, dt, a, J, p, &F00)) { lf_zero(F); return 0; }
+  if (OR_PLANT == 2) { *F = F00; return 1; }
   long f = face_id(g, a, J);
   int t[2];
   transverse(g->D, a, t);
@@ -1114,7 +1124,7 @@ long or_assemble(const or_geom* g, const or_data* dt, long* rows, long* cols, do
         if (nnz < cap) { rows[nnz] = r; cols[nnz] = L.idx[k]; vals[nnz] = -L.w[k]; }
         ++nnz;
       }
-      b[r] = g->kappa[p][c] * dt->s[(long)p * g->ncell + c] + L.c;
+      b[r] = (OR_PLANT == 3 ? 1.0 : g->kappa[p][c]) * dt->s[(long)p * g->ncell + c] + L.c;
     }
   return nnz;
 }

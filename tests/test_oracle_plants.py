@@ -1,0 +1,43 @@
+"""Planted mistakes in the oracle, each caught by a pin.
+
+The oracle's C source carries three switches that a separate build turns on
+(-DOR_PLANT=k; the oracle itself is built with none):
+  1  the first-order Dirichlet wall flux where the second-order one-sided
+     formula of Sec. 3.3 applies;
+  2  face-centre fluxes without their interpolation to the face centroid
+     (Sec. 3.3);
+  3  the right-hand side s instead of kappa s (the integral form integrates
+     the source over the cut cell's volume).
+Each must make the quadratic-exactness pin fail, so that pin does test the
+wall formula, the centroid interpolation and the volume weighting.
+"""
+import pytest
+
+import oracle
+import test_oracle_pins as T
+import test_oracle_pins_3d as T3
+
+
+@pytest.fixture
+def plant(monkeypatch):
+    def use(k):
+        monkeypatch.setattr(oracle, "_lib", oracle.planted(k))
+    return use
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_plant_breaks_quadratic_exactness(plant, k):
+    plant(k)
+    with pytest.raises(AssertionError):
+        T.test_quadratic_exactness_single_phase(32, "circle")
+
+
+def test_plant_without_centroid_interpolation_breaks_3d_planar_pin(plant):
+    plant(2)
+    with pytest.raises(AssertionError):
+        T3.test_planar_electrode_truncation_zero(16)
+
+
+def test_unplanted_build_passes_the_same_pins():
+    T.test_quadratic_exactness_single_phase(32, "circle")
+    T3.test_planar_electrode_truncation_zero(16)
