@@ -35,7 +35,8 @@
  * build with -DOR_PLANT=k (the oracle itself is built with 0, no plant).
  *   1  the first-order Dirichlet wall flux even where the second-order one applies
  *   2  face-centre fluxes instead of their interpolation to the face centroid
- *   3  right-hand side s instead of kappa s in cut cells */
+ *   3  right-hand side s instead of kappa s in cut cells
+ *   4  the two permittivities swapped in the boundary-state elimination */
 #ifndef OR_PLANT
 #define OR_PLANT 0
 #endif
@@ -1073,7 +1074,7 @@ static void eb_dphidn(const or_geom* g, const or_data* dt, long c, int p, lform*
   lform Sg, Sd, phiB;
   stencil_form(g, &g->st[0][c], 0, &Sg);
   stencil_form(g, &g->st[1][c], 1, &Sd);
-  double eg = g->d.eps[0], ed = g->d.eps[1];
+  double eg = g->d.eps[OR_PLANT == 4 ? 1 : 0], ed = g->d.eps[OR_PLANT == 4 ? 0 : 1];
   double Dn = eg * g->st[0][c].w0 + ed * g->st[1][c].w0;
   lf_zero(&phiB);
   lf_axpy(&phiB, -eg / Dn, &Sg);

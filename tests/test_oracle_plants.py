@@ -7,9 +7,12 @@ The oracle's C source carries three switches that a separate build turns on
   2  face-centre fluxes without their interpolation to the face centroid
      (Sec. 3.3);
   3  the right-hand side s instead of kappa s (the integral form integrates
-     the source over the cut cell's volume).
-Each must make the quadratic-exactness pin fail, so that pin does test the
-wall formula, the centroid interpolation and the volume weighting.
+     the source over the cut cell's volume);
+  4  the two permittivities swapped where the boundary state of a dielectric
+     interface is eliminated (Sec. 3.3.1, the matching condition).
+Each of 1-3 must make the single-phase quadratic-exactness pin fail, so that
+pin does test the wall formula, the centroid interpolation and the volume
+weighting; 4 must fail the multifluid exactness pin and the coaxial closed form.
 """
 import pytest
 
@@ -38,6 +41,15 @@ def test_plant_without_centroid_interpolation_breaks_3d_planar_pin(plant):
         T3.test_planar_electrode_truncation_zero(16)
 
 
+def test_plant_with_swapped_permittivities_breaks_multifluid_pins(plant):
+    plant(4)
+    with pytest.raises(AssertionError):
+        T.test_quadratic_exactness_multifluid(32)
+    with pytest.raises(AssertionError):
+        T.test_coaxial_closed_form_second_order(0.0)
+
+
 def test_unplanted_build_passes_the_same_pins():
     T.test_quadratic_exactness_single_phase(32, "circle")
     T3.test_planar_electrode_truncation_zero(16)
+    T.test_quadratic_exactness_multifluid(32)
