@@ -178,3 +178,44 @@ def test_pin_plane_solution_mirror_symmetric():
     assert np.abs(f - f.transpose(0, 2, 1)).max() <= 1e-12 * m
     k = g.kappa[0].reshape(n, n, n)
     assert np.abs(k - k[:, :, ::-1]).max() <= 1e-13
+
+
+def test_field_exact_for_quadratic_3d():
+    """E = -grad phi (Sec. 2.1) of a full quadratic (cross terms included) with a
+    tilted planar electrode: centred differences at cell centres and the ray-cast
+    EB stencil at electrode centroids away from the walls are exact."""
+    n = 16
+    c = np.random.default_rng(7).normal(size=10)
+
+    def phi(x, y, z):
+        return (c[0] + c[1] * x + c[2] * y + c[3] * z + c[4] * x * x + c[5] * y * y + c[6] * z * z + c[7] * x * y
+                + c[8] * y * z + c[9] * x * z)
+
+    def grad(x, y, z):
+        return np.stack([c[1] + 2 * c[4] * x + c[7] * y + c[9] * z, c[2] + 2 * c[5] * y + c[7] * x + c[8] * z,
+                         c[3] + 2 * c[6] * z + c[8] * y + c[9] * x])
+    nv = np.array([0.3, 0.5, 0.81])
+    nv /= np.linalg.norm(nv)
+    dd = nv @ np.array([0.37, 0.41, 0.45])
+    d = W._desc(3, (n, n, n), (0, 0, 0), 1.0 / n, [(W.PRIM_HALFSPACE, [nv[0], nv[1], nv[2], dd])], [(0, 0, 0)], 0,
+                -1, (1.0, 1.0), [1] * 6, 0.0, [0] * 6)
+    g = oracle.Geometry(d)
+    pd = _wall_values(g, phi)
+    data = g.data(s=np.zeros((2, g.ncell)), phiE=phi(g.ebx[:, 0], g.ebx[:, 1], g.ebx[:, 2]),
+                  phidom=np.stack([pd, pd]))
+    X, Y, Z = g.cell_centres()
+    E, En = g.field(data, g.to_dofs(np.stack([phi(X, Y, Z)] * 2)))
+    idx = np.arange(g.ncell)
+    i, j, k = idx % n, (idx // n) % n, idx // (n * n)
+    dof = g.dof[0]
+    inner = idx[(i > 0) & (i < n - 1) & (j > 0) & (j < n - 1) & (k > 0) & (k < n - 1) & (dof >= 0) & (g.cut == 0)]
+    both = inner[(dof[inner - 1] >= 0) & (dof[inner + 1] >= 0) & (dof[inner - n] >= 0) & (dof[inner + n] >= 0)
+                 & (dof[inner - n * n] >= 0) & (dof[inner + n * n] >= 0)]
+    assert len(both) > 1000
+    assert np.abs(E[:, 0, both] + grad(X, Y, Z)[:, both]).max() < 1e-12
+    m = 3
+    eb = np.nonzero((g.ebkind == oracle.EB_ELECTRODE) & (i >= m) & (i < n - m) & (j >= m) & (j < n - m)
+                    & (k >= m) & (k < n - m))[0]
+    assert len(eb) > 100
+    dn = (grad(g.ebx[eb, 0], g.ebx[eb, 1], g.ebx[eb, 2]).T * -g.ebn[eb]).sum(1)
+    assert np.abs(En[eb, 0] + dn).max() < 1e-12 * np.abs(dn).max() + 1e-13
