@@ -73,6 +73,13 @@ def _tangential_weights(off):
     return (off * (off - 1.0) / 2.0, 1.0 - off * off, off * (off + 1.0) / 2.0)
 
 
+def _normal_weights(quadratic):
+    """Weights (fine cell at -1/2, fine cell at -3/2, coarse value at +1) of the
+    ghost at +1/2 along the CF normal, in fine-cell units: quadratic Lagrange
+    through the three, or linear through the first and the last."""
+    return (2.0 / 3.0, -1.0 / 5.0, 8.0 / 15.0) if quadratic else (1.0 / 3.0, 0.0, 2.0 / 3.0)
+
+
 class Composite:
     def __init__(self, desc: dict, box_lo, box_hi):
         self.D = D = int(desc["dim"])
@@ -187,10 +194,7 @@ class Composite:
                             # normal step
                             F2 = list(FI)
                             F2[a] += 1 if s == 0 else -1
-                            if self._f_available(F2):
-                                wf, wf2, wc = 2.0 / 3.0, -1.0 / 5.0, 8.0 / 15.0
-                            else:
-                                wf, wf2, wc = 1.0 / 3.0, 0.0, 2.0 / 3.0
+                            wf, wf2, wc = _normal_weights(self._f_available(F2))
                             terms = [("f", int(gf.dof[0][fc]), wf)]
                             if wf2 != 0.0:
                                 terms.append(("f", int(gf.dof[0][self.fcell(F2)]), wf2))

@@ -12,7 +12,9 @@
 - second-order convergence of the coaxial closed form (Sec. 4.2) with a box
   in the gas shell;
 - a box covering the whole domain reduces to the plain fine-grid problem;
-- a dielectric unknown next to a CF side is rejected.
+- a dielectric unknown next to a CF side is rejected;
+- planted mistakes (linear tangential weights, a linear normal step) break
+  the exactness pin.
 """
 import math
 
@@ -169,3 +171,20 @@ def test_planted_missing_coarse_flux_removal_breaks_conservation(monkeypatch):
     d = W.pin_plane_3d(16, radius=0.1, disk=False)
     C = OC.Composite(d, [4, 4, 4], [12, 12, 12])
     assert _conservation_gap_3d(C) > 1e-6
+
+
+def test_planted_linear_normal_interpolation_breaks_exactness(monkeypatch):
+    """Plant a mistake in the oracle: the linear normal step (fine cell at -1/2
+    and coarse value only) everywhere.  The 2D quadratic-exactness pin must fail."""
+    import oracle.composite as OC
+    monkeypatch.setattr(OC, "_normal_weights", lambda quadratic: (1.0 / 3.0, 0.0, 2.0 / 3.0))
+    n = 32
+    d = W._desc(2, (n, n), (0, 0), 1.0 / n, [(W.PRIM_SPHERE, [0.2, 0.2, 0.0, 0.1])], [(0, 0, 0)], 0, -1,
+                (1.0, 1.0), [1] * 4 + [0, 0], 0.0, [0] * 6)
+    C = OC.Composite(d, [16, 16], [24, 24])
+    c = np.array([0.3, -0.7, 0.4, 1.1, -0.6, 0.9])
+
+    def phi(x, y, z):
+        return c[0] + c[1] * x + c[2] * y + c[3] * x * x + c[4] * y * y + c[5] * x * y
+    rel, *_ = _quadratic_truncation(C, phi, 2 * (c[3] + c[4]))
+    assert rel > 1e-8
