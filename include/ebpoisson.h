@@ -371,7 +371,8 @@ eb_status eb_server_submit(eb_server* S, const eb_geom_desc* desc, const double*
  * returns EB_OK, and forgets the ticket.  A failed request returns EB_OK
  * with info->status holding its error.  EB_ERR_INVALID for an unknown ticket. */
 eb_status eb_server_poll(eb_server* S, unsigned long long ticket, double* h_phi, eb_solve_info* info);
-/* eb_server_poll that blocks up to timeout_s seconds (EB_ERR_BUSY after that). */
+/* eb_server_poll that blocks up to timeout_s seconds (EB_ERR_BUSY after that);
+ * timeout_s is clamped to [0, 1e7] (NaN counts as 0, +inf as 1e7). */
 eb_status eb_server_wait(eb_server* S, unsigned long long ticket, double timeout_s, double* h_phi,
                          eb_solve_info* info);
 eb_status eb_server_query(eb_server* S, eb_server_stats* out);

@@ -391,7 +391,9 @@ extern "C" eb_status eb_server_wait(eb_server* S, unsigned long long ticket, dou
     auto it = S->state.find(ticket);
     return it == S->state.end() || it->second == 2;
   };
-  S->cv_done.wait_for(lk, std::chrono::duration<double>(std::max(0.0, timeout_s)), ready);
+  // NaN, negative and infinite timeouts become 0 and 1e7 s: the clock arithmetic must not overflow
+  const double t = std::isfinite(timeout_s) ? std::min(std::max(0.0, timeout_s), 1e7) : (timeout_s > 0 ? 1e7 : 0.0);
+  S->cv_done.wait_for(lk, std::chrono::duration<double>(t), ready);
   auto it = S->state.find(ticket);
   if (it == S->state.end()) {
     set_error("unknown ticket");
