@@ -306,3 +306,30 @@ def test_rejects_cell_cut_by_both_interfaces():
     with pytest.raises(oracle.OracleError) as ei:
         oracle.Geometry(desc)
     assert ei.value.status == oracle.UNSUPPORTED
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_interface_field_satisfies_matching_condition(dim):
+    """Eq. (matching): eps_g dphi/dn_g + eps_d dphi/dn_d = -sigma/eps0 at every
+    dielectric EB.  With phi_B eliminated (Sec. 3.3.1) the two one-sided normal
+    derivatives satisfy it for any phi, so the EB normal field En = -dphi/dn_in
+    of both phases must give eps_g En_g + eps_d En_d = sigma/eps0 exactly, for
+    random phi and a random sigma per cell; eps_g != eps_d catches a swap."""
+    eg, ed = 1.0, 4.0
+    if dim == 2:
+        n = 32
+        desc = W._desc(2, (n, n), (0, 0), 1.0 / n, [(W.PRIM_SPHERE, [0.48, 0.53, 0, 0.27])], [(0, 0, 0)], -1, 0,
+                       (eg, ed), [1, 1, 1, 1, 0, 0], 0.0, [0] * 6)
+    else:
+        n = 16
+        desc = W._desc(3, (n, n, n), (0, 0, 0), 1.0 / n, [(W.PRIM_SPHERE, [0.48, 0.53, 0.51, 0.3])], [(0, 0, 0)],
+                       -1, 0, (eg, ed), [1] * 6, 0.0, [0] * 6)
+    g = oracle.Geometry(desc)
+    rng = np.random.default_rng(dim)
+    sigma = rng.uniform(-1.0, 1.0, size=g.ncell)
+    data = g.data(sigma=sigma)
+    E, En = g.field(data, rng.normal(size=g.ndof))
+    ib = np.nonzero((g.ebkind == oracle.EB_INTERFACE) & (g.dof[0] >= 0) & (g.dof[1] >= 0))[0]
+    assert len(ib) > 20
+    r = eg * En[ib, 0] + ed * En[ib, 1] - sigma[ib]
+    assert np.abs(r).max() <= 1e-10 * np.abs(En[ib]).max()

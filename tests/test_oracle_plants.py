@@ -12,7 +12,8 @@ The oracle's C source carries three switches that a separate build turns on
      interface is eliminated (Sec. 3.3.1, the matching condition).
 Each of 1-3 must make the single-phase quadratic-exactness pin fail, so that
 pin does test the wall formula, the centroid interpolation and the volume
-weighting; 4 must fail the multifluid exactness pin and the coaxial closed form.
+weighting; 4 must fail the multifluid exactness pin, the coaxial closed form and
+the matching condition of the interface field.
 """
 import pytest
 
@@ -47,9 +48,12 @@ def test_plant_with_swapped_permittivities_breaks_multifluid_pins(plant):
         T.test_quadratic_exactness_multifluid(32)
     with pytest.raises(AssertionError):
         T.test_coaxial_closed_form_second_order(0.0)
+    with pytest.raises(AssertionError):
+        T.test_interface_field_satisfies_matching_condition(2)
 
 
 def test_unplanted_build_passes_the_same_pins():
     T.test_quadratic_exactness_single_phase(32, "circle")
     T3.test_planar_electrode_truncation_zero(16)
     T.test_quadratic_exactness_multifluid(32)
+    T.test_interface_field_satisfies_matching_condition(2)
