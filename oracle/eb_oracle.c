@@ -36,7 +36,8 @@
  *   1  the first-order Dirichlet wall flux even where the second-order one applies
  *   2  face-centre fluxes instead of their interpolation to the face centroid
  *   3  right-hand side s instead of kappa s in cut cells
- *   4  the two permittivities swapped in the boundary-state elimination */
+ *   4  the two permittivities swapped in the boundary-state elimination
+ *   5  the first-order EB stencil divided by h instead of the ray length */
 #ifndef OR_PLANT
 #define OR_PLANT 0
 #endif
@@ -671,6 +672,7 @@ static int build_stencil(const or_geom* g, const long I[3], int p, const double 
         cnt++;
       }
     if (ok) {
+      if (OR_PLANT == 5) l = h;
       S->order = 1;
       S->w0 = -1.0 / l;
       for (int k = 0; k < cnt; ++k) { S->cell[S->n] = cells[k]; S->w[S->n] = wts[k] / l; S->n++; }

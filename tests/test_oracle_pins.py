@@ -333,3 +333,34 @@ def test_interface_field_satisfies_matching_condition(dim):
     assert len(ib) > 20
     r = eg * En[ib, 0] + ed * En[ib, 1] - sigma[ib]
     assert np.abs(r).max() <= 1e-10 * np.abs(En[ib]).max()
+
+
+def test_linear_exactness_with_first_order_eb_stencils():
+    """A slot 1.3 cells wide, tilted, between two electrodes: most EB stencils
+    fall back to first order (one plane, linear transverse interpolation;
+    Sec. 3.3.1 allows it where the second plane is not in the fluid), which is
+    still exact for linear phi.  The truncation error and the EB normal field of
+    a linear phi vanish."""
+    n = 32
+    h = 1.0 / n
+    c, s, y0, width = math.cos(0.2), math.sin(0.2), 0.45, 1.3 * h
+    prims = [(W.PRIM_HALFSPACE, [-s, c, 0, -s * 0.5 + c * y0]),
+             (W.PRIM_HALFSPACE, [s, -c, 0, s * 0.5 - c * (y0 + width)])]
+    d = W._desc(2, (n, n), (0, 0), h, prims, [(0, 0, 0), (0, 1, 0), (1, 0, 1)], 2, -1, (1.0, 1.0),
+                [1, 1, 0, 0, 0, 0], 0.0, [0] * 6)
+    g = oracle.Geometry(d)
+    assert g.stencil_counts["order1"] > 40
+    a0, a1, a2 = 0.3, -1.7, 2.3
+
+    def phi(x, y, z):
+        return a0 + a1 * x + a2 * y
+    pd = _wall_values(g, phi)
+    data = g.data(s=np.zeros((2, g.ncell)), phiE=phi(g.ebx[:, 0], g.ebx[:, 1], 0), phidom=np.stack([pd, pd]))
+    A, b = g.assemble(data)
+    X, Y, Z = g.cell_centres()
+    xe = g.to_dofs(np.stack([phi(X, Y, Z)] * 2))
+    assert np.abs(A @ xe - b).max() <= 1e-12 * np.abs(b).max()
+    E, En = g.field(data, xe)
+    eb = np.nonzero(g.ebkind == oracle.EB_ELECTRODE)[0]
+    dn = -(a1 * g.ebn[eb, 0] + a2 * g.ebn[eb, 1])
+    assert np.abs(En[eb, 0] + dn).max() <= 1e-12 * np.abs(dn).max()

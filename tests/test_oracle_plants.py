@@ -9,11 +9,13 @@ The oracle's C source carries three switches that a separate build turns on
   3  the right-hand side s instead of kappa s (the integral form integrates
      the source over the cut cell's volume);
   4  the two permittivities swapped where the boundary state of a dielectric
-     interface is eliminated (Sec. 3.3.1, the matching condition).
+     interface is eliminated (Sec. 3.3.1, the matching condition);
+  5  the first-order EB stencil divided by h instead of the ray length.
 Each of 1-3 must make the single-phase quadratic-exactness pin fail, so that
 pin does test the wall formula, the centroid interpolation and the volume
 weighting; 4 must fail the multifluid exactness pin, the coaxial closed form and
-the matching condition of the interface field.
+the matching condition of the interface field; 5 must fail the linear exactness
+of the first-order EB stencils.
 """
 import pytest
 
@@ -52,8 +54,15 @@ def test_plant_with_swapped_permittivities_breaks_multifluid_pins(plant):
         T.test_interface_field_satisfies_matching_condition(2)
 
 
+def test_plant_in_first_order_eb_stencil_breaks_linear_exactness(plant):
+    plant(5)
+    with pytest.raises(AssertionError):
+        T.test_linear_exactness_with_first_order_eb_stencils()
+
+
 def test_unplanted_build_passes_the_same_pins():
     T.test_quadratic_exactness_single_phase(32, "circle")
     T3.test_planar_electrode_truncation_zero(16)
     T.test_quadratic_exactness_multifluid(32)
     T.test_interface_field_satisfies_matching_condition(2)
+    T.test_linear_exactness_with_first_order_eb_stencils()
