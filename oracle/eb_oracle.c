@@ -21,6 +21,10 @@
  * The linear system is handed back as COO triplets; the caller solves it with
  * a library sparse direct solver.
  *
+ * Parity unpinned: the least-squares fallback of the EB normal-derivative
+ * stencil, which no test geometry needs (every other part is pinned by the
+ * tests' closed forms, exactness, conservation and symmetry checks).
+ *
  * Everything is written dimension-generic over D = 2 or 3, one cell or face
  * at a time, with no blocking or fusion.  Compile with -ffp-contract=off so
  * that a*b+c is never fused: the geometry is meant to be reproducible to the
