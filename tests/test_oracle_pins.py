@@ -335,32 +335,40 @@ def test_interface_field_satisfies_matching_condition(dim):
     assert np.abs(r).max() <= 1e-10 * np.abs(En[ib]).max()
 
 
-def test_linear_exactness_with_first_order_eb_stencils():
-    """A slot 1.3 cells wide, tilted, between two electrodes: most EB stencils
-    fall back to first order (one plane, linear transverse interpolation;
-    Sec. 3.3.1 allows it where the second plane is not in the fluid), which is
-    still exact for linear phi.  The truncation error and the EB normal field of
-    a linear phi vanish."""
-    n = 32
+@pytest.mark.parametrize("dim", [2, 3])
+def test_linear_exactness_with_first_order_eb_stencils(dim):
+    """A tilted slot between two electrodes, 1.3 cells wide in 2D and 1.6 in 3D:
+    most EB stencils fall back to first order (one plane, (bi)linear transverse
+    interpolation; Sec. 3.3.1 allows it where the second plane is not in the
+    fluid), which is still exact for linear phi.  The truncation error and the
+    EB normal field of a linear phi vanish."""
+    n = 32 if dim == 2 else 16
     h = 1.0 / n
-    c, s, y0, width = math.cos(0.2), math.sin(0.2), 0.45, 1.3 * h
-    prims = [(W.PRIM_HALFSPACE, [-s, c, 0, -s * 0.5 + c * y0]),
-             (W.PRIM_HALFSPACE, [s, -c, 0, s * 0.5 - c * (y0 + width)])]
-    d = W._desc(2, (n, n), (0, 0), h, prims, [(0, 0, 0), (0, 1, 0), (1, 0, 1)], 2, -1, (1.0, 1.0),
-                [1, 1, 0, 0, 0, 0], 0.0, [0] * 6)
+    if dim == 2:
+        nv, p0, width = np.array([-math.sin(0.2), math.cos(0.2), 0.0]), np.array([0.5, 0.45, 0.0]), 1.3 * h
+    else:
+        nv, p0, width = np.array([0.15, -0.2, 1.0]), np.array([0.5, 0.5, 0.45]), 1.6 * h
+        nv /= np.linalg.norm(nv)
+    # electrode: below the plane through p0 or above its copy `width` higher
+    prims = [(W.PRIM_HALFSPACE, [nv[0], nv[1], nv[2], nv @ p0]),
+             (W.PRIM_HALFSPACE, [-nv[0], -nv[1], -nv[2], -(nv @ p0 + width)])]
+    bc = [1, 1, 0, 0, 0, 0] if dim == 2 else [1, 1, 1, 1, 0, 0]
+    d = W._desc(dim, (n,) * dim, (0,) * dim, h, prims, [(0, 0, 0), (0, 1, 0), (1, 0, 1)], 2, -1, (1.0, 1.0), bc,
+                0.0, [0] * 6)
     g = oracle.Geometry(d)
     assert g.stencil_counts["order1"] > 40
-    a0, a1, a2 = 0.3, -1.7, 2.3
+    a = np.array([0.3, -1.7, 2.3, 0.9 if dim == 3 else 0.0])
 
     def phi(x, y, z):
-        return a0 + a1 * x + a2 * y
+        return a[0] + a[1] * x + a[2] * y + a[3] * z
     pd = _wall_values(g, phi)
-    data = g.data(s=np.zeros((2, g.ncell)), phiE=phi(g.ebx[:, 0], g.ebx[:, 1], 0), phidom=np.stack([pd, pd]))
+    data = g.data(s=np.zeros((2, g.ncell)), phiE=phi(g.ebx[:, 0], g.ebx[:, 1], g.ebx[:, 2]),
+                  phidom=np.stack([pd, pd]))
     A, b = g.assemble(data)
     X, Y, Z = g.cell_centres()
     xe = g.to_dofs(np.stack([phi(X, Y, Z)] * 2))
     assert np.abs(A @ xe - b).max() <= 1e-12 * np.abs(b).max()
     E, En = g.field(data, xe)
     eb = np.nonzero(g.ebkind == oracle.EB_ELECTRODE)[0]
-    dn = -(a1 * g.ebn[eb, 0] + a2 * g.ebn[eb, 1])
+    dn = -(g.ebn[eb] @ a[1:])
     assert np.abs(En[eb, 0] + dn).max() <= 1e-12 * np.abs(dn).max()

@@ -56,8 +56,9 @@ def test_plant_with_swapped_permittivities_breaks_multifluid_pins(plant):
 
 def test_plant_in_first_order_eb_stencil_breaks_linear_exactness(plant):
     plant(5)
-    with pytest.raises(AssertionError):
-        T.test_linear_exactness_with_first_order_eb_stencils()
+    for dim in (2, 3):
+        with pytest.raises(AssertionError):
+            T.test_linear_exactness_with_first_order_eb_stencils(dim)
 
 
 def test_unplanted_build_passes_the_same_pins():
@@ -65,4 +66,5 @@ def test_unplanted_build_passes_the_same_pins():
     T3.test_planar_electrode_truncation_zero(16)
     T.test_quadratic_exactness_multifluid(32)
     T.test_interface_field_satisfies_matching_condition(2)
-    T.test_linear_exactness_with_first_order_eb_stencils()
+    T.test_linear_exactness_with_first_order_eb_stencils(2)
+    T.test_linear_exactness_with_first_order_eb_stencils(3)
