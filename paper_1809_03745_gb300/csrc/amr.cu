@@ -296,6 +296,11 @@ extern "C" eb_status eb_amr_setup(const eb_geom_desc* desc, const int box_lo[3],
     return EB_ERR_INVALID;
   }
   *out = nullptr;
+  if (desc->n_prims < 0 || desc->n_prims > EB_MAX_PRIMS || desc->n_nodes < 0 || desc->n_nodes > EB_MAX_NODES ||
+      (desc->n_prims && !desc->prims) || (desc->n_nodes && !desc->nodes)) {
+    set_error("invalid primitive or CSG node list");
+    return EB_ERR_INVALID;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   eb_amr* A = new eb_amr();
   A->D = desc->dim;

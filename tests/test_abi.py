@@ -57,6 +57,13 @@ def test_status_strings_and_validation_without_gpu():
     st = lib.eb_poisson_solve_batched(hs, 2, ptrs, None, ptrs, None, None)
     assert st == E.EB_ERR_INVALID
     assert b"twice" in lib.eb_last_error()
+    # a composite set-up with a negative primitive count is refused before any copy
+    d2, keep2 = E.make_desc(W.rod_plane_2d(64))
+    d2.n_prims = -1
+    lo, hi = (ctypes.c_int * 3)(16, 16, 0), (ctypes.c_int * 3)(32, 32, 1)
+    st = lib.eb_amr_setup(ctypes.byref(d2), lo, hi, None, None, ctypes.byref(h))
+    assert st == E.EB_ERR_INVALID
+    assert b"primitive" in lib.eb_last_error()
 
 
 def test_binding_refuses_to_run_without_library(monkeypatch, tmp_path):
