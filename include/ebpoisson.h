@@ -187,7 +187,18 @@ typedef struct {
   long long kernel_launches; /* kernels this call launched (graph nodes counted per replay) */
   double kernel_ms; /* device time of the persistent solve kernel(s) of this call, from CUDA
                        events on the stream they ran on; 0 on the multi-launch paths */
+  int bottom;       /* how the coarsest level was solved: EB_BOTTOM_* */
+  int levels;       /* multigrid levels of the V-cycle */
 } eb_solve_info;
+
+/* Bottom solves of the V-cycle (Sec. 3.3.2 solves the coarsest level directly
+ * or by relaxation; which one applies follows from the coarsest level's size):
+ * an exact FP64 inverse for at most 256 unknowns, applied inside one CTA; an
+ * FP32 Gauss-Jordan inverse for at most 1024 unknowns, applied by the whole
+ * grid; BiCGStab over the whole grid when coarsening stopped above 4096 cells;
+ * else red-black relaxation sweeps inside one CTA (also the bottom of the
+ * per-phase launch paths). */
+enum { EB_BOTTOM_RELAX = 1, EB_BOTTOM_INV64 = 2, EB_BOTTOM_INV32 = 3, EB_BOTTOM_KRYLOV = 4 };
 
 typedef struct eb_poisson eb_poisson;
 
@@ -217,11 +228,15 @@ eb_status eb_poisson_residual(eb_poisson* P, const double* d_rhs, const double* 
  * residuals) lives in one file-scope device array of 2^21 + 2^19 + 8 doubles
  * (about 20.1 MB), held on every device that loads the library until the
  * process exits.  Limits: at most 2^20 finest-level cells and 2^19 sparse
- * rows, else EB_ERR_INVALID before any device work.  It calls no cudaMalloc
- * or cudaFree.  The first call on a device resolves the array's address
- * (cudaGetSymbolAddress) and should come before any stream capture.  Every
- * call shares the one array: calls whose work overlaps on the device race and
- * give undefined results.  Synchronises the stream before returning. */
+ * rows, else EB_ERR_INVALID before any device work; EB_ERR_INVALID too when
+ * the current device is not the one g was built on.  d_phi is read as given
+ * (no masked copy): its entries without an unknown must be finite.  It calls
+ * no cudaMalloc or cudaFree.  Every call looks up the array's address on the
+ * current device (cudaGetSymbolAddress, so a context created afresh after
+ * cudaDeviceReset is handled); the first call on a device may load the
+ * module and should come before any stream capture.  Every call shares the
+ * one array: calls whose work overlaps on the device race and give undefined
+ * results.  Synchronises the stream before returning. */
 eb_status eb_poisson_residual_noalloc(const eb_geom* g, const double* d_rhs, const double* d_sigma,
                                       const double* d_phi, double* d_r, void* stream);
 

@@ -21,9 +21,10 @@
  * The linear system is handed back as COO triplets; the caller solves it with
  * a library sparse direct solver.
  *
- * Parity unpinned: the least-squares fallback of the EB normal-derivative
- * stencil, which no test geometry needs (every other part is pinned by the
- * tests' closed forms, exactness, conservation and symmetry checks).
+ * Every part is pinned by the tests' closed forms, exactness, conservation
+ * and symmetry checks; the least-squares fallback of the EB normal-derivative
+ * stencil by linear exactness at the apex of acute fluid wedges, where
+ * neither ray stencil finds its cells.
  *
  * Everything is written dimension-generic over D = 2 or 3, one cell or face
  * at a time, with no blocking or fusion.  Compile with -ffp-contract=off so
@@ -41,7 +42,10 @@
  *   2  face-centre fluxes instead of their interpolation to the face centroid
  *   3  right-hand side s instead of kappa s in cut cells
  *   4  the two permittivities swapped in the boundary-state elimination
- *   5  the first-order EB stencil divided by h instead of the ray length */
+ *   5  the first-order EB stencil divided by h instead of the ray length
+ *   6  the least-squares EB stencil with the boundary weight's sign dropped
+ *   7  the least-squares fit taken about the cell centre instead of the EB centroid
+ *   8  no unknown on a fragment of zero volume (treated as covered) */
 #ifndef OR_PLANT
 #define OR_PLANT 0
 #endif
@@ -697,6 +701,8 @@ static int build_stencil(const or_geom* g, const long I[3], int p, const double 
           if (dof_of(g, J, p) < 0) continue;
           double dx[3] = {0.0, 0.0, 0.0}, dn = 0.0;
           for (int k = 0; k < D; ++k) { dx[k] = cell_x(g, k, J[k]) - xB[k]; dn = dn + dx[k] * nin[k]; }
+          if (OR_PLANT == 7)
+            for (int k = 0; k < D; ++k) dx[k] = cell_x(g, k, J[k]) - cell_x(g, k, I[k]);
           if (!(dn > 0.0)) continue;
           for (int k = 0; k < 3; ++k) dv[cnt][k] = dx[k];
           cells[cnt++] = (int)cell_id(g, J);
@@ -737,7 +743,7 @@ static int build_stencil(const or_geom* g, const long I[3], int p, const double 
       S->n++;
       sw = sw + wk;
     }
-    S->w0 = -sw;
+    S->w0 = (OR_PLANT == 6) ? sw : -sw;
     return OR_OK;
   }
   return OR_UNSUPPORTED;
@@ -850,7 +856,7 @@ or_geom* or_geom_build(const or_desc* d, int* status)
     cell_ijk(g, c, I);
     for (int p = 0; p < 2; ++p) {
       g->dof[p][c] = -1;
-      if (open_face(g, I, p)) g->dof[p][c] = g->ndof++;
+      if (open_face(g, I, p) && !(OR_PLANT == 8 && !(g->kappa[p][c] > 0.0))) g->dof[p][c] = g->ndof++;
     }
   }
   /* 6. EB stencils */

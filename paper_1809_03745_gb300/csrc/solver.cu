@@ -280,6 +280,7 @@ struct eb_poisson {
   unsigned long long* d_stamps = nullptr;  // [8] first-V-cycle timestamps of the last solve
   void* d_binv = nullptr;
   int bm = 0;
+  int bottom = EB_BOTTOM_RELAX;  // EB_BOTTOM_* of the persistent hierarchy
   int smem_bytes = 0;  // dynamic shared memory of the persistent kernel
   cudaEvent_t kev[2] = {nullptr, nullptr};  // bracket the persistent kernel
   double kernel_ms = 0.0;                   // its device time in the last call
@@ -586,6 +587,7 @@ static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
     if (st != EB_OK) return st;
   }
   P->bm = H.bm;
+  P->bottom = H.gkry ? EB_BOTTOM_KRYLOV : H.gbot ? EB_BOTTOM_INV32 : H.bm ? EB_BOTTOM_INV64 : EB_BOTTOM_RELAX;
   P->smem_bytes = H.smem_bytes;
   P->d_hier = dev_alloc(P->allocs, sizeof(Hier<T>), &P->bytes, &st);
   if (st == EB_OK) {
@@ -890,6 +892,8 @@ extern "C" eb_status eb_poisson_solve(eb_poisson* P, const double* d_rhs, const 
     inf.vcycles = cycles;
     inf.bnorm = b;
     inf.rel_res = b > 0.0 ? r / b : 0.0;
+    inf.bottom = P->bottom;
+    inf.levels = P->nlev;
     if (info) *info = inf;
     return st;
   }
@@ -941,6 +945,8 @@ extern "C" eb_status eb_poisson_solve(eb_poisson* P, const double* d_rhs, const 
   inf.outer_iters = outer;
   inf.vcycles = cycles;
   inf.rel_res = b > 0.0 ? r / b : 0.0;
+  inf.bottom = EB_BOTTOM_RELAX;  // the per-phase paths relax the coarsest level
+  inf.levels = P->nlev;
   if (info) *info = inf;
   return st;
 }
@@ -1152,6 +1158,8 @@ void batch_info(eb_poisson* Q, eb_solve_info* inf) {
   inf->vcycles = Q->h_out[2];
   inf->bnorm = b;
   inf->rel_res = b > 0.0 ? r / b : 0.0;
+  inf->bottom = Q->bottom;
+  inf->levels = Q->nlev;
 }
 
 extern "C" eb_status eb_poisson_solve_batched(eb_poisson* const* P, int n, const double* const* d_rhs,
@@ -1350,28 +1358,17 @@ static constexpr long long NA_MAX_CELLS = 1LL << 20;  // cells of the finest lev
 static constexpr long long NA_MAX_ROWS = 1LL << 19;   // sparse rows (two per irregular cell)
 static __device__ __align__(256) double g_na_scratch[NA_MAX_CELLS * 2 + NA_MAX_ROWS + 8];
 
-static std::mutex g_na_mutex;
-static double* g_na_addr[256] = {nullptr};  // device address of g_na_scratch, per device
-
-// Resolves the device address of the static array for the current device
-// (once per device; the first call on a device does this and should come
-// before any stream capture).
+// Resolves the device address of the static array on the current device.
+// It is looked up on every call (a cheap host call): an address cached per
+// device ordinal would go stale once the context is torn down and created
+// again (cudaDeviceReset), since the module is then loaded afresh.  The first
+// call on a device may load the module, so it should come before any stream
+// capture.
 static eb_status na_scratch(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "device query");
-  if (dev < 0 || dev >= 256) {
-    set_error("device ordinal out of range");
-    return EB_ERR_INVALID;
-  }
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_na_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "static scratch address");
-    g_na_addr[dev] = (double*)p;
-  }
-  *out = g_na_addr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "static scratch address");
+  *out = (double*)p;
   return EB_OK;
 }
 
@@ -1383,9 +1380,24 @@ extern "C" eb_status eb_poisson_residual_noalloc(const eb_geom* G, const double*
   }
   const DevLevel& F = G->L[0];
   long long n = F.g.ncell, nrow = 2 * F.nirr;
-  if (n > NA_MAX_CELLS || nrow > NA_MAX_ROWS) {
-    set_error("problem exceeds the static scratch of the allocation-free residual (" + std::to_string(NA_MAX_CELLS) +
-              " cells, " + std::to_string(NA_MAX_ROWS) + " sparse rows)");
+  if (n > NA_MAX_CELLS) {
+    set_error("problem exceeds the static scratch of the allocation-free residual: " + std::to_string(n) +
+              " cells, at most " + std::to_string(NA_MAX_CELLS));
+    return EB_ERR_INVALID;
+  }
+  if (nrow > NA_MAX_ROWS) {
+    set_error("problem exceeds the static scratch of the allocation-free residual: " + std::to_string(nrow) +
+              " sparse rows, at most " + std::to_string(NA_MAX_ROWS) + " (the sparse-row limit)");
+    return EB_ERR_INVALID;
+  }
+  // the geometry's arrays live on the device it was built on; the static
+  // array used is the current device's, so the two must be the same device
+  int dev = -1;
+  cudaError_t ed = cudaGetDevice(&dev);
+  if (ed != cudaSuccess) return cuda_fail(ed, "device query");
+  if (dev != G->device) {
+    set_error("the current device (" + std::to_string(dev) + ") is not the geometry's device (" +
+              std::to_string(G->device) + ")");
     return EB_ERR_INVALID;
   }
   double* base = nullptr;

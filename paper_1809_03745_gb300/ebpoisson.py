@@ -21,6 +21,9 @@ _lib = None
 EB_OK, EB_ERR_INVALID, EB_ERR_OOM, EB_ERR_NOT_CONVERGED, EB_ERR_CUDA, EB_ERR_TIMEOUT, EB_ERR_UNSUPPORTED, \
     EB_ERR_BUSY = range(8)
 EB_PREC_FP64, EB_PREC_MIXED = 0, 1
+EB_BOTTOM_RELAX, EB_BOTTOM_INV64, EB_BOTTOM_INV32, EB_BOTTOM_KRYLOV = 1, 2, 3, 4
+BOTTOM_NAMES = {EB_BOTTOM_RELAX: "relax", EB_BOTTOM_INV64: "inverse_fp64", EB_BOTTOM_INV32: "inverse_fp32",
+                EB_BOTTOM_KRYLOV: "bicgstab"}
 
 
 class EBError(RuntimeError):
@@ -64,7 +67,8 @@ class SolverOpts(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("vcycles", C.c_int), ("rel_res", C.c_double),
-                ("bnorm", C.c_double), ("kernel_launches", C.c_longlong), ("kernel_ms", C.c_double)]
+                ("bnorm", C.c_double), ("kernel_launches", C.c_longlong), ("kernel_ms", C.c_double),
+                ("bottom", C.c_int), ("levels", C.c_int)]
 
 
 class ServerOpts(C.Structure):
@@ -272,7 +276,8 @@ def eb_poisson_solve(handle, rhs, sigma, phi, stream=None) -> dict:
     if st not in (EB_OK, EB_ERR_NOT_CONVERGED):
         _check(st, "eb_poisson_solve")
     return dict(status=info.status, outer_iters=info.outer_iters, vcycles=info.vcycles, rel_res=info.rel_res,
-                bnorm=info.bnorm, kernel_launches=info.kernel_launches, kernel_ms=info.kernel_ms)
+                bnorm=info.bnorm, kernel_launches=info.kernel_launches, kernel_ms=info.kernel_ms,
+                bottom=BOTTOM_NAMES.get(info.bottom, "none"), levels=info.levels)
 
 
 def eb_poisson_profile(handle, kernel: int, reps: int, stream=None):
@@ -284,7 +289,8 @@ def eb_poisson_profile(handle, kernel: int, reps: int, stream=None):
 
 def _info_dict(info):
     return dict(status=info.status, outer_iters=info.outer_iters, vcycles=info.vcycles, rel_res=info.rel_res,
-                bnorm=info.bnorm, kernel_launches=info.kernel_launches, kernel_ms=info.kernel_ms)
+                bnorm=info.bnorm, kernel_launches=info.kernel_launches, kernel_ms=info.kernel_ms,
+                bottom=BOTTOM_NAMES.get(info.bottom, "none"), levels=info.levels)
 
 
 def eb_poisson_solve_batched(handles, rhs, sigma, phi, stream=None) -> list:

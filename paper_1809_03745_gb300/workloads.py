@@ -158,6 +158,29 @@ def coaxial_exact(r, *, R0=0.3, R1=0.6, R2=0.9, eps_g=1.0, eps_d=4.0, phi0=1.0, 
     return phi_g, phi_d
 
 
+def fluid_wedge(dim=2, n=32, *, half=0.6, angle=1.3, apex=(0.3123, 0.4571, 0.5213), tilt=0.0, V=1.0):
+    """An acute fluid wedge cut out of a planar electrode: the electrode is the
+    union of two half-spaces whose boundary planes meet at `apex`, making
+    angles angle +- half with the x axis (in 3D both planes are tilted by
+    +-tilt out of the z axis).  Near the apex neither ray stencil of the EB
+    normal derivative finds its cells in the fluid, so the least-squares
+    fallback (Sec. 3.3.1) is used there.  Electrode at V, walls Dirichlet 0."""
+    h = 1.0 / n
+    a1, a2 = angle + half, angle - half
+    n1 = np.array([math.sin(a1), -math.cos(a1), 0.0])
+    n2 = np.array([-math.sin(a2), math.cos(a2), 0.0])
+    if dim == 3:
+        n1[2], n2[2] = tilt, -tilt
+        n1 /= np.linalg.norm(n1)
+        n2 /= np.linalg.norm(n2)
+    p = np.array(list(apex[:dim]) + [0.5] * (3 - dim))
+    prims = [(PRIM_HALFSPACE, [n1[0], n1[1], n1[2], float(n1 @ p)]),
+             (PRIM_HALFSPACE, [n2[0], n2[1], n2[2], float(n2 @ p)])]
+    nodes = [(CSG_PRIM, 0, 0), (CSG_PRIM, 1, 0), (CSG_UNION, 0, 1)]
+    bc = [DIRICHLET] * 4 + ([NEUMANN] * 2 if dim == 2 else [DIRICHLET] * 2)
+    return _desc(dim, (n,) * dim, (0.0,) * dim, h, prims, nodes, 2, -1, (1.0, 1.0), bc, V, [0.0] * 6)
+
+
 # --------------------------------------------------------------- 3D workloads
 
 def pin_plane_3d(n=256, *, tip_z=0.5, radius=0.02, V=1.0, disk=True, eps_d=3.0, disk_r=0.3, disk_t=0.05):

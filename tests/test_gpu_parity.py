@@ -28,6 +28,15 @@ def _cases():
     out.append(("coax_136_sigma", d, np.zeros((2, W.ncells(d))), np.full(W.ncells(d), 0.7)))
     d, S, sig = W.c2_inputs(256)
     out.append(("c2_256", d, S, sig))
+    # least-squares EB stencils at the apex of an acute fluid wedge
+    d = W.fluid_wedge(2, 64)
+    out.append(("wedge_64_ls", d, np.full((2, W.ncells(d)), 10.0), np.zeros(W.ncells(d))))
+    # an electrode surface on a plane of cell faces: zero-volume fragments with unknowns
+    d = W._desc(2, (64, 64), (0, 0), 1.0 / 64, [(W.PRIM_HALFSPACE, [0.0, 1.0, 0.0, 0.25])], [(0, 0, 0)], 0, -1,
+                (1.0, 1.0), [1, 1, 1, 1, 0, 0], 1.0, [0.0, 0.0, 0.0, 0.5, 0.0, 0.0])
+    x, y, _ = W.cell_centres(d)
+    out.append(("faces_64_sliver", d, np.stack([30.0 * np.exp(-((x - 0.4) ** 2 + (y - 0.6) ** 2) / 0.02),
+                                                np.zeros_like(x)]), np.zeros(W.ncells(d))))
     return out
 
 
@@ -68,6 +77,10 @@ def test_geometry_parity(case, oracles):
     assert g.info["stencil_order"] == og.stencil_counts
     assert g.info["n_dof"] == og.ndof
     assert g.info["n_eb"] == og.n_eb
+    if name.endswith("_ls"):
+        assert og.stencil_counts["ls"] > 0
+    if name.endswith("_sliver"):
+        assert ((og.dof[0] >= 0) & (og.kappa[0] < 1e-12)).sum() == 64
 
 
 @pytest.mark.parametrize("case", CASES, ids=IDS)

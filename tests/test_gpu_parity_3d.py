@@ -31,8 +31,13 @@ def _pin(n, **kw):
     return d, S, np.zeros(W.ncells(d))
 
 
+def _wedge():
+    d = W.fluid_wedge(3, 16, half=0.45, angle=1.2, tilt=0.2)
+    return d, np.full((2, W.ncells(d)), 10.0), np.zeros(W.ncells(d))
+
+
 CASES = [("pin_disk_32", *_pin(32, radius=0.12)), ("concentric_32_sigma", *_concentric(32)),
-         ("pin_disk_40", *_pin(40, radius=0.1))]
+         ("pin_disk_40", *_pin(40, radius=0.1)), ("wedge_16_ls", *_wedge())]
 IDS = [c[0] for c in CASES]
 
 
@@ -57,6 +62,13 @@ def test_geometry_parity_3d(case, oracles):
     assert np.abs(ex["eb_normal"].cpu().numpy() - og.ebn[eb]).max() < 1e-12
     assert np.abs(ex["eb_centroid"].cpu().numpy() - og.ebx[eb]).max() < 1e-13
     assert g.info["stencil_order"] == og.stencil_counts
+    oo = og.stencil_order()
+    so = ex["stencil_order"].cpu().numpy()
+    for p in range(2):
+        m = og.dof[p, eb] >= 0
+        assert np.array_equal(so[m, p], oo[p, eb][m])
+    if name.endswith("_ls"):
+        assert og.stencil_counts["ls"] > 30
 
 
 @pytest.mark.parametrize("case", CASES, ids=IDS)
@@ -84,7 +96,7 @@ def test_solve_parity_3d(case, precision, oracles):
     assert np.abs(phi.cpu().numpy() - ophi).max() <= 1e-9 * np.abs(ophi).max(), info
 
 
-@pytest.mark.parametrize("case", CASES[:2], ids=IDS[:2])
+@pytest.mark.parametrize("case", CASES[:2] + CASES[3:], ids=IDS[:2] + IDS[3:])
 def test_field_parity_3d(case, oracles):
     name, d, S, sig = case
     og, ophi, A, b, data = oracles[name]

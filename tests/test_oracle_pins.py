@@ -372,3 +372,85 @@ def test_linear_exactness_with_first_order_eb_stencils(dim):
     eb = np.nonzero(g.ebkind == oracle.EB_ELECTRODE)[0]
     dn = -(g.ebn[eb] @ a[1:])
     assert np.abs(En[eb, 0] + dn).max() <= 1e-12 * np.abs(dn).max()
+
+
+def _wedge(dim):
+    if dim == 2:
+        return W.fluid_wedge(2, 32)
+    return W.fluid_wedge(3, 16, half=0.45, angle=1.2, tilt=0.2)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_linear_exactness_with_least_squares_eb_stencils(dim):
+    """At the apex of an acute fluid wedge neither ray stencil of Sec. 3.3.1
+    finds its interpolation cells in the fluid, and the EB normal derivative
+    falls back to the least-squares fit of phi_B + g.(x - x_B) over the fluid
+    neighbours on the fluid side.  That fit reproduces any linear phi, so the
+    truncation error and the EB normal field of a linear phi vanish there too.
+    The same geometry also carries first-order and ray stencils."""
+    g = oracle.Geometry(_wedge(dim))
+    c = g.stencil_counts
+    assert c["ls"] >= (2 if dim == 2 else 30) and c["order1"] > 0 and c["order2"] > 0, c
+    order = g.stencil_order()
+    ls_cells = np.nonzero(order[0] == 3)[0]
+    assert len(ls_cells) == c["ls"]
+    a = np.array([0.3, -1.7, 2.3, 0.9 if dim == 3 else 0.0])
+
+    def phi(x, y, z):
+        return a[0] + a[1] * x + a[2] * y + a[3] * z
+    pd = _wall_values(g, phi)
+    data = g.data(s=np.zeros((2, g.ncell)), phiE=phi(g.ebx[:, 0], g.ebx[:, 1], g.ebx[:, 2]),
+                  phidom=np.stack([pd, pd]))
+    A, b = g.assemble(data)
+    X, Y, Z = g.cell_centres()
+    xe = g.to_dofs(np.stack([phi(X, Y, Z)] * 2))
+    assert np.abs(A @ xe - b).max() <= 1e-12 * np.abs(b).max()
+    # the least-squares cells' own rows, checked on their own as well
+    rows = g.dof[0, ls_cells]
+    assert np.abs((A @ xe - b)[rows]).max() <= 1e-12 * np.abs(b).max()
+    E, En = g.field(data, xe)
+    dn = -(g.ebn[ls_cells] @ a[1:])
+    assert np.abs(En[ls_cells, 0] + dn).max() <= 1e-12 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("offset", [0.0, -1e-10, 1e-10])
+def test_quadratic_exactness_with_eb_on_grid_faces(dim, offset):
+    """An electrode whose surface lies on a plane of cell faces, exactly or
+    within the crossing snap distance (1e-8 h).  Just below that plane each
+    cell keeps a fluid fragment of zero volume whose top face is open: it
+    carries an unknown whose row equates the face flux with the EB flux
+    (reading: a fragment has an unknown when it has an open face).  Above
+    the plane the cells are full, and where the surface lies just above the
+    plane (offset +1e-10) the EB sits on their bottom faces instead.  In both
+    forms the face flux (phi_above - phi_below)/h is the derivative at the
+    face for a quadratic, so the discrete solution equals a quadratic phi at
+    every unknown, the zero-volume ones included."""
+    n = 32 if dim == 2 else 16
+    h = 1.0 / n
+    y0 = 0.5 + offset
+    prims = [(W.PRIM_HALFSPACE, [0.0, 1.0, 0.0, y0])]
+    bc = [1, 1, 1, 1, 0, 0] if dim == 2 else [1] * 6
+    d = W._desc(dim, (n,) * dim, (0,) * dim, h, prims, [(0, 0, 0)], 0, -1, (1.0, 1.0), bc, 0.0, [0] * 6)
+    g = oracle.Geometry(d)
+    sliver = np.nonzero((g.dof[0] >= 0) & (g.kappa[0] < 1e-12))[0]
+    nplane = n ** (dim - 1)
+    assert len(sliver) == (0 if offset > 0 else nplane)
+    assert g.n_eb == nplane
+    co = np.array([0.3, -0.7, 1.1, 0.8, -0.6, 0.5, 0.4 if dim == 3 else 0.0, 0.2 if dim == 3 else 0.0])
+
+    def phi(x, y, z):
+        return (co[0] + co[1] * x + co[2] * y + co[3] * x * x + co[4] * x * y + co[5] * y * y + co[6] * z * z
+                + co[7] * y * z)
+    lap = 2 * co[3] + 2 * co[5] + 2 * co[6]
+    s = np.full((2, g.ncell), -lap)
+    pd = _wall_values(g, phi)
+    data = g.data(s=s, phiE=phi(g.ebx[:, 0], g.ebx[:, 1], g.ebx[:, 2]), phidom=np.stack([pd, pd]))
+    A, bb = g.assemble(data)
+    x = g.to_cells(oracle.solve_system(A, bb))[0]
+    X, Y, Z = g.cell_centres()
+    ex = phi(X, Y, Z)
+    m = g.dof[0] >= 0
+    assert np.abs(x[m] - ex[m]).max() <= 1e-12 * np.abs(ex).max()
+    if len(sliver):
+        assert np.abs(x[sliver] - ex[sliver]).max() <= 1e-12 * np.abs(ex).max()

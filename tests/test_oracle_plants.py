@@ -10,12 +10,17 @@ The oracle's C source carries three switches that a separate build turns on
      the source over the cut cell's volume);
   4  the two permittivities swapped where the boundary state of a dielectric
      interface is eliminated (Sec. 3.3.1, the matching condition);
-  5  the first-order EB stencil divided by h instead of the ray length.
+  5  the first-order EB stencil divided by h instead of the ray length;
+  6  the least-squares EB stencil with the boundary weight's sign dropped;
+  7  the least-squares fit taken about the cell centre instead of the EB
+     centroid;
+  8  no unknown on a fluid fragment of zero volume (treated as covered).
 Each of 1-3 must make the single-phase quadratic-exactness pin fail, so that
 pin does test the wall formula, the centroid interpolation and the volume
 weighting; 4 must fail the multifluid exactness pin, the coaxial closed form and
 the matching condition of the interface field; 5 must fail the linear exactness
-of the first-order EB stencils.
+of the first-order EB stencils, 6 and 7 that of the least-squares stencils; 8
+must fail the quadratic exactness with an electrode surface on grid faces.
 """
 import pytest
 
@@ -61,6 +66,21 @@ def test_plant_in_first_order_eb_stencil_breaks_linear_exactness(plant):
             T.test_linear_exactness_with_first_order_eb_stencils(dim)
 
 
+@pytest.mark.parametrize("k", [6, 7])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_plant_in_least_squares_stencil_breaks_linear_exactness(plant, k, dim):
+    plant(k)
+    with pytest.raises(AssertionError):
+        T.test_linear_exactness_with_least_squares_eb_stencils(dim)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_plant_without_zero_volume_unknowns_breaks_face_aligned_exactness(plant, dim):
+    plant(8)
+    with pytest.raises(AssertionError):
+        T.test_quadratic_exactness_with_eb_on_grid_faces(dim, 0.0)
+
+
 def test_unplanted_build_passes_the_same_pins():
     T.test_quadratic_exactness_single_phase(32, "circle")
     T3.test_planar_electrode_truncation_zero(16)
@@ -68,3 +88,6 @@ def test_unplanted_build_passes_the_same_pins():
     T.test_interface_field_satisfies_matching_condition(2)
     T.test_linear_exactness_with_first_order_eb_stencils(2)
     T.test_linear_exactness_with_first_order_eb_stencils(3)
+    for dim in (2, 3):
+        T.test_linear_exactness_with_least_squares_eb_stencils(dim)
+        T.test_quadratic_exactness_with_eb_on_grid_faces(dim, 0.0)
