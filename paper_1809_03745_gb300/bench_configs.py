@@ -13,11 +13,17 @@ Times are wall-clock around the solve calls after warm-up (device work
 synchronised on both sides); inputs are resident on the device; all solves
 run to max|r| <= 1e-10 max|b|.
 
+With --trace c1|c2|c3 it instead prints where one V-cycle's time goes: the
+persistent kernel's phase stamps of the first V-cycle (eb_poisson_trace),
+summed per level and phase kind, and the grid-barrier cost.
+
 Usage: python -m paper_1809_03745_gb300.bench_configs [--only C1 C2 C3 C4]
+       python -m paper_1809_03745_gb300.bench_configs --trace c2 [--n N] [--precision mixed|fp64]
 """
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import time
 
@@ -109,11 +115,48 @@ def c4(count=64):
            "ms": dt2 * 1e3, "cells_per_s": cells / dt2, "statuses": sorted(set(i["status"] for i in inf2))}
 
 
+TRACE_KIND = {1: "red", 2: "rows", 3: "black", 4: "write", 5: "resrows", 6: "restrict", 7: "prolong",
+              8: "coarseend", 9: "bottom", 12: "update", 13: "sweep"}
+
+
+def trace(workload, n=None, precision="mixed"):
+    """Phase trace of the first V-cycle of one solve (after two warm-up solves)."""
+    gen = {"c1": (W.c1_inputs, 128), "c2": (W.c2_inputs, 1024), "c3": (W.c3_inputs, 128)}[workload]
+    d, S, sig = gen[0](n or gen[1])
+    P = E.Poisson(E.Geometry(d), precision=precision, tol=1e-10, max_cycles=400)
+    rhs, sg = torch.from_numpy(S).cuda(), torch.from_numpy(sig).cuda()
+    for _ in range(2):
+        P.solve(rhs, sg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, info = P.solve(rhs, sg)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    print(f"{workload} n={n or gen[1]} {precision}: {info['vcycles']} V-cycles, {info['outer_iters']} outer, "
+          f"rel_res {info['rel_res']:.2e}, wall {wall * 1e3:.2f} ms, kernel {info['kernel_ms']:.2f} ms")
+    tr = P.trace()
+    agg = collections.OrderedDict()
+    for lev, k, ms in tr:
+        key = (lev, TRACE_KIND.get(k, str(k)))
+        cnt, t = agg.get(key, (0, 0.0))
+        agg[key] = (cnt + 1, t + ms)
+    print(f"  first V-cycle: {len(tr)} phases, {sum(ms for _, _, ms in tr) * 1e3:.1f} us")
+    for (lev, k), (cnt, t) in agg.items():
+        print(f"    L{lev:2d} {k:10s} n={cnt:3d} {t * 1e3:8.1f} us  avg {t * 1e3 / cnt:6.2f}")
+    print(f"  grid barrier: {P.profile(2, 1000)[0] * 1e3:.2f} us")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", nargs="+", default=["C1", "C2", "C3", "C4"])
+    ap.add_argument("--trace", choices=["c1", "c2", "c3"], default=None)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
     E.load()
+    if args.trace:
+        trace(args.trace, args.n, args.precision)
+        return
     for name, fn in (("C1", c1), ("C2", c2), ("C3", c3), ("C4", c4)):
         if name in args.only:
             for line in fn():

@@ -39,6 +39,10 @@ def _wedge():
 CASES = [("pin_disk_32", *_pin(32, radius=0.12)), ("concentric_32_sigma", *_concentric(32)),
          ("pin_disk_40", *_pin(40, radius=0.1)), ("wedge_16_ls", *_wedge())]
 IDS = [c[0] for c in CASES]
+# 32^3 grids stop at 16^3 (4096 cells, relaxation); 40^3 stops at 20^3 = 8000
+# cells, above the 4096 that one CTA relaxes, so its bottom is BiCGStab over
+# the whole grid; the 16^3 wedge does not coarsen at all
+BOTTOM = {"pin_disk_32": "relax", "concentric_32_sigma": "relax", "pin_disk_40": "bicgstab", "wedge_16_ls": "relax"}
 
 
 @pytest.fixture(scope="module")
@@ -93,7 +97,13 @@ def test_solve_parity_3d(case, precision, oracles):
     P = E.Poisson(g, precision=precision, tol=1e-12, max_cycles=300)
     phi, info = P.solve(torch.from_numpy(S), torch.from_numpy(sig))
     assert info["status"] == 0, info
+    assert info["bottom"] == BOTTOM[name], info
     assert np.abs(phi.cpu().numpy() - ophi).max() <= 1e-9 * np.abs(ophi).max(), info
+
+
+def test_every_bottom_variant_has_an_oracle_parity_case():
+    import test_gpu_parity as T2
+    assert set(BOTTOM.values()) | set(T2.BOTTOM.values()) == {"inverse_fp64", "inverse_fp32", "bicgstab", "relax"}
 
 
 @pytest.mark.parametrize("case", CASES[:2] + CASES[3:], ids=IDS[:2] + IDS[3:])
