@@ -189,6 +189,9 @@ typedef struct {
                        events on the stream they ran on; 0 on the multi-launch paths */
   int bottom;       /* how the coarsest level was solved: EB_BOTTOM_* */
   int levels;       /* multigrid levels of the V-cycle */
+  int sweep_levels; /* levels relaxed by tile-streamed sweeps (FP32 3D levels from 64^3 cells with an x
+                       extent a multiple of 16: both colours in one pass over the level, tiles staged
+                       in shared memory by TMA); the others use one pass per colour */
 } eb_solve_info;
 
 /* Bottom solves of the V-cycle (Sec. 3.3.2 solves the coarsest level directly

@@ -16,6 +16,27 @@ constexpr int MAXLEV = 16;
 constexpr int PT = 512;                          // threads per CTA of the persistent kernel
 constexpr long long BAR_WAIT_CYCLES = 4000000000LL;  // ~2 s of SM clock: a barrier wait gives up after this
 
+// Tile-streamed sweep of large 3D levels (sweep3d.cuh): tiles of SW_TX x ty
+// cells, boxes with a halo of SW_HX cells in x (16 bytes of 4-byte data, the
+// TMA alignment of the x coordinate), SW_HY in y, flags boxes SW_FBX bytes
+// wide from SW_FHX cells left of the tile (16-byte alignment of bytes).
+constexpr int SW_TX = 32, SW_HX = 4, SW_BX = SW_TX + 2 * SW_HX, SW_HY = 2, SW_FHX = 16, SW_FBX = 64;
+constexpr int SW_NS_MAX = 16;     // ring slots at most
+constexpr int SW_MASK_MAX = 256;  // words of the per-item dielectric mask (8192 tiles x chunks)
+constexpr int SW_HEAD = ((8 * SW_NS_MAX + 4 * SW_MASK_MAX + 4 * SW_NS_MAX + 127) / 128) * 128;
+
+template <class T>
+struct SweepLev {
+  int on;       // 1: the level relaxes by tile-streamed sweeps, x -> alt
+  int ty;       // tile rows (16 or 32)
+  int zc;       // planes per z-chunk
+  int ntx, nty, nzc, nitems;  // tiles per axis, z-chunks, work items (tile x chunk)
+  int par;      // 0: x holds the iterate; 1: alt does (this CTA's copy, flipped per sweep)
+  T* alt[2];    // the second buffer per phase
+  const void* maps;      // 7 tensor maps (128 bytes each): x[buf][phase] (buf 0 = x, 1 = alt), b[phase], flags
+  const unsigned* has1;  // bit per item: dielectric unknowns in the item's boxes
+};
+
 template <class T>
 struct Hier {
   int nlev;  // multigrid levels
@@ -36,7 +57,9 @@ struct Hier {
   // offsets of row_ptr, col, val, diag, irr_cell, irr_of_cell, and the entry count
   int srows[MAXLEV], off_rp[MAXLEV], off_col[MAXLEV], off_val[MAXLEV], off_dg[MAXLEV], off_ic[MAXLEV],
       off_io[MAXLEV], rnnz[MAXLEV];
+  int sw_ns;  // ring slots of the tile-streamed sweeps
   Op<T> op[MAXLEV];
+  SweepLev<T> sw[MAXLEV];
 };
 
 struct Barrier {
@@ -445,6 +468,10 @@ __device__ __forceinline__ void ph_write(const Op<T>& o, long long rb, long long
   }
 }
 
+}  // namespace ebp
+#include "sweep3d.cuh"
+namespace ebp {
+
 // Residual + restriction by blocks: one coarse cell per work item; the
 // children and their face neighbours (4 x 4 without corners in 2D, the 2^3
 // block and its 24 face neighbours in 3D) are loaded in one round for each
@@ -773,6 +800,29 @@ __device__ bool ph_smooth(const Op<T>& o, int nu, const Ctx& c, int l) {
   return true;
 }
 
+// nu sweeps of grid level l: tile-streamed when the level has them (and the
+// group has CTAs besides CTA 0), else the colour passes above.  A streamed
+// sweep first gives the cut cells their Gauss-Seidel values from the current
+// iterate (all at once) and writes them into x, then relaxes the regular
+// cells of both colours in one pass.
+template <class T>
+__device__ bool ph_smooth_grid(const Hier<T>& H, int l, int nu, const Ctx& c) {
+  const Op<T>& o = H.op[l];
+  if (!H.sw[l].on || c.local || c.gsize < 2) return ph_smooth(o, nu, c, l);
+  extern __shared__ __align__(128) unsigned char sw_dyn[];
+  for (int s = 0; s < nu; ++s) {
+    if (o.nirr) {
+      ph_rows(o, 0, 2 * o.nirr, 0, c);
+      if (!c.sync((l << 4) | 2)) return false;
+      ph_write(o, 0, 2 * o.nirr, c);
+      if (!c.sync((l << 4) | 4)) return false;
+    }
+    if (!ph_sweep3d(H, l, c, sw_dyn)) return false;
+    if (!c.sync((l << 4) | 13)) return false;
+  }
+  return true;
+}
+
 template <class T>
 __device__ bool ph_bottom(const Hier<T>& H, const Op<T>* ops, const Ctx& c) {
   const Op<T>& o = ops[H.nlev - 1];
@@ -1026,7 +1076,7 @@ template <class T>
 __device__ bool vcycle_dev(const Hier<T>& H, const Op<T>* lop, const Ctx& G) {
   for (int l = 0; l < H.lc; ++l) {
     const Op<T>& o = H.op[l];
-    if (!ph_smooth(o, H.nu1, G, l)) return false;
+    if (!ph_smooth_grid(H, l, H.nu1, G)) return false;
     if (o.nirr) {
       ph_rows(o, 0, 2 * o.nirr, 1, G);
       if (!G.sync((l << 4) | 5)) return false;
@@ -1049,7 +1099,7 @@ __device__ bool vcycle_dev(const Hier<T>& H, const Op<T>* lop, const Ctx& G) {
   for (int l = H.lc - 1; l >= 0; --l) {
     ph_prolong(H.op[l], H.op[l + 1], G);
     if (!G.sync((l << 4) | 7)) return false;
-    if (!ph_smooth(H.op[l], H.nu2, G, l)) return false;
+    if (!ph_smooth_grid(H, l, H.nu2, G)) return false;
   }
   return true;
 }
@@ -1114,7 +1164,7 @@ __device__ __forceinline__ void solve_group(const Hier<T>* __restrict__ Hg, cons
   __shared__ Op<T> lop[MAXLEV];  // level views used inside CTA 0 (shared-memory data for levels lc..)
   __shared__ unsigned epoch;
   __shared__ unsigned tn;
-  extern __shared__ __align__(16) unsigned char dyn[];
+  extern __shared__ __align__(128) unsigned char dyn[];
   {
     const int* src = (const int*)Hg;
     int* dst = (int*)&H;
@@ -1249,6 +1299,27 @@ __global__ void __launch_bounds__(PT, 1) k_solve_batch(const BatchItem<T>* __res
                                                        const int* __restrict__ cta_item) {
   const BatchItem<T>& it = items[cta_item[blockIdx.x]];
   solve_group(it.H, it.F, it.ctl, it.B, (int)blockIdx.x - it.start, it.size);
+}
+
+// Setup of the tile-streamed sweep: bit `it` of has1 is set when the boxes
+// item `it` loads (its tile with the halo, planes z0 - 2 .. z1 + 1) hold a
+// dielectric unknown; one CTA per item.
+__global__ void k_sweep_has1(const uint8_t* __restrict__ flags, int n0, int n1, int n2, int ntx, int nty, int ty,
+                             int zc, int nitems, unsigned* has1) {
+  const int it = blockIdx.x;
+  if (it >= nitems) return;
+  const int tx = it % ntx, r = it / ntx;
+  const int x0 = tx * SW_TX, y0 = (r % nty) * ty, z0 = (r / nty) * zc, z1 = min(z0 + zc, n2);
+  const int xa = max(x0 - SW_HX, 0), xb = min(x0 + SW_TX + SW_HX, n0);
+  const int ya = max(y0 - SW_HY, 0), yb = min(y0 + ty + SW_HY, n1);
+  const int za = max(z0 - 2, 0), zb = min(z1 + 2, n2);
+  const long long nx = xb - xa, ny = yb - ya, nz = zb - za;
+  int found = 0;
+  for (long long e = threadIdx.x; e < nx * ny * nz && !found; e += blockDim.x) {
+    const long long x = xa + e % nx, y = ya + (e / nx) % ny, z = za + e / (nx * ny);
+    if (flags[(z * n1 + y) * n0 + x] & 2) found = 1;
+  }
+  if (__syncthreads_or(found) && threadIdx.x == 0) atomicOr(&has1[it >> 5], 1u << (it & 31));
 }
 
 // ------------------------------------------------------------ bottom inverse
@@ -1505,6 +1576,23 @@ __global__ void __launch_bounds__(PT) k_dense_phase(Op<T> o, int colour) {
   c.gsize = (int)gridDim.x;
   c.gcta = (int)blockIdx.x;
   ph_dense(o, colour, c);
+}
+
+// one tile-streamed sweep of level l on its own, in the persistent kernel's
+// grid shape (CTA 0 sits out as in the solve); x -> alt as in the solve
+template <class T>
+__global__ void __launch_bounds__(PT, 1) k_sweep_phase(const Hier<T>* __restrict__ Hg, int l, int* err) {
+  __shared__ Hier<T> H;
+  extern __shared__ __align__(128) unsigned char dyn[];
+  const int* src = (const int*)Hg;
+  int* dst = (int*)&H;
+  for (int i = threadIdx.x; i < (int)(sizeof(Hier<T>) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  Ctx c{};
+  c.gsize = (int)gridDim.x;
+  c.gcta = (int)blockIdx.x;
+  c.B.err = err;
+  ph_sweep3d(H, l, c, dyn);
 }
 
 template <class T>

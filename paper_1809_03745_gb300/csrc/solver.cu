@@ -1,6 +1,8 @@
 // solver.cu -- multigrid driver and the C ABI of the EB Poisson library
 // (arXiv:1809.03745, Sec. 3.3.2).
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -9,6 +11,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "eb_internal.h"
@@ -281,6 +284,10 @@ struct eb_poisson {
   void* d_binv = nullptr;
   int bm = 0;
   int bottom = EB_BOTTOM_RELAX;  // EB_BOTTOM_* of the persistent hierarchy
+  int sweep_levels = 0;          // grid levels relaxed by tile-streamed sweeps
+  int sweep_bytes = 0;           // their shared memory per CTA
+  int sweep_ns = 0;              // ring slots
+  int sweep_first = -1;          // the finest of them
   int smem_bytes = 0;  // dynamic shared memory of the persistent kernel
   cudaEvent_t kev[2] = {nullptr, nullptr};  // bracket the persistent kernel
   double kernel_ms = 0.0;                   // its device time in the last call
@@ -428,6 +435,149 @@ static void iteration(eb_poisson* P, cudaStream_t s) {
   }
 }
 
+
+// ------------------------------------------------- tile-streamed sweeps (sweep3d.cuh)
+
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// a 3D tensor map over one level array (x fastest), boxes of bx x by x 1
+static bool tmap3(CUtensorMap* m, CUtensorMapDataType type, int esize, const void* base, const int n[3], int bx,
+                  int by) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+  if (!enc) return false;
+  cuuint64_t dim[3] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2]};
+  cuuint64_t str[2] = {(cuuint64_t)n[0] * esize, (cuuint64_t)n[0] * n[1] * esize};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, type, 3, const_cast<void*>(base), dim, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static constexpr long long SW_MIN_CELLS = 1LL << 18;  // levels from 64^3 up stream their sweeps
+
+// Tile rows and z-chunk of a level for `workers` CTAs: the least of
+// (rounds of items per CTA) x (planes per item) x (bytes of a plane's boxes
+// + a fixed cost per step), over ty in {16, 32} and chunks of 4..n2 planes.
+static void sweep_shape(const int n[3], int workers, int* ty_out, int* zc_out) {
+  double best = 1e300;
+  *ty_out = 32;
+  *zc_out = n[2];
+  for (int ty : {32, 16}) {
+    const long long ntx = (n[0] + SW_TX - 1) / SW_TX, nty = (n[1] + ty - 1) / ty;
+    for (int zc = 4; zc <= n[2]; zc += 4) {
+      const long long nzc = (n[2] + zc - 1) / zc, items = ntx * nty * nzc;
+      if (items > 32LL * SW_MASK_MAX) continue;
+      const long long rounds = (items + workers - 1) / workers;
+      const double plane = (double)SW_BX * (ty + 2 * SW_HY) * 9.6 + 2048.0;
+      const double cost = (double)rounds * (zc + 4) * plane;
+      if (cost < best * (1.0 - 1e-9)) {
+        best = cost;
+        *ty_out = ty;
+        *zc_out = zc;
+      }
+    }
+  }
+}
+
+// Marks the FP32 3D grid levels of at least SW_MIN_CELLS cells (x extent a
+// multiple of 16) for tile-streamed sweeps: a second x buffer per phase,
+// tensor maps of x, the second buffer, b and the flags, the per-item
+// dielectric mask.  Levels stay on the colour passes when any of it fails or
+// the shared memory cannot hold six ring slots.
+template <class T>
+static eb_status setup_sweeps(eb_poisson* P, std::vector<Op<T>>& ops, Hier<T>& H, int smem_cap) {
+  if (!std::is_same<T, float>::value) return EB_OK;
+  if (const char* env = std::getenv("EBP_SWEEP"))
+    if (std::atoi(env) == 0) return EB_OK;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->G->device);
+  const int workers = std::max(1, nsm - 1);
+  long long min_cells = SW_MIN_CELLS;  // EBP_SWEEP_MIN_CELLS lowers it (tests run small grids through the path)
+  if (const char* env = std::getenv("EBP_SWEEP_MIN_CELLS")) min_cells = std::max(1LL, std::atoll(env));
+  int slot_max = 0;
+  std::vector<int> cand;
+  for (int l = 0; l < H.lc; ++l) {
+    const Op<T>& o = ops[l];
+    if (o.D != 3 || o.ncell < min_cells || (o.n[0] % 16) != 0) continue;
+    int ty = 32, zc = 4;
+    sweep_shape(o.n, workers, &ty, &zc);
+    H.sw[l].ty = ty;
+    H.sw[l].zc = zc;
+    SweepSlot<T> L(ty, o.x[1] != nullptr);
+    slot_max = std::max(slot_max, L.bytes);
+    cand.push_back(l);
+  }
+  if (cand.empty()) return EB_OK;
+  const int ns = std::min(SW_NS_MAX, (smem_cap - SW_HEAD - 128) / slot_max);
+  if (ns < 6) return EB_OK;
+  eb_status st = EB_OK;
+  for (int l : cand) {
+    Op<T>& o = ops[l];
+    SweepLev<T>& sw = H.sw[l];
+    const DevLevel& Lv = P->G->L[l];
+    const int two = o.x[1] != nullptr;
+    sw.ntx = (o.n[0] + SW_TX - 1) / SW_TX;
+    sw.nty = (o.n[1] + sw.ty - 1) / sw.ty;
+    sw.nzc = (o.n[2] + sw.zc - 1) / sw.zc;
+    sw.nitems = sw.ntx * sw.nty * sw.nzc;
+    if (sw.nitems > 32 * SW_MASK_MAX) continue;  // more items than the mask in shared memory holds
+    for (int p = 0; p < 2; ++p) {
+      sw.alt[p] = nullptr;
+      if (o.x[p]) {
+        sw.alt[p] = (T*)dev_alloc(P->allocs, sizeof(T) * (size_t)o.ncell, &P->bytes, &st);
+        if (st == EB_OK) cudaMemsetAsync(sw.alt[p], 0, sizeof(T) * (size_t)o.ncell, P->s);
+      }
+    }
+    const int nw = (sw.nitems + 31) / 32;
+    unsigned* has1 = (unsigned*)dev_alloc(P->allocs, sizeof(unsigned) * nw, &P->bytes, &st);
+    CUtensorMap* dmaps = (CUtensorMap*)dev_alloc(P->allocs, sizeof(CUtensorMap) * 7, &P->bytes, &st);
+    if (st != EB_OK) return st;
+    CUtensorMap maps[7];
+    std::memset(maps, 0, sizeof(maps));
+    const int by = sw.ty + 2 * SW_HY;
+    const CUtensorMapDataType ft = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    bool ok = tmap3(&maps[0], ft, 4, o.x[0], o.n, SW_BX, by) && tmap3(&maps[2], ft, 4, sw.alt[0], o.n, SW_BX, by) &&
+              tmap3(&maps[4], ft, 4, o.b[0], o.n, SW_BX, by) &&
+              tmap3(&maps[6], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, Lv.flags, o.n, SW_FBX, by);
+    if (ok && two)
+      ok = tmap3(&maps[1], ft, 4, o.x[1], o.n, SW_BX, by) && tmap3(&maps[3], ft, 4, sw.alt[1], o.n, SW_BX, by) &&
+           tmap3(&maps[5], ft, 4, o.b[1], o.n, SW_BX, by);
+    if (!ok) continue;  // this level keeps the colour passes
+    cudaMemsetAsync(has1, 0, sizeof(unsigned) * nw, P->s);
+    if (two)
+      k_sweep_has1<<<sw.nitems, 256, 0, P->s>>>(Lv.flags, o.n[0], o.n[1], o.n[2], sw.ntx, sw.nty, sw.ty, sw.zc,
+                                                sw.nitems, has1);
+    cudaError_t e = cudaMemcpyAsync(dmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, P->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep setup");
+    sw.maps = dmaps;
+    sw.has1 = has1;
+    sw.par = 0;
+    sw.on = 1;
+    ++P->sweep_levels;
+    if (P->sweep_first < 0) P->sweep_first = l;
+  }
+  if (P->sweep_levels) {
+    H.sw_ns = ns;
+    P->sweep_ns = ns;
+    P->sweep_bytes = SW_HEAD + 128 + ns * slot_max;
+  }
+  return EB_OK;
+}
 
 template <class T>
 static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
@@ -588,7 +738,17 @@ static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
   }
   P->bm = H.bm;
   P->bottom = H.gkry ? EB_BOTTOM_KRYLOV : H.gbot ? EB_BOTTOM_INV32 : H.bm ? EB_BOTTOM_INV64 : EB_BOTTOM_RELAX;
-  P->smem_bytes = H.smem_bytes;
+  {
+    // dynamic shared memory the persistent kernel may take (the device's
+    // opt-in maximum less room for its static shared memory)
+    int smax = 0;
+    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->G->device);
+    st = setup_sweeps<T>(P, ops, H, smax - 16 * 1024);
+    if (st != EB_OK) return st;
+  }
+  // CTA 0 keeps the coarse levels in its dynamic shared memory and sits the
+  // streamed sweeps out; the other CTAs use the same bytes for the sweep ring
+  P->smem_bytes = std::max(H.smem_bytes, P->sweep_bytes);
   P->d_hier = dev_alloc(P->allocs, sizeof(Hier<T>), &P->bytes, &st);
   if (st == EB_OK) {
     cudaError_t e = cudaMemcpy(P->d_hier, &H, sizeof(Hier<T>), cudaMemcpyHostToDevice);
@@ -627,6 +787,8 @@ static eb_status setup_persistent(eb_poisson* P) {
     const void* fb = mixed ? (const void*)k_solve_batch<float> : (const void*)k_solve_batch<double>;
     e = cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
   }
+  if (e == cudaSuccess && P->sweep_levels)
+    e = cudaFuncSetAttribute((const void*)k_sweep_phase<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
   if (e == cudaSuccess)
     e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<float>, PT, P->smem_bytes)
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<double>, PT, P->smem_bytes);
@@ -894,6 +1056,7 @@ extern "C" eb_status eb_poisson_solve(eb_poisson* P, const double* d_rhs, const 
     inf.rel_res = b > 0.0 ? r / b : 0.0;
     inf.bottom = P->bottom;
     inf.levels = P->nlev;
+    inf.sweep_levels = P->sweep_levels;
     if (info) *info = inf;
     return st;
   }
@@ -947,6 +1110,7 @@ extern "C" eb_status eb_poisson_solve(eb_poisson* P, const double* d_rhs, const 
   inf.rel_res = b > 0.0 ? r / b : 0.0;
   inf.bottom = EB_BOTTOM_RELAX;  // the per-phase paths relax the coarsest level
   inf.levels = P->nlev;
+  inf.sweep_levels = 0;  // the per-phase paths relax by colour passes
   if (info) *info = inf;
   return st;
 }
@@ -957,18 +1121,23 @@ extern "C" eb_status eb_poisson_solve(eb_poisson* P, const double* d_rhs, const 
 // CTAs per instance for a batch on `total` CTAs: one each, the rest in
 // proportion to the instances' cell counts (largest remainders), at most
 // `cap` per instance.
-static std::vector<int> split_ctas(const std::vector<long long>& cells, int total, int cap) {
+// An instance with tile-streamed sweeps takes at least two CTAs (its CTA 0
+// sits the sweeps out), given in `mins`.
+static std::vector<int> split_ctas(const std::vector<long long>& cells, int total, int cap,
+                                   const std::vector<int>& mins) {
   int n = (int)cells.size();
-  std::vector<int> size(n, 1);
+  std::vector<int> size(mins);
   long long sum = 0;
+  int used = 0;
   for (long long c : cells) sum += c;
-  int left = total - n;
+  for (int m : mins) used += m;
+  int left = total - used;
   if (left <= 0 || sum <= 0) return size;
   std::vector<std::pair<double, int>> rem;
   int given = 0;
   for (int i = 0; i < n; ++i) {
     double share = (double)left * (double)cells[i] / (double)sum;
-    int whole = std::min((int)share, cap - 1);
+    int whole = std::max(0, std::min((int)share, cap - size[i]));
     size[i] += whole;
     given += whole;
     rem.push_back({share - whole, i});
@@ -993,7 +1162,9 @@ static eb_status launch_batch_t(eb_poisson* const* P, int n, int max_iters, int 
   for (int i = 0; i < n; ++i) cells[i] = P[i]->G->L[0].g.ncell;
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P[0]->G->device);
-  std::vector<int> size = split_ctas(cells, grid_total, std::max(1, nsm));
+  std::vector<int> mins(n);
+  for (int i = 0; i < n; ++i) mins[i] = P[i]->sweep_levels ? 2 : 1;
+  std::vector<int> size = split_ctas(cells, grid_total, std::max(2, nsm), mins);
   std::vector<BatchItem<T>> items(n);
   std::vector<int> cta_item;
   int start = 0;
@@ -1127,9 +1298,15 @@ eb_status batch_step(eb_poisson* const* P, int n, const double* const* rhs, cons
       eb_status st = batch_prepare(P[i], rhs[i], sigma ? sigma[i] : nullptr, phi[i], s);
       if (st != EB_OK) return st;
     }
-  // at most `total` instances per launch
-  for (int b0 = 0; b0 < n; b0 += total) {
-    int m = std::min(total, n - b0);
+  // as many instances per launch as their minimum CTA counts allow
+  for (int b0 = 0, m = 0; b0 < n; b0 += m) {
+    int need = 0;
+    for (m = 0; b0 + m < n; ++m) {
+      const int c = P[b0 + m]->sweep_levels ? 2 : 1;
+      if (need + c > total) break;
+      need += c;
+    }
+    if (m == 0) m = 1;  // (total >= 2 on every device with a persistent kernel)
     eb_status st = mixed ? launch_batch_t<float>(P + b0, m, max_iters, total, smem, s, kernel_ms)
                          : launch_batch_t<double>(P + b0, m, max_iters, total, smem, s, kernel_ms);
     if (st != EB_OK) return st;
@@ -1160,6 +1337,7 @@ void batch_info(eb_poisson* Q, eb_solve_info* inf) {
   inf->rel_res = b > 0.0 ? r / b : 0.0;
   inf->bottom = Q->bottom;
   inf->levels = Q->nlev;
+  inf->sweep_levels = Q->sweep_levels;
 }
 
 extern "C" eb_status eb_poisson_solve_batched(eb_poisson* const* P, int n, const double* const* d_rhs,
@@ -1270,6 +1448,41 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
       set_error("a grid barrier wait gave up");
       return EB_ERR_TIMEOUT;
     }
+    return EB_OK;
+  }
+  if (P && kernel == 4 && reps >= 1 && ms && bytes) {
+    // one tile-streamed sweep (both colours) of the finest level on its own
+    if (!P->persistent || P->o.precision != EB_PREC_MIXED || P->sweep_first != 0) {
+      set_error("the finest level has no tile-streamed sweep");
+      return EB_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(P->d_bar, 0, 4 * sizeof(unsigned), s);
+    int* err = (int*)(P->d_bar + 2);
+    const Hier<float>* H = (const Hier<float>*)P->d_hier;
+    const size_t dyn = (size_t)P->sweep_bytes;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_sweep_phase<float><<<P->grid, PT, dyn, s>>>(H, 0, err);
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < reps; ++i) k_sweep_phase<float><<<P->grid, PT, dyn, s>>>(H, 0, err);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    unsigned bar[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(bar, P->d_bar, sizeof(bar), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep profile");
+    if (bar[2]) {
+      set_error("a sweep wait gave up");
+      return EB_ERR_TIMEOUT;
+    }
+    *ms = (double)t / reps;
+    // read x and b, write x (4 bytes each), read the flag byte, per cell
+    *bytes = (double)P->G->L[0].g.ncell * 13.0;
     return EB_OK;
   }
   if (!P || reps < 1 || (kernel != 0 && kernel != 1) || !ms || !bytes) {

@@ -68,7 +68,7 @@ class SolverOpts(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("vcycles", C.c_int), ("rel_res", C.c_double),
                 ("bnorm", C.c_double), ("kernel_launches", C.c_longlong), ("kernel_ms", C.c_double),
-                ("bottom", C.c_int), ("levels", C.c_int)]
+                ("bottom", C.c_int), ("levels", C.c_int), ("sweep_levels", C.c_int)]
 
 
 class ServerOpts(C.Structure):
@@ -277,7 +277,8 @@ def eb_poisson_solve(handle, rhs, sigma, phi, stream=None) -> dict:
         _check(st, "eb_poisson_solve")
     return dict(status=info.status, outer_iters=info.outer_iters, vcycles=info.vcycles, rel_res=info.rel_res,
                 bnorm=info.bnorm, kernel_launches=info.kernel_launches, kernel_ms=info.kernel_ms,
-                bottom=BOTTOM_NAMES.get(info.bottom, "none"), levels=info.levels)
+                bottom=BOTTOM_NAMES.get(info.bottom, "none"), levels=info.levels,
+                sweep_levels=info.sweep_levels)
 
 
 def eb_poisson_profile(handle, kernel: int, reps: int, stream=None):
@@ -290,7 +291,8 @@ def eb_poisson_profile(handle, kernel: int, reps: int, stream=None):
 def _info_dict(info):
     return dict(status=info.status, outer_iters=info.outer_iters, vcycles=info.vcycles, rel_res=info.rel_res,
                 bnorm=info.bnorm, kernel_launches=info.kernel_launches, kernel_ms=info.kernel_ms,
-                bottom=BOTTOM_NAMES.get(info.bottom, "none"), levels=info.levels)
+                bottom=BOTTOM_NAMES.get(info.bottom, "none"), levels=info.levels,
+                sweep_levels=info.sweep_levels)
 
 
 def eb_poisson_solve_batched(handles, rhs, sigma, phi, stream=None) -> list:

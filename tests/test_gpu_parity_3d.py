@@ -132,3 +132,20 @@ def test_pin_plane_128_solution_satisfies_oracle_system():
     assert info["status"] == 0 and info["rel_res"] <= 1e-10, info
     rel = np.abs(b - A @ og.to_dofs(phi.cpu().numpy())).max() / np.abs(b).max()
     assert rel <= 2e-10, rel
+
+
+@pytest.mark.parametrize("case", CASES[:2], ids=IDS[:2])
+def test_solve_parity_3d_tile_streamed_sweeps(case, oracles, monkeypatch):
+    """The 32^3 cases with the finest level relaxed by tile-streamed sweeps
+    (TMA-staged, both colours per pass; the default applies them from 64^3):
+    the FP32 V-cycles in FP64 defect correction still reach the oracle's
+    solution."""
+    monkeypatch.setenv("EBP_SWEEP_MIN_CELLS", "1")
+    name, d, S, sig = case
+    og, ophi = oracles[name][:2]
+    g = E.Geometry(d)
+    P = E.Poisson(g, precision="mixed", tol=1e-12, max_cycles=300)
+    phi, info = P.solve(torch.from_numpy(S), torch.from_numpy(sig))
+    assert info["status"] == 0, info
+    assert info["sweep_levels"] >= 1, info
+    assert np.abs(phi.cpu().numpy() - ophi).max() <= 1e-9 * np.abs(ophi).max(), info
