@@ -189,7 +189,7 @@ typedef struct {
                        events on the stream they ran on; 0 on the multi-launch paths */
   int bottom;       /* how the coarsest level was solved: EB_BOTTOM_* */
   int levels;       /* multigrid levels of the V-cycle */
-  int sweep_levels; /* levels relaxed by tile-streamed sweeps (FP32 3D levels from 64^3 cells with an x
+  int sweep_levels; /* levels relaxed by tile-streamed sweeps (FP32 3D levels from 128^3 cells with an x
                        extent a multiple of 16: both colours in one pass over the level, tiles staged
                        in shared memory by TMA); the others use one pass per colour */
 } eb_solve_info;
@@ -338,6 +338,13 @@ eb_status eb_amr_residual(eb_amr* A, const double* d_rhs_c, const double* d_sig_
  * The work space (27 composite vectors) is allocated at the first call. */
 eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double* d_sig_c, const double* d_rhs_f,
                        const double* d_sig_f, double* d_phi_c, double* d_phi_f, eb_solve_info* info, void* stream);
+/* Benchmark hook (no counterpart in the paper): the persistent multigrid
+ * launches of the last eb_amr_solve, for the coarse correction solver
+ * (out[0..3]) and the fine one (out[4..7]): launches, their summed device
+ * time in ms (CUDA events on their stream), V-cycles, FP64 outer iterations.
+ * info->kernel_ms of eb_amr_solve is the summed time of those launches;
+ * info->kernel_launches counts every kernel the call launched. */
+eb_status eb_amr_kernel_stats(const eb_amr* A, double out[8]);
 void eb_amr_destroy(eb_amr* A);
 
 /* ---------------------------------------------------------------- serving

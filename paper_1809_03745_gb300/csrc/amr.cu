@@ -269,7 +269,17 @@ struct eb_amr {
   double* d_part = nullptr;
   std::vector<void*> allocs;
   long long bytes = 0;
+  // persistent solve launches of the last composite solve, coarse [0] and
+  // fine [1] correction solvers: launches, kernel ms, V-cycles, FP64 outer iterations
+  double kstat[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
 };
+
+static void amr_count(eb_amr* A, int which, int cyc, int outer, double ms) {
+  A->kstat[which][0] += 1.0;
+  A->kstat[which][1] += ms;
+  A->kstat[which][2] += cyc;
+  A->kstat[which][3] += outer;
+}
 
 static eb_status amr_fail(eb_amr* A, eb_status st) {
   eb_amr_destroy(A);
@@ -445,19 +455,24 @@ static eb_status amr_resid(eb_amr* A, const double* rhs_c, const double* sig_c, 
                            const double* sig_f, const double* phi_c, const double* phi_f, cudaStream_t s) {
   cudaMemcpyAsync(A->pcf, phi_c, 2 * A->ncc * sizeof(double), cudaMemcpyDeviceToDevice, s);
   k_avg_down<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->cflags, A->fflags, A->kf, phi_f, A->pcf, A->ncc, A->nff);
+  note_launch();
   eb_status st = eb_poisson_residual(A->Pc, rhs_c, sig_c, A->pcf, A->rc, s);
   if (st == EB_OK) st = eb_poisson_residual(A->Pf, rhs_f, sig_f, phi_f, A->rf, s);
   if (st != EB_OK) return st;
   if (A->nface) {
     k_cf_flux<<<nb(A->nface), TBA, 0, s>>>(A->faces, A->nface, A->pcf, phi_f, A->eps0, A->hf, A->fl);
+    note_launch();
     for (int sd = 0; sd < A->cfb.nside; ++sd) {
       long long t0 = A->cfb.off[sd], t1 = A->cfb.off[sd + 1];
       k_cf_fine_apply<<<nb(t1 - t0), TBA, 0, s>>>(A->faces, t0, t1, A->fl, A->hf, A->rf);
+      note_launch();
     }
     k_cf_coarse_apply<<<nb(A->ncface), TBA, 0, s>>>(A->cfaces, A->ncface, A->fl, A->pcf, A->ncc, A->hc, A->D,
                                                      A->rc);
+    note_launch();
   }
   k_zero_under<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->rc, A->ncc);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? EB_OK : cuda_fail(e, "composite residual");
 }
@@ -465,7 +480,9 @@ static eb_status amr_resid(eb_amr* A, const double* rhs_c, const double* sig_c, 
 static eb_status amr_norm(eb_amr* A, cudaStream_t s, double* out) {
   cudaMemsetAsync(A->d_norm, 0, sizeof(unsigned long long), s);
   k_absmax2<<<nb(A->ncc), TBA, 0, s>>>(A->cflags, A->ncc, A->rc, A->d_norm);
+  note_launch();
   k_absmax2<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, A->rf, A->d_norm);
+  note_launch();
   unsigned long long v = 0;
   cudaError_t e = cudaMemcpyAsync(&v, A->d_norm, sizeof(v), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -492,7 +509,9 @@ extern "C" eb_status eb_amr_residual(eb_amr* A, const double* d_rhs_c, const dou
 
 static double cv_dot(eb_amr* A, const CVec& a, const CVec& b, cudaStream_t s) {
   k_cv_dot<<<DOT_BLOCKS, TBA, 0, s>>>(A->B, A->cflags, A->ncc, 1, a.c, b.c, A->d_part);
+  note_launch();
   k_cv_dot<<<DOT_BLOCKS, TBA, 0, s>>>(A->B, A->fflags, A->nff, 0, a.f, b.f, A->d_part + DOT_BLOCKS);
+  note_launch();
   double h[2 * DOT_BLOCKS];
   cudaMemcpyAsync(h, A->d_part, sizeof(h), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
@@ -502,7 +521,9 @@ static double cv_dot(eb_amr* A, const CVec& a, const CVec& b, cudaStream_t s) {
 }
 static void cv_axpby(eb_amr* A, double a, const CVec& x, double b, const CVec& y, cudaStream_t s) {
   k_cv_axpby<<<nb(A->ncc), TBA, 0, s>>>(A->cflags, A->ncc, a, x.c, b, y.c);
+  note_launch();
   k_cv_axpby<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, a, x.f, b, y.f);
+  note_launch();
 }
 
 // accuracy asked of the two multigrid corrections inside one FAC step: loose
@@ -517,24 +538,34 @@ static eb_status fac_apply(eb_amr* A, const CVec& v, const CVec& z, const double
   const double tol = FAC_TOL;
   cudaMemcpyAsync(A->rc, v.c, 2 * A->ncc * sizeof(double), cudaMemcpyDeviceToDevice, s);
   k_zero_under<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->rc, A->ncc);
+  note_launch();
   k_restrict_under<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->fflags, v.f, A->rc, A->ncc, A->nff);
-  int cyc = 0;
-  eb_status st = poisson_solve_b(A->Pc, A->rc, A->ec, tol, &cyc, s);
+  note_launch();
+  int cyc = 0, outer = 0;
+  double kms = 0.0;
+  eb_status st = poisson_solve_b(A->Pc, A->rc, A->ec, tol, &cyc, s, &outer, &kms);
   *cycles += cyc;
+  amr_count(A, 0, cyc, outer, kms);
   if (st != EB_OK) return st;
   cudaMemsetAsync(z.c, 0, 2 * A->ncc * sizeof(double), s);
   cudaMemsetAsync(z.f, 0, 2 * A->nff * sizeof(double), s);
   k_add_coarse<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->ec, z.c, A->ncc);
+  note_launch();
   k_prolong_const<<<nb(A->nff), TBA, 0, s>>>(A->B, A->fflags, A->ec, z.f, A->ncc, A->nff);
+  note_launch();
   // what remains on the box: v_f - (A z)_f = v_f - b_f + r_f(z)
   st = amr_resid(A, rhs_c, sig_c, rhs_f, sig_f, z.c, z.f, s);
   if (st != EB_OK) return st;
   k_cv_sub<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, A->bvec.f, A->rf, A->tmp.f);  // (A z)_f
+  note_launch();
   k_cv_axpby<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, 1.0, v.f, -1.0, A->tmp.f);  // v_f - (A z)_f
-  st = poisson_solve_b(A->Pf0, A->tmp.f, A->ef, tol, &cyc, s);
+  note_launch();
+  st = poisson_solve_b(A->Pf0, A->tmp.f, A->ef, tol, &cyc, s, &outer, &kms);
   *cycles += cyc;
+  amr_count(A, 1, cyc, outer, kms);
   if (st != EB_OK) return st;
   k_axpy_masked<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, A->ef, z.f);
+  note_launch();
   return EB_OK;
 }
 
@@ -544,8 +575,11 @@ static eb_status op_apply(eb_amr* A, const CVec& z, const CVec& w, const double*
   eb_status st = amr_resid(A, rhs_c, sig_c, rhs_f, sig_f, z.c, z.f, s);
   if (st != EB_OK) return st;
   k_cv_sub<<<nb(A->ncc), TBA, 0, s>>>(A->cflags, A->ncc, A->bvec.c, A->rc, w.c);
+  note_launch();
   k_zero_under<<<nb(A->ncc), TBA, 0, s>>>(A->B, w.c, A->ncc);
+  note_launch();
   k_cv_sub<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, A->bvec.f, A->rf, w.f);
+  note_launch();
   return EB_OK;
 }
 
@@ -582,6 +616,8 @@ extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double
   cudaStream_t s = (cudaStream_t)stream;
   eb_solve_info inf;
   std::memset(&inf, 0, sizeof(inf));
+  std::memset(A->kstat, 0, sizeof(A->kstat));
+  const long long launches0 = launch_total();
   eb_status st = amr_workspace(A);
   if (st != EB_OK) return st;
   // b: the composite residual at phi = 0
@@ -615,6 +651,7 @@ extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double
     cudaMemcpyAsync(A->V[0].c, A->rc, 2 * A->ncc * sizeof(double), cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(A->V[0].f, A->rf, 2 * A->nff * sizeof(double), cudaMemcpyDeviceToDevice, s);
     k_zero_under<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->V[0].c, A->ncc);
+    note_launch();
     double beta = std::sqrt(cv_dot(A, A->V[0], A->V[0], s));
     if (!(beta > 0.0)) {
       st = EB_OK;
@@ -674,6 +711,7 @@ extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double
   // report phi_c under the box as the fine means
   if (st == EB_OK || st == EB_ERR_NOT_CONVERGED) {
     k_avg_down<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->cflags, A->fflags, A->kf, d_phi_f, d_phi_c, A->ncc, A->nff);
+    note_launch();
     if (st == EB_ERR_NOT_CONVERGED) set_error("composite iteration cap reached");
   }
   cudaError_t e = cudaStreamSynchronize(s);
@@ -683,6 +721,18 @@ extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double
   inf.vcycles = cycles;
   inf.bnorm = bn;
   inf.rel_res = bn > 0.0 ? r / bn : 0.0;
+  inf.kernel_ms = A->kstat[0][1] + A->kstat[1][1];
+  inf.kernel_launches = launch_total() - launches0;
   if (info) *info = inf;
   return st;
+}
+
+extern "C" eb_status eb_amr_kernel_stats(const eb_amr* A, double out[8]) {
+  if (!A || !out) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  for (int w = 0; w < 2; ++w)
+    for (int k = 0; k < 4; ++k) out[4 * w + k] = A->kstat[w][k];
+  return EB_OK;
 }

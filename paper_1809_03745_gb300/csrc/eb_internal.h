@@ -92,6 +92,11 @@ struct CFCoarse {
 eb_status build_cf(const eb_geom* Gf, const eb_geom* Gc, const CFBox& B, CFFace* faces, CFCoarse* cfaces,
                    int* d_status, cudaStream_t s);
 
+// kernels launched by the calling host thread since it started (every launch
+// site of the library adds to it); a call's launches are the difference
+void note_launch(int k = 1);
+long long launch_total();
+
 // error reporting
 void set_error(const std::string& msg);
 eb_status cuda_fail(cudaError_t e, const char* what);
@@ -121,4 +126,5 @@ eb_status batch_step(eb_poisson* const* P, int n, const double* const* rhs, cons
 void batch_info(eb_poisson* Q, eb_solve_info* inf);
 eb_status batch_copy_out(eb_poisson* P, double* phi, cudaStream_t s);
 long long poisson_device_bytes(const eb_poisson* P);
-eb_status poisson_solve_b(eb_poisson* P, const double* d_b, double* d_x, double tol, int* cycles, cudaStream_t user);
+eb_status poisson_solve_b(eb_poisson* P, const double* d_b, double* d_x, double tol, int* cycles, cudaStream_t user,
+                          int* outer = nullptr, double* kernel_ms = nullptr);

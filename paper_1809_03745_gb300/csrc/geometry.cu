@@ -886,6 +886,7 @@ eb_status launch_rhs64(const eb_geom* G, const double* s_rhs, const double* sigm
                        cudaStream_t s) {
   const DevLevel& L = G->L[0];
   k_rhs64<<<nblk(L.g.ncell), TB, 0, s>>>(view(L), s_rhs, sigma, L.bconst, L.bsig, b, (unsigned long long*)bnorm);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? EB_OK : cuda_fail(e, "rhs");
 }

@@ -21,7 +21,8 @@ constexpr long long BAR_WAIT_CYCLES = 4000000000LL;  // ~2 s of SM clock: a barr
 // TMA alignment of the x coordinate), SW_HY in y, flags boxes SW_FBX bytes
 // wide from SW_FHX cells left of the tile (16-byte alignment of bytes).
 constexpr int SW_TX = 32, SW_HX = 4, SW_BX = SW_TX + 2 * SW_HX, SW_HY = 2, SW_FHX = 16, SW_FBX = 64;
-constexpr int SW_NS_MAX = 16;     // ring slots at most
+constexpr int SW_NS = 8;          // ring slots: four planes in use, four in flight
+constexpr int SW_NS_MAX = 16;     // ring slots the shared-memory head has room for
 constexpr int SW_MASK_MAX = 256;  // words of the per-item dielectric mask (8192 tiles x chunks)
 constexpr int SW_HEAD = ((8 * SW_NS_MAX + 4 * SW_MASK_MAX + 4 * SW_NS_MAX + 127) / 128) * 128;
 
@@ -802,23 +803,32 @@ __device__ bool ph_smooth(const Op<T>& o, int nu, const Ctx& c, int l) {
 
 // nu sweeps of grid level l: tile-streamed when the level has them (and the
 // group has CTAs besides CTA 0), else the colour passes above.  A streamed
-// sweep first gives the cut cells their Gauss-Seidel values from the current
-// iterate (all at once) and writes them into x, then relaxes the regular
-// cells of both colours in one pass.
+// sweep relaxes, in order, the red cut cells (their sparse rows from the
+// current iterate, then written), the red and the black regular cells in one
+// pass over the level, and the black cut cells.  Within each of the four
+// groups no cell reads another's new value except through the colour order,
+// as in the colour passes.
 template <class T>
 __device__ bool ph_smooth_grid(const Hier<T>& H, int l, int nu, const Ctx& c) {
   const Op<T>& o = H.op[l];
   if (!H.sw[l].on || c.local || c.gsize < 2) return ph_smooth(o, nu, c, l);
   extern __shared__ __align__(128) unsigned char sw_dyn[];
+  const long long rr = 2 * o.nirr_red, rn = 2 * o.nirr;
   for (int s = 0; s < nu; ++s) {
-    if (o.nirr) {
-      ph_rows(o, 0, 2 * o.nirr, 0, c);
+    if (rr > 0) {
+      ph_rows(o, 0, rr, 0, c);
       if (!c.sync((l << 4) | 2)) return false;
-      ph_write(o, 0, 2 * o.nirr, c);
+      ph_write(o, 0, rr, c);
       if (!c.sync((l << 4) | 4)) return false;
     }
     if (!ph_sweep3d(H, l, c, sw_dyn)) return false;
     if (!c.sync((l << 4) | 13)) return false;
+    if (rn > rr) {
+      ph_rows(H.op[l], rr, rn, 0, c);  // H.op[l]: the swapped view, x now the new iterate
+      if (!c.sync((l << 4) | 2)) return false;
+      ph_write(H.op[l], rr, rn, c);
+      if (!c.sync((l << 4) | 4)) return false;
+    }
   }
   return true;
 }

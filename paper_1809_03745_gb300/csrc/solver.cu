@@ -356,7 +356,13 @@ static Op<T> make_op(const DevLevel& L, std::vector<void*>& owner, long long* by
 static inline int blocks(long long n, int tb = 256) { return (int)std::max<long long>(1, (n + tb - 1) / tb); }
 
 static thread_local long long* g_count = nullptr;  // launch counter of the current call
+static thread_local long long g_total = 0;         // every launch of this thread
+namespace ebp {
+void note_launch(int k) { g_total += k; }
+long long launch_total() { return g_total; }
+}  // namespace ebp
 static inline void counted(int k = 1) {
+  g_total += k;
   if (g_count) *g_count += k;
 }
 
@@ -467,7 +473,7 @@ static bool tmap3(CUtensorMap* m, CUtensorMapDataType type, int esize, const voi
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-static constexpr long long SW_MIN_CELLS = 1LL << 18;  // levels from 64^3 up stream their sweeps
+static constexpr long long SW_MIN_CELLS = 1LL << 21;  // levels from 128^3 up stream their sweeps
 
 // Tile rows and z-chunk of a level for `workers` CTAs: the least of
 // (rounds of items per CTA) x (planes per item) x (bytes of a plane's boxes
@@ -522,8 +528,7 @@ static eb_status setup_sweeps(eb_poisson* P, std::vector<Op<T>>& ops, Hier<T>& H
     cand.push_back(l);
   }
   if (cand.empty()) return EB_OK;
-  const int ns = std::min(SW_NS_MAX, (smem_cap - SW_HEAD - 128) / slot_max);
-  if (ns < 6) return EB_OK;
+  if ((smem_cap - SW_HEAD - 128) / slot_max < SW_NS) return EB_OK;
   eb_status st = EB_OK;
   for (int l : cand) {
     Op<T>& o = ops[l];
@@ -572,9 +577,9 @@ static eb_status setup_sweeps(eb_poisson* P, std::vector<Op<T>>& ops, Hier<T>& H
     if (P->sweep_first < 0) P->sweep_first = l;
   }
   if (P->sweep_levels) {
-    H.sw_ns = ns;
-    P->sweep_ns = ns;
-    P->sweep_bytes = SW_HEAD + 128 + ns * slot_max;
+    H.sw_ns = SW_NS;
+    P->sweep_ns = SW_NS;
+    P->sweep_bytes = SW_HEAD + 128 + SW_NS * slot_max;
   }
   return EB_OK;
 }
@@ -1001,6 +1006,7 @@ extern "C" eb_status eb_poisson_residual(eb_poisson* P, const double* d_rhs, con
   const Op<double>& o = P->op64[0];
   if (o.nirr) k_rows<double><<<blocks(2 * o.nirr), 256, 0, P->s>>>(o, 0, 2 * o.nirr, 1);
   k_resid_field<<<blocks(n), 256, 0, P->s>>>(o, d_r);
+  counted(o.nirr ? 3 : 2);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
   join_out(P, user);
@@ -1242,7 +1248,8 @@ long long poisson_device_bytes(const eb_poisson* P) { return P->bytes; }
 // A x = b for a right-hand side given in integrated form (boundary data not
 // added: a correction equation with homogeneous data), from x = 0, to
 // max|r| <= tol max|b|.  d_b and d_x are [2][ncell] on `user`'s stream.
-eb_status poisson_solve_b(eb_poisson* P, const double* d_b, double* d_x, double tol, int* cycles, cudaStream_t user) {
+eb_status poisson_solve_b(eb_poisson* P, const double* d_b, double* d_x, double tol, int* cycles, cudaStream_t user,
+                          int* outer, double* kernel_ms) {
   if (!P->persistent) {
     set_error("correction solves need the persistent path");
     return EB_ERR_UNSUPPORTED;
@@ -1253,6 +1260,7 @@ eb_status poisson_solve_b(eb_poisson* P, const double* d_b, double* d_x, double 
   k_copy_masked<<<blocks(n), 256, 0, P->s>>>(F.flags, n, d_b, P->b64);
   cudaMemsetAsync(P->d_norm + 1, 0, sizeof(unsigned long long), P->s);
   k_absmax_masked<<<blocks(n), 256, 0, P->s>>>(F.flags, n, P->b64, P->d_norm + 1);
+  counted(2);
   cudaMemsetAsync(P->phi64, 0, 2 * n * sizeof(double), P->s);
   double keep = P->o.tol;
   P->o.tol = tol;
@@ -1262,10 +1270,13 @@ eb_status poisson_solve_b(eb_poisson* P, const double* d_b, double* d_x, double 
   P->o.tol = keep;
   if (st == EB_OK && status != EB_OK && status != EB_ERR_NOT_CONVERGED) st = (eb_status)status;
   k_copy_masked<<<blocks(n), 256, 0, P->s>>>(F.flags, n, P->phi64, d_x);
+  counted();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess && st == EB_OK) st = cuda_fail(e, "correction solve");
   join_out(P, user);
   if (cycles) *cycles = cyc;
+  if (outer) *outer = iters;
+  if (kernel_ms) *kernel_ms = P->kernel_ms;
   return st;
 }
 

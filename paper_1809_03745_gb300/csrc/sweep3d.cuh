@@ -88,24 +88,30 @@ struct SweepSlot {
   }
 };
 
-// Relaxes one regular cell (i, j, k) at box position (lx, ly) of the ring
-// slots sm (plane k - 1), s0 (plane k), sp (plane k + 1): the implicit
-// stencil of reg_stencil, with the same terms in the same order.
+// Relaxes one cell (i, j, k) at box position (lx, ly) of the ring slots sm
+// (plane k - 1), s0 (plane k), sp (plane k + 1) when it is a regular cell of
+// the level: the implicit stencil of reg_stencil, with the same terms in the
+// same order.  Cells off the grid, cut cells and cells without an unknown
+// are left alone.
 template <class T>
 __device__ __forceinline__ void sw_relax(const Op<T>& o, unsigned char* ring, const SweepSlot<T>& L, int two, int i,
                                          int j, int k, int lx, int ly, int sm, int s0, int sp) {
-  if (i < 0 || i >= o.n[0] || j < 0 || j >= o.n[1]) return;
-  const int by = L.fb / SW_FBX;
-  const unsigned char* F = ring + (long long)s0 * L.bytes + (two ? 4 : 2) * L.xb;
-  const unsigned f = F[ly * SW_FBX + lx + (SW_FHX - SW_HX)];
-  if ((f & F_IRR) || !(f & 3u)) return;
-  const int p = (f & 1u) ? 0 : 1;
+  if ((unsigned)i >= (unsigned)o.n[0] || (unsigned)j >= (unsigned)o.n[1]) return;
+  const unsigned char* F = ring + s0 * L.bytes + (two ? 4 : 2) * L.xb;
+  const unsigned f = F[ly * SW_FBX + lx + (SW_FHX - SW_HX)] & 7u;
+  if (f != 1u && f != 2u) return;  // regular: exactly one phase, no sparse row
+  const int p = (int)f - 1;
   const int xo = p * L.xb, bo = (two ? 2 : 1) * L.xb + p * L.xb;
-  T* Xc = (T*)(ring + (long long)s0 * L.bytes + xo);
-  const T* Xm = (const T*)(ring + (long long)sm * L.bytes + xo);
-  const T* Xp = (const T*)(ring + (long long)sp * L.bytes + xo);
-  const T* Bc = (const T*)(ring + (long long)s0 * L.bytes + bo);
+  T* Xc = (T*)(ring + s0 * L.bytes + xo);
+  const T* Xm = (const T*)(ring + sm * L.bytes + xo);
+  const T* Xp = (const T*)(ring + sp * L.bytes + xo);
+  const T bc = ((const T*)(ring + s0 * L.bytes + bo))[ly * SW_BX + lx];
   const int e = ly * SW_BX + lx;
+  if (i > 0 && i < o.n[0] - 1 && j > 0 && j < o.n[1] - 1 && k > 0 && k < o.n[2] - 1) {
+    const T sum = ((((Xc[e - 1] + Xc[e + 1]) + Xc[e - SW_BX]) + Xc[e + SW_BX]) + Xm[e]) + Xp[e];
+    Xc[e] = (o.h2e[p] * bc + sum) * inv_count(6, T(0));
+    return;
+  }
   const T third = T(1) / T(3);
   T sum = T(0);
   int dg = 0;
@@ -151,30 +157,37 @@ __device__ __forceinline__ void sw_relax(const Op<T>& o, unsigned char* ring, co
     sum += Xm[e] * third;
     dg += 3;
   }
-  (void)by;
-  Xc[e] = (o.h2e[p] * Bc[e] + sum) * inv_count(dg, T(0));
+  Xc[e] = (o.h2e[p] * bc + sum) * inv_count(dg, T(0));
 }
 
-// One fused sweep of grid level l (SweepLev on), x -> alt, then x and alt
-// swap in this CTA's copy of the hierarchy.  CTA 0 of the group keeps the
-// coarse levels in its shared memory and sits the sweep out; the other CTAs
-// take the tiles round-robin.  `dyn` is the dynamic shared memory.
+// One fused pass over the regular cells of grid level l (SweepLev on),
+// x -> alt, then x and alt swap in this CTA's copy of the hierarchy.  CTA 0
+// of the group keeps the coarse levels in its shared memory and sits the
+// pass out; the other CTAs take the tiles round-robin.  `dyn` is the
+// dynamic shared memory.
+//
+// Step zs of an item: wait for plane zs + 1; red cells of plane zs (tile
+// and ring); one block barrier; black cells of plane zs - 1 (tile); store
+// plane zs - 2, final since the barrier; refill the slot of plane zs - 3,
+// which nothing reads any more.  The ring has SW_NS slots: four planes in
+// use, four in flight.
 template <class T>
 __device__ bool ph_sweep3d(const Hier<T>& Hc, int l, const Ctx& c, unsigned char* dyn) {
   Hier<T>& H = const_cast<Hier<T>&>(Hc);
   Op<T>& o = H.op[l];
   SweepLev<T>& sw = H.sw[l];
   const int two = o.x[1] != nullptr;
-  const int ty = sw.ty, by = ty + 2 * SW_HY, NS = H.sw_ns;
+  const int ty = sw.ty;
   const SweepSlot<T> L(ty, two);
   const int nw = c.gsize - 1, w = c.gcta - 1;
   const int n0 = o.n[0], n1 = o.n[1], n2 = o.n[2];
   const long long sxy = (long long)n0 * n1;
   const int K = (w >= 0 && sw.nitems > w) ? (sw.nitems - 1 - w) / nw + 1 : 0;
-  // layout: NS mbarriers, item mask words, NS has1 flags, then the ring (128-aligned)
+  // layout: SW_NS mbarriers, item mask words, SW_NS has1 flags, a fail flag, then the ring
   unsigned long long* bars = (unsigned long long*)dyn;
   unsigned* mask = (unsigned*)(dyn + 8 * SW_NS_MAX);
   int* slot1 = (int*)(dyn + 8 * SW_NS_MAX + 4 * SW_MASK_MAX);
+  volatile int* sfail = slot1 + SW_NS_MAX;
   // the ring starts on a 128-byte boundary of the shared window (the host
   // reserves 128 bytes of slack for this)
   unsigned char* ring = dyn + SW_HEAD + ((128u - (smem_u32(dyn + SW_HEAD) & 127u)) & 127u);
@@ -184,8 +197,9 @@ __device__ bool ph_sweep3d(const Hier<T>& Hc, int l, const Ctx& c, unsigned char
     const int nwords = (sw.nitems + 31) >> 5;
     for (int q = threadIdx.x; q < nwords; q += blockDim.x) mask[q] = two ? sw.has1[q] : 0u;
     if (threadIdx.x == 0) {
-      for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
+      for (int s = 0; s < SW_NS; ++s) mbar_init(bar0 + 8 * s, 1);
       fence_mbar_init();
+      *sfail = 0;
     }
     __syncthreads();
     const int ntx = sw.ntx, nty = sw.nty, zc = sw.zc;
@@ -195,9 +209,6 @@ __device__ bool ph_sweep3d(const Hier<T>& Hc, int l, const Ctx& c, unsigned char
     const void* mb0 = mp + 128 * 4;
     const void* mb1 = mp + 128 * 5;
     const void* mf = mp + 128 * 6;
-    // issue cursor (thread 0): item ik, plane index it within it, load index iq
-    int ik = 0, itp = 0;
-    unsigned long long iq = 0;
     auto geom = [&](int k, int& x0, int& y0, int& z0, int& z1, int& h1) {
       const int it = w + k * nw;
       const int tx = it % ntx, r = it / ntx;
@@ -207,122 +218,134 @@ __device__ bool ph_sweep3d(const Hier<T>& Hc, int l, const Ctx& c, unsigned char
       z1 = min(z0 + zc, n2);
       h1 = (mask[it >> 5] >> (it & 31)) & 1;
     };
-    auto issue = [&](unsigned long long limit) {
+    // issue cursor (thread 0): item ik and its geometry, plane index itp, load index iq
+    int ik = 0, itp = 0, iq = 0;
+    int gx0 = 0, gy0 = 0, gz0 = 0, gz1 = 0, gh1 = 0;
+    if (threadIdx.x == 0) geom(0, gx0, gy0, gz0, gz1, gh1);
+    auto issue = [&](int limit) {
       while (iq < limit && ik < K) {
-        int x0, y0, z0, z1, h1;
-        geom(ik, x0, y0, z0, z1, h1);
-        const int s = (int)(iq % NS);
+        const int s = iq & (SW_NS - 1);
         const unsigned bar = bar0 + 8 * s;
-        const unsigned base = smem_u32(ring + (long long)s * L.bytes);
-        const int z = z0 - 2 + itp;
-        slot1[s] = h1;
-        mbar_expect_tx(bar, (unsigned)((h1 ? 4 : 2) * L.xb + L.fb));
-        tma_load3(base, mx0, x0 - SW_HX, y0 - SW_HY, z, bar);
-        tma_load3(base + (two ? 2 : 1) * L.xb, mb0, x0 - SW_HX, y0 - SW_HY, z, bar);
-        if (h1) {
-          tma_load3(base + L.xb, mx1, x0 - SW_HX, y0 - SW_HY, z, bar);
-          tma_load3(base + 3 * L.xb, mb1, x0 - SW_HX, y0 - SW_HY, z, bar);
+        const unsigned base = smem_u32(ring + s * L.bytes);
+        const int z = gz0 - 2 + itp;
+        slot1[s] = gh1;
+        mbar_expect_tx(bar, (unsigned)((gh1 ? 4 : 2) * L.xb + L.fb));
+        tma_load3(base, mx0, gx0 - SW_HX, gy0 - SW_HY, z, bar);
+        tma_load3(base + (two ? 2 : 1) * L.xb, mb0, gx0 - SW_HX, gy0 - SW_HY, z, bar);
+        if (gh1) {
+          tma_load3(base + L.xb, mx1, gx0 - SW_HX, gy0 - SW_HY, z, bar);
+          tma_load3(base + 3 * L.xb, mb1, gx0 - SW_HX, gy0 - SW_HY, z, bar);
         }
-        tma_load3(base + (two ? 4 : 2) * L.xb, mf, x0 - SW_FHX, y0 - SW_HY, z, bar);
+        tma_load3(base + (two ? 4 : 2) * L.xb, mf, gx0 - SW_FHX, gy0 - SW_HY, z, bar);
         ++iq;
-        if (++itp == z1 - z0 + 4) {
+        if (++itp == gz1 - gz0 + 4) {
           itp = 0;
-          ++ik;
+          if (++ik < K) geom(ik, gx0, gy0, gz0, gz1, gh1);
         }
       }
     };
     if (threadIdx.x == 0) {
       fence_async_global();  // x was last written by generic stores of other CTAs
-      issue((unsigned long long)NS);
+      issue(SW_NS);
     }
-    unsigned long long qb = 0, waited = 0;
+    // thread mapping: the tile's cells of one colour, 16 per row (t < 16 ty);
+    // the ring's red cells (2 rows of 17, one per tile row) by t < ty + 34
+    const int t = threadIdx.x;
+    const int tr = t >> 4, tm = t & 15;
+    const bool tin = t < 16 * ty;
+    int qb = 0, waited = 0;
     for (int k = 0; k < K && ok; ++k) {
       int x0, y0, z0, z1, h1;
       geom(k, x0, y0, z0, z1, h1);
-      for (int zs = z0 - 1; zs <= z1; ++zs) {
-        // planes up to zs + 1 have landed
-        const unsigned long long need = qb + (unsigned long long)(zs - z0 + 3);
-        bool good = true;
+      for (int zs = z0 - 1; zs <= z1 + 1; ++zs) {
+        // planes up to zs + 1 (the item's last is z1 + 1) have landed
+        const int need = qb + min(zs + 1, z1 + 1) - (z0 - 2);
         for (; waited <= need; ++waited)
-          if (!mbar_wait(bar0 + 8 * (unsigned)(waited % NS), (unsigned)((waited / NS) & 1ull))) {
-            good = false;
+          if (!mbar_wait(bar0 + 8 * (waited & (SW_NS - 1)), (unsigned)((waited / SW_NS) & 1))) {
+            *sfail = 1;
             break;
           }
-        if (__syncthreads_or(!good)) {
-          ok = false;
-          break;
-        }
-        // ring slots of planes zs - 2 .. zs + 1 (the first is unused at zs = z0 - 1)
-        const long long qz = (long long)qb + (zs - z0);
-        const int sm2 = (int)((qz < 0 ? qz + NS : qz) % NS), sm = (int)((qz + 1) % NS), s0 = (int)((qz + 2) % NS),
-                  sp = (int)((qz + 3) % NS);
+        const int q0 = qb + zs - z0 + 2;  // load index of plane zs
+        const int sm2 = (q0 - 2) & (SW_NS - 1), sm = (q0 - 1) & (SW_NS - 1), s0 = q0 & (SW_NS - 1),
+                  sp = (q0 + 1) & (SW_NS - 1);
         // red cells of plane zs on the tile and its one-cell ring
-        if (zs >= 0 && zs < n2) {
-          const int nred = (ty + 2) * 17;
-          for (int idx = threadIdx.x; idx < nred; idx += blockDim.x) {
-            const int ly = 1 + idx / 17, m = idx - (idx / 17) * 17;
-            const int j = y0 - SW_HY + ly;
-            const int lx = 3 + ((j + zs + 1) & 1) + 2 * m;
-            sw_relax(o, ring, L, two, x0 - SW_HX + lx, j, zs, lx, ly, sm, s0, sp);
+        if (zs <= z1 && zs >= 0 && zs < n2) {
+          if (tin) {
+            const int j = y0 + tr;
+            const int lx = SW_HX + ((j + zs) & 1) + 2 * tm;
+            sw_relax(o, ring, L, two, x0 - SW_HX + lx, j, zs, lx, SW_HY + tr, sm, s0, sp);
           }
-        }
-        __syncthreads();
-        // black cells of plane zs - 1 on the tile
-        const int zw = zs - 1;
-        if (zw >= z0 && zw < n2) {
-          const int nblk = ty * 16;
-          for (int idx = threadIdx.x; idx < nblk; idx += blockDim.x) {
-            const int ly = SW_HY + (idx >> 4), m = idx & 15;
-            const int j = y0 - SW_HY + ly;
-            const int lx = SW_HX + ((j + zw + 1) & 1) + 2 * m;
-            sw_relax(o, ring, L, two, x0 - SW_HX + lx, j, zw, lx, ly, sm2, sm, s0);
+          if (t < ty + 34) {
+            int j, lx, ly;
+            if (t < 34) {  // ring rows above and below the tile
+              ly = t < 17 ? SW_HY - 1 : SW_HY + ty;
+              j = y0 - SW_HY + ly;
+              lx = SW_HX - 1 + ((j + zs + 1) & 1) + 2 * (t < 17 ? t : t - 17);
+            } else {  // the ring cell at the left or right end of a tile row
+              ly = SW_HY + t - 34;
+              j = y0 - SW_HY + ly;
+              lx = ((j + zs) & 1) ? SW_HX - 1 : SW_HX + SW_TX;
+            }
+            sw_relax(o, ring, L, two, x0 - SW_HX + lx, j, zs, lx, ly, sm, s0, sp);
           }
         }
         fence_async_smem();
         __syncthreads();
-        // plane zs - 2 is no longer read: its slot takes the next load
-        if (threadIdx.x == 0) issue((unsigned long long)(qz + 1 + NS));
-        // store plane zs - 1 (the tile's unknowns, both colours, cut cells as given)
-        if (zw >= z0 && zw < n2) {
-          const unsigned char* F = ring + (long long)sm * L.bytes + (two ? 4 : 2) * L.xb;
-          const int h1w = slot1[sm];
-          for (int idx = threadIdx.x; idx < SW_TX * ty; idx += blockDim.x) {
+        if (*sfail) {
+          ok = false;
+          break;
+        }
+        // black cells of plane zs - 1 on the tile
+        const int zw = zs - 1;
+        if (zw >= z0 && zw < z1 && tin) {
+          const int j = y0 + tr;
+          const int lx = SW_HX + ((j + zw + 1) & 1) + 2 * tm;
+          sw_relax(o, ring, L, two, x0 - SW_HX + lx, j, zw, lx, SW_HY + tr, sm2, sm, s0);
+        }
+        // store plane zs - 2: the tile's unknowns, both colours, cut cells as given
+        const int zo = zs - 2;
+        if (zo >= z0 && zo < z1) {
+          const int so = (q0 - 2 - 0) & (SW_NS - 1);
+          const unsigned char* F = ring + ((q0 - 2) & (SW_NS - 1)) * L.bytes + (two ? 4 : 2) * L.xb;
+          (void)so;
+          const int h1w = slot1[(q0 - 2) & (SW_NS - 1)];
+          const T* X0 = (const T*)(ring + ((q0 - 2) & (SW_NS - 1)) * L.bytes);
+          for (int idx = t; idx < SW_TX * ty; idx += blockDim.x) {
             const int ry = idx >> 5, rx = idx & 31;
             const int i = x0 + rx, j = y0 + ry;
             if (i >= n0 || j >= n1) continue;
             const int ly = SW_HY + ry, lx = SW_HX + rx;
             const unsigned f = F[ly * SW_FBX + lx + (SW_FHX - SW_HX)];
-            const long long cc = (long long)zw * sxy + (long long)j * n0 + i;
+            const long long cc = (long long)zo * sxy + (long long)j * n0 + i;
             const int e = ly * SW_BX + lx;
-            if (f & 1u) sw.alt[0][cc] = ((const T*)(ring + (long long)sm * L.bytes))[e];
-            if ((f & 2u) && h1w) sw.alt[1][cc] = ((const T*)(ring + (long long)sm * L.bytes + L.xb))[e];
+            if (f & 1u) sw.alt[0][cc] = X0[e];
+            if ((f & 2u) && h1w) sw.alt[1][cc] = ((const T*)((const unsigned char*)X0 + L.xb))[e];
           }
         }
+        // the slots of planes up to zs - 3 are free (their last readers ran
+        // before the barrier): refill them
+        if (t == 0) issue(qb + max(0, zs - z0) + SW_NS);
       }
-      qb += (unsigned long long)(z1 - z0 + 4);
-      // the item's last planes are free once every thread has stored plane z1 - 1
-      fence_async_smem();
-      __syncthreads();
-      if (threadIdx.x == 0 && ok) issue(qb + (unsigned long long)NS);
+      qb += z1 - z0 + 4;
     }
     if (!ok) {
       // give up: raise the error word, then let this CTA's copies in flight land
-      if (threadIdx.x == 0) {
+      if (t == 0) {
         atomicOr(c.B.err, 1);
         for (; waited < iq; ++waited)
-          if (!mbar_wait(bar0 + 8 * (unsigned)(waited % NS), (unsigned)((waited / NS) & 1ull))) break;
+          if (!mbar_wait(bar0 + 8 * (waited & (SW_NS - 1)), (unsigned)((waited / SW_NS) & 1))) break;
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0)
-      for (int s = 0; s < NS; ++s) mbar_inval(bar0 + 8 * s);
+    if (t == 0)
+      for (int s = 0; s < SW_NS; ++s) mbar_inval(bar0 + 8 * s);
   }
   __syncthreads();
   if (threadIdx.x == 0) {  // the new iterate is in alt: swap the buffers of this CTA's view
     for (int p = 0; p < 2; ++p) {
-      T* t = o.x[p];
+      T* tmp = o.x[p];
       o.x[p] = sw.alt[p];
-      sw.alt[p] = t;
+      sw.alt[p] = tmp;
     }
     sw.par ^= 1;
   }

@@ -89,7 +89,8 @@ EXPORTS = ["eb_status_str", "eb_last_error", "eb_geom_build", "eb_geom_query", "
            "eb_poisson_solve", "eb_field_eval", "eb_poisson_profile", "eb_poisson_trace",
            "eb_poisson_residual_noalloc", "eb_poisson_solve_batched", "eb_server_opts_default", "eb_server_create",
            "eb_server_submit", "eb_server_poll", "eb_server_wait", "eb_server_query", "eb_server_destroy",
-           "eb_amr_setup", "eb_amr_query", "eb_amr_residual", "eb_amr_solve", "eb_amr_destroy"]
+           "eb_amr_setup", "eb_amr_query", "eb_amr_residual", "eb_amr_solve", "eb_amr_kernel_stats",
+           "eb_amr_destroy"]
 
 
 def lib_path() -> str:
@@ -148,6 +149,8 @@ def load(build_if_missing: bool = False):
         lib.eb_amr_solve.restype = C.c_int
         lib.eb_amr_solve.argtypes = [P] + [P] * 6 + [C.POINTER(SolveInfo), P]
         lib.eb_amr_destroy.argtypes = [P]
+        lib.eb_amr_kernel_stats.restype = C.c_int
+        lib.eb_amr_kernel_stats.argtypes = [P, C.POINTER(C.c_double)]
         lib.eb_server_opts_default.argtypes = [C.POINTER(ServerOpts)]
         lib.eb_server_create.restype = C.c_int
         lib.eb_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(P)]
@@ -572,6 +575,14 @@ class Composite:
         if st not in (EB_OK, EB_ERR_NOT_CONVERGED):
             _check(st, "eb_amr_solve")
         return pc, pf, _info_dict(info)
+
+    def kernel_stats(self):
+        """Persistent multigrid launches of the last solve: {"coarse": ..., "fine": ...}, each with
+        launches, kernel_ms, vcycles, outer."""
+        out = (C.c_double * 8)()
+        _check(load().eb_amr_kernel_stats(self._h, out), "eb_amr_kernel_stats")
+        keys = ("launches", "kernel_ms", "vcycles", "outer")
+        return {w: {k: out[4 * i + j] for j, k in enumerate(keys)} for i, w in enumerate(("coarse", "fine"))}
 
     def close(self):
         if getattr(self, "_h", None):

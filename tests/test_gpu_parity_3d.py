@@ -137,7 +137,7 @@ def test_pin_plane_128_solution_satisfies_oracle_system():
 @pytest.mark.parametrize("case", CASES[:2], ids=IDS[:2])
 def test_solve_parity_3d_tile_streamed_sweeps(case, oracles, monkeypatch):
     """The 32^3 cases with the finest level relaxed by tile-streamed sweeps
-    (TMA-staged, both colours per pass; the default applies them from 64^3):
+    (TMA-staged, both colours per pass; the default applies them from 128^3):
     the FP32 V-cycles in FP64 defect correction still reach the oracle's
     solution."""
     monkeypatch.setenv("EBP_SWEEP_MIN_CELLS", "1")
