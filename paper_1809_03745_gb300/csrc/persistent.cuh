@@ -1091,7 +1091,13 @@ __device__ bool vcycle_dev(const Hier<T>& H, const Op<T>* lop, const Ctx& G) {
       ph_rows(o, 0, 2 * o.nirr, 1, G);
       if (!G.sync((l << 4) | 5)) return false;
     }
-    ph_restrict(o, H.op[l + 1], G);
+    if (H.sw[l].on && G.gsize >= 2 && o.n[0] == 2 * H.op[l + 1].n[0] && o.n[1] == 2 * H.op[l + 1].n[1] &&
+        o.n[2] == 2 * H.op[l + 1].n[2]) {
+      extern __shared__ __align__(128) unsigned char rs_dyn[];
+      if (!ph_restrict3d(H, l, G, rs_dyn)) return false;
+    } else {
+      ph_restrict(o, H.op[l + 1], G);
+    }
     if (!G.sync((l << 4) | 6)) return false;
   }
   if (H.gbot) {
@@ -1603,6 +1609,23 @@ __global__ void __launch_bounds__(PT, 1) k_sweep_phase(const Hier<T>* __restrict
   c.gcta = (int)blockIdx.x;
   c.B.err = err;
   ph_sweep3d(H, l, c, dyn);
+}
+
+// the streamed residual + restriction of level l on its own (cut-cell
+// residual rows as left in tmp), in the persistent kernel's grid shape
+template <class T>
+__global__ void __launch_bounds__(PT, 1) k_restrict3d_phase(const Hier<T>* __restrict__ Hg, int l, int* err) {
+  __shared__ Hier<T> H;
+  extern __shared__ __align__(128) unsigned char dyn[];
+  const int* src = (const int*)Hg;
+  int* dst = (int*)&H;
+  for (int i = threadIdx.x; i < (int)(sizeof(Hier<T>) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  Ctx c{};
+  c.gsize = (int)gridDim.x;
+  c.gcta = (int)blockIdx.x;
+  c.B.err = err;
+  ph_restrict3d(H, l, c, dyn);
 }
 
 template <class T>

@@ -794,6 +794,9 @@ static eb_status setup_persistent(eb_poisson* P) {
   }
   if (e == cudaSuccess && P->sweep_levels)
     e = cudaFuncSetAttribute((const void*)k_sweep_phase<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  if (e == cudaSuccess && P->sweep_levels)
+    e = cudaFuncSetAttribute((const void*)k_restrict3d_phase<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smax);
   if (e == cudaSuccess)
     e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<float>, PT, P->smem_bytes)
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<double>, PT, P->smem_bytes);
@@ -1461,9 +1464,10 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
     }
     return EB_OK;
   }
-  if (P && kernel == 4 && reps >= 1 && ms && bytes) {
-    // one tile-streamed sweep (both colours) of the finest level on its own
-    if (!P->persistent || P->o.precision != EB_PREC_MIXED || P->sweep_first != 0) {
+  if (P && (kernel == 4 || kernel == 5) && reps >= 1 && ms && bytes) {
+    // kernel 4: one tile-streamed sweep (both colours) of the finest level on
+    // its own; kernel 5: the streamed residual + restriction of that level
+    if (!P->persistent || P->o.precision != EB_PREC_MIXED || P->sweep_first != 0 || P->nlev < 2) {
       set_error("the finest level has no tile-streamed sweep");
       return EB_ERR_UNSUPPORTED;
     }
@@ -1475,9 +1479,13 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    k_sweep_phase<float><<<P->grid, PT, dyn, s>>>(H, 0, err);
+    auto go = [&]() {
+      if (kernel == 4) k_sweep_phase<float><<<P->grid, PT, dyn, s>>>(H, 0, err);
+      else k_restrict3d_phase<float><<<P->grid, PT, dyn, s>>>(H, 0, err);
+    };
+    go();
     cudaEventRecord(e0, s);
-    for (int i = 0; i < reps; ++i) k_sweep_phase<float><<<P->grid, PT, dyn, s>>>(H, 0, err);
+    for (int i = 0; i < reps; ++i) go();
     cudaEventRecord(e1, s);
     cudaError_t e = cudaEventSynchronize(e1);
     float t = 0.0f;
@@ -1492,8 +1500,9 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
       return EB_ERR_TIMEOUT;
     }
     *ms = (double)t / reps;
-    // read x and b, write x (4 bytes each), read the flag byte, per cell
-    *bytes = (double)P->G->L[0].g.ncell * 13.0;
+    // sweep: read x and b, write x (4 bytes each), read the flag byte, per cell;
+    // restriction: read x and b, the flag byte, write coarse b and x (8 / 8 bytes)
+    *bytes = (double)P->G->L[0].g.ncell * (kernel == 4 ? 13.0 : 10.0);
     return EB_OK;
   }
   if (!P || reps < 1 || (kernel != 0 && kernel != 1) || !ms || !bytes) {
