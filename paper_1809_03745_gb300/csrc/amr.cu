@@ -41,10 +41,16 @@ struct BoxIdx {
   int nc[3], nf[3], lo[3], hi[3];
 };
 
+// cell indices of linear index c (grids of fewer than 2^32 cells: 32-bit
+// divisions, several times cheaper than 64-bit ones in these memory-bound
+// passes over every coarse cell)
 __device__ __forceinline__ void ijk3(const int n[3], long long c, int I[3]) {
-  I[0] = (int)(c % n[0]);
-  I[1] = (int)((c / n[0]) % n[1]);
-  I[2] = (int)(c / ((long long)n[0] * n[1]));
+  const unsigned cu = (unsigned)c, n0 = (unsigned)n[0], n1 = (unsigned)n[1];
+  const unsigned r = cu / n0;
+  I[0] = (int)(cu - r * n0);
+  const unsigned k = r / n1;
+  I[1] = (int)(r - k * n1);
+  I[2] = (int)k;
 }
 __device__ __forceinline__ long long lin3(const int n[3], const int I[3]) {
   return (long long)I[0] + (long long)n[0] * ((long long)I[1] + (long long)n[1] * I[2]);
@@ -223,6 +229,65 @@ __global__ void k_cv_dot(BoxIdx B, const uint8_t* flags, long long n, int coarse
   }
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
+// Dot products of w with m vectors at once (m <= CV_MAXV): per block the m
+// partial sums, part[i * gridDim.x + block]; the caller adds the blocks in
+// order (deterministic).  Coarse entries under the box are skipped.
+constexpr int CV_MAXV = 14;
+struct CVPtrs {
+  const double* v[CV_MAXV];
+  double a[CV_MAXV];
+};
+__global__ void k_cv_mdot(BoxIdx B, const uint8_t* flags, long long n, int coarse, int m, CVPtrs V, const double* w,
+                          double* part) {
+  __shared__ double sh[CV_MAXV][TBA / 32];
+  double acc[CV_MAXV];
+#pragma unroll
+  for (int i = 0; i < CV_MAXV; ++i) acc[i] = 0.0;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    if (coarse) {
+      int I[3];
+      ijk3(B.nc, c, I);
+      if (under_box(B, I)) continue;
+    }
+    const unsigned f = flags[c];
+    for (int p = 0; p < 2; ++p) {
+      if (!((f >> p) & 1u)) continue;
+      const double wv = w[p * n + c];
+#pragma unroll
+      for (int i = 0; i < CV_MAXV; ++i)
+        if (i < m) acc[i] += V.v[i][p * n + c] * wv;
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < CV_MAXV; ++i) {
+    double a = acc[i];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[i][wid] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < m) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[threadIdx.x][k];
+    part[threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+}
+// w -= sum_i a_i v_i on the entries with an unknown (others 0)
+__global__ void k_cv_maxpy(const uint8_t* flags, long long n, int m, CVPtrs V, double* w) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const unsigned f = flags[c];
+  for (int p = 0; p < 2; ++p) {
+    if (!((f >> p) & 1u)) {
+      w[p * n + c] = 0.0;
+      continue;
+    }
+    double t = w[p * n + c];
+    for (int i = 0; i < m; ++i) t -= V.a[i] * V.v[i][p * n + c];
+    w[p * n + c] = t;
+  }
+}
+
 // y = a x + b y on the entries with an unknown
 __global__ void k_cv_axpby(const uint8_t* flags, long long n, double a, const double* x, double b, double* y) {
   long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -269,6 +334,7 @@ struct eb_amr {
   double* d_part = nullptr;
   std::vector<void*> allocs;
   long long bytes = 0;
+  double *bc0 = nullptr, *bf0 = nullptr;  // b of the coarse and fine operators for the current data
   // persistent solve launches of the last composite solve, coarse [0] and
   // fine [1] correction solvers: launches, kernel ms, V-cycles, FP64 outer iterations
   double kstat[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
@@ -366,6 +432,10 @@ extern "C" eb_status eb_amr_setup(const eb_geom_desc* desc, const int box_lo[3],
   if (st != EB_OK) return amr_fail(A, st);
   A->ncc = A->Gc->L[0].g.ncell;
   A->nff = A->Gf->L[0].g.ncell;
+  if (A->ncc >= (1LL << 32) || A->nff >= (1LL << 32)) {  // the composite kernels index cells in 32 bits
+    set_error("composite grids are limited to 2^32 cells per level");
+    return amr_fail(A, EB_ERR_INVALID);
+  }
   A->hc = desc->h;
   A->hf = desc->h / 2.0;
   A->eps0 = desc->eps_gas;
@@ -408,6 +478,8 @@ extern "C" eb_status eb_amr_setup(const eb_geom_desc* desc, const int box_lo[3],
   A->kf = (double*)alloc(sizeof(double) * 2 * A->nff);
   A->pcf = (double*)alloc(sizeof(double) * 2 * A->ncc);
   A->rc = (double*)alloc(sizeof(double) * 2 * A->ncc);
+  A->bc0 = (double*)alloc(sizeof(double) * 2 * A->ncc);
+  A->bf0 = (double*)alloc(sizeof(double) * 2 * A->nff);
   A->ec = (double*)alloc(sizeof(double) * 2 * A->ncc);
   A->rf = (double*)alloc(sizeof(double) * 2 * A->nff);
   A->ef = (double*)alloc(sizeof(double) * 2 * A->nff);
@@ -451,13 +523,20 @@ extern "C" eb_status eb_amr_query(const eb_amr* A, long long* n_coarse, long lon
 }
 
 // composite residual into A->rc / A->rf (phi_c values under the box are replaced by fine means)
-static eb_status amr_resid(eb_amr* A, const double* rhs_c, const double* sig_c, const double* rhs_f,
-                           const double* sig_f, const double* phi_c, const double* phi_f, cudaStream_t s) {
+// b of both operators for the given data, into A->bc0 / A->bf0
+static eb_status amr_rhs(eb_amr* A, const double* rhs_c, const double* sig_c, const double* rhs_f,
+                         const double* sig_f, cudaStream_t s) {
+  eb_status st = poisson_rhs(A->Pc, rhs_c, sig_c, A->bc0, s);
+  if (st == EB_OK) st = poisson_rhs(A->Pf, rhs_f, sig_f, A->bf0, s);
+  return st;
+}
+
+static eb_status amr_resid(eb_amr* A, const double* phi_c, const double* phi_f, cudaStream_t s) {
   cudaMemcpyAsync(A->pcf, phi_c, 2 * A->ncc * sizeof(double), cudaMemcpyDeviceToDevice, s);
   k_avg_down<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->cflags, A->fflags, A->kf, phi_f, A->pcf, A->ncc, A->nff);
   note_launch();
-  eb_status st = eb_poisson_residual(A->Pc, rhs_c, sig_c, A->pcf, A->rc, s);
-  if (st == EB_OK) st = eb_poisson_residual(A->Pf, rhs_f, sig_f, phi_f, A->rf, s);
+  eb_status st = poisson_residual_view(A->Pc, A->bc0, A->pcf, A->rc, s);
+  if (st == EB_OK) st = poisson_residual_view(A->Pf, A->bf0, phi_f, A->rf, s);
   if (st != EB_OK) return st;
   if (A->nface) {
     k_cf_flux<<<nb(A->nface), TBA, 0, s>>>(A->faces, A->nface, A->pcf, phi_f, A->eps0, A->hf, A->fl);
@@ -499,7 +578,8 @@ extern "C" eb_status eb_amr_residual(eb_amr* A, const double* d_rhs_c, const dou
     return EB_ERR_INVALID;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  eb_status st = amr_resid(A, d_rhs_c, d_sig_c, d_rhs_f, d_sig_f, d_phi_c, d_phi_f, s);
+  eb_status st = amr_rhs(A, d_rhs_c, d_sig_c, d_rhs_f, d_sig_f, s);
+  if (st == EB_OK) st = amr_resid(A, d_phi_c, d_phi_f, s);
   if (st != EB_OK) return st;
   cudaMemcpyAsync(d_r_c, A->rc, 2 * A->ncc * sizeof(double), cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(d_r_f, A->rf, 2 * A->nff * sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -526,6 +606,41 @@ static void cv_axpby(eb_amr* A, double a, const CVec& x, double b, const CVec& y
   note_launch();
 }
 
+// h[i] = (V[i], w) for i < m, both grids, one launch per grid and one sync
+static void cv_mdot(eb_amr* A, int m, const CVec& w, double* h, cudaStream_t s) {
+  CVPtrs pc{}, pf{};
+  for (int i = 0; i < m; ++i) {
+    pc.v[i] = A->V[i].c;
+    pf.v[i] = A->V[i].f;
+  }
+  k_cv_mdot<<<DOT_BLOCKS, TBA, 0, s>>>(A->B, A->cflags, A->ncc, 1, m, pc, w.c, A->d_part);
+  note_launch();
+  k_cv_mdot<<<DOT_BLOCKS, TBA, 0, s>>>(A->B, A->fflags, A->nff, 0, m, pf, w.f, A->d_part + CV_MAXV * DOT_BLOCKS);
+  note_launch();
+  std::vector<double> hp(2 * CV_MAXV * DOT_BLOCKS);
+  cudaMemcpyAsync(hp.data(), A->d_part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  for (int i = 0; i < m; ++i) {
+    double t = 0.0;
+    for (int b = 0; b < DOT_BLOCKS; ++b) t += hp[i * DOT_BLOCKS + b];
+    for (int b = 0; b < DOT_BLOCKS; ++b) t += hp[CV_MAXV * DOT_BLOCKS + i * DOT_BLOCKS + b];
+    h[i] = t;
+  }
+}
+// w -= sum_{i < m} h[i] V[i]
+static void cv_maxpy(eb_amr* A, int m, const double* h, const CVec& w, cudaStream_t s) {
+  CVPtrs pc{}, pf{};
+  for (int i = 0; i < m; ++i) {
+    pc.v[i] = A->V[i].c;
+    pf.v[i] = A->V[i].f;
+    pc.a[i] = pf.a[i] = h[i];
+  }
+  k_cv_maxpy<<<nb(A->ncc), TBA, 0, s>>>(A->cflags, A->ncc, m, pc, w.c);
+  note_launch();
+  k_cv_maxpy<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, m, pf, w.f);
+  note_launch();
+}
+
 // accuracy asked of the two multigrid corrections inside one FAC step: loose
 // enough that each stops after its first V-cycle
 constexpr double FAC_TOL = 3e-1;
@@ -533,8 +648,7 @@ constexpr double FAC_TOL = 3e-1;
 // z = M^-1 v: one FAC step from zero (coarse correction over the domain,
 // constant per parent on the box, then a fine correction of what remains);
 // uses A->rc / rf / ec / ef / tmp as scratch.
-static eb_status fac_apply(eb_amr* A, const CVec& v, const CVec& z, const double* rhs_c, const double* sig_c,
-                           const double* rhs_f, const double* sig_f, int* cycles, cudaStream_t s) {
+static eb_status fac_apply(eb_amr* A, const CVec& v, const CVec& z, int* cycles, cudaStream_t s) {
   const double tol = FAC_TOL;
   cudaMemcpyAsync(A->rc, v.c, 2 * A->ncc * sizeof(double), cudaMemcpyDeviceToDevice, s);
   k_zero_under<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->rc, A->ncc);
@@ -554,7 +668,7 @@ static eb_status fac_apply(eb_amr* A, const CVec& v, const CVec& z, const double
   k_prolong_const<<<nb(A->nff), TBA, 0, s>>>(A->B, A->fflags, A->ec, z.f, A->ncc, A->nff);
   note_launch();
   // what remains on the box: v_f - (A z)_f = v_f - b_f + r_f(z)
-  st = amr_resid(A, rhs_c, sig_c, rhs_f, sig_f, z.c, z.f, s);
+  st = amr_resid(A, z.c, z.f, s);
   if (st != EB_OK) return st;
   k_cv_sub<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, A->bvec.f, A->rf, A->tmp.f);  // (A z)_f
   note_launch();
@@ -570,9 +684,8 @@ static eb_status fac_apply(eb_amr* A, const CVec& v, const CVec& z, const double
 }
 
 // w = A z (homogeneous operator) = b - r(z)
-static eb_status op_apply(eb_amr* A, const CVec& z, const CVec& w, const double* rhs_c, const double* sig_c,
-                          const double* rhs_f, const double* sig_f, cudaStream_t s) {
-  eb_status st = amr_resid(A, rhs_c, sig_c, rhs_f, sig_f, z.c, z.f, s);
+static eb_status op_apply(eb_amr* A, const CVec& z, const CVec& w, cudaStream_t s) {
+  eb_status st = amr_resid(A, z.c, z.f, s);
   if (st != EB_OK) return st;
   k_cv_sub<<<nb(A->ncc), TBA, 0, s>>>(A->cflags, A->ncc, A->bvec.c, A->rc, w.c);
   note_launch();
@@ -598,7 +711,7 @@ static eb_status amr_workspace(eb_amr* A) {
   for (int i = 0; i < GM; ++i) A->Z.push_back(vec());
   A->bvec = vec();
   A->tmp = vec();
-  A->d_part = (double*)dev_alloc(A->allocs, 2 * DOT_BLOCKS * sizeof(double), &A->bytes, &st);
+  A->d_part = (double*)dev_alloc(A->allocs, 2 * CV_MAXV * DOT_BLOCKS * sizeof(double), &A->bytes, &st);
   if (st != EB_OK) {
     A->V.clear();
     A->Z.clear();
@@ -623,7 +736,8 @@ extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double
   // b: the composite residual at phi = 0
   cudaMemsetAsync(A->ec, 0, 2 * A->ncc * sizeof(double), s);
   cudaMemsetAsync(A->ef, 0, 2 * A->nff * sizeof(double), s);
-  st = amr_resid(A, d_rhs_c, d_sig_c, d_rhs_f, d_sig_f, A->ec, A->ef, s);
+  st = amr_rhs(A, d_rhs_c, d_sig_c, d_rhs_f, d_sig_f, s);
+  if (st == EB_OK) st = amr_resid(A, A->ec, A->ef, s);
   double bn = 0.0, r = 0.0;
   if (st == EB_OK) st = amr_norm(A, s, &bn);
   if (st != EB_OK) return st;
@@ -636,7 +750,7 @@ extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double
   // multigrid as the inner solver of every correction)
   st = EB_ERR_NOT_CONVERGED;
   while (it < max_it) {
-    eb_status s2 = amr_resid(A, d_rhs_c, d_sig_c, d_rhs_f, d_sig_f, x.c, x.f, s);
+    eb_status s2 = amr_resid(A, x.c, x.f, s);
     if (s2 == EB_OK) s2 = amr_norm(A, s, &r);
     if (s2 != EB_OK) {
       st = s2;
@@ -667,12 +781,16 @@ extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double
     g[0] = beta;
     int k = 0;
     for (; k < GM && it < max_it; ++k, ++it) {
-      s2 = fac_apply(A, A->V[k], A->Z[k], d_rhs_c, d_sig_c, d_rhs_f, d_sig_f, &cycles, s);
-      if (s2 == EB_OK) s2 = op_apply(A, A->Z[k], A->V[k + 1], d_rhs_c, d_sig_c, d_rhs_f, d_sig_f, s);
+      s2 = fac_apply(A, A->V[k], A->Z[k], &cycles, s);
+      if (s2 == EB_OK) s2 = op_apply(A, A->Z[k], A->V[k + 1], s);
       if (s2 != EB_OK) break;
-      for (int i = 0; i <= k; ++i) {  // modified Gram-Schmidt
-        H[i][k] = cv_dot(A, A->V[k + 1], A->V[i], s);
-        cv_axpby(A, -H[i][k], A->V[i], 1.0, A->V[k + 1], s);
+      // classical Gram-Schmidt twice: all k + 1 projections in one pass, twice
+      for (int i = 0; i <= k; ++i) H[i][k] = 0.0;
+      for (int pass = 0; pass < 2; ++pass) {
+        double hp[CV_MAXV];
+        cv_mdot(A, k + 1, A->V[k + 1], hp, s);
+        cv_maxpy(A, k + 1, hp, A->V[k + 1], s);
+        for (int i = 0; i <= k; ++i) H[i][k] += hp[i];
       }
       H[k + 1][k] = std::sqrt(cv_dot(A, A->V[k + 1], A->V[k + 1], s));
       if (H[k + 1][k] > 0.0) cv_axpby(A, 0.0, A->V[k + 1], 1.0 / H[k + 1][k], A->V[k + 1], s);

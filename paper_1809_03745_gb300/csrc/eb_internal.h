@@ -128,3 +128,5 @@ eb_status batch_copy_out(eb_poisson* P, double* phi, cudaStream_t s);
 long long poisson_device_bytes(const eb_poisson* P);
 eb_status poisson_solve_b(eb_poisson* P, const double* d_b, double* d_x, double tol, int* cycles, cudaStream_t user,
                           int* outer = nullptr, double* kernel_ms = nullptr);
+eb_status poisson_rhs(eb_poisson* P, const double* d_rhs, const double* d_sigma, double* d_b, cudaStream_t s);
+eb_status poisson_residual_view(eb_poisson* P, const double* d_b, const double* d_phi, double* d_r, cudaStream_t s);

@@ -992,6 +992,32 @@ __global__ void k_resid_field(Op<double> o, double* r) {
   for (int p = 0; p < 2; ++p) r[p * o.ncell + c] = ((f >> p) & 1) ? cell_residual(o, c, p, I) : 0.0;
 }
 
+// b (FP64 [2][n_cells]) of the finest level for the given data: kappa rhs
+// plus the boundary and surface-charge terms; enqueued on s, no sync.
+eb_status poisson_rhs(eb_poisson* P, const double* d_rhs, const double* d_sigma, double* d_b, cudaStream_t s) {
+  cudaMemsetAsync(P->d_norm + 1, 0, sizeof(unsigned long long), s);
+  return launch_rhs64(P->G, d_rhs, d_sigma, d_b, (double*)(P->d_norm + 1), s);
+}
+
+// r = b - A phi on the finest level for a b formed by poisson_rhs; phi is
+// read as given (its entries without an unknown must be finite), the sparse
+// rows use the handle's row scratch; enqueued on s, no sync.
+eb_status poisson_residual_view(eb_poisson* P, const double* d_b, const double* d_phi, double* d_r, cudaStream_t s) {
+  Op<double> o = P->op64[0];
+  const long long n = o.ncell;
+  o.x[0] = const_cast<double*>(d_phi);
+  o.b[0] = const_cast<double*>(d_b);
+  if (o.x[1]) {
+    o.x[1] = const_cast<double*>(d_phi) + n;
+    o.b[1] = const_cast<double*>(d_b) + n;
+  }
+  if (o.nirr) k_rows<double><<<blocks(2 * o.nirr), 256, 0, s>>>(o, 0, 2 * o.nirr, 1);
+  k_resid_field<<<blocks(n), 256, 0, s>>>(o, d_r);
+  counted(o.nirr ? 2 : 1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? EB_OK : cuda_fail(e, "residual");
+}
+
 extern "C" eb_status eb_poisson_residual(eb_poisson* P, const double* d_rhs, const double* d_sigma,
                                          const double* d_phi, double* d_r, void* stream) {
   if (!P || !d_rhs || !d_phi || !d_r) {

@@ -64,3 +64,44 @@ def test_two_ranks_gloo_job_time_and_shards():
         assert ms == 15.0  # the slowest rank's time
         assert thr == pytest.approx(2 * 1000 / 0.015)
         assert sorted(objs[0] + objs[1]) == list(range(10)) and not set(objs[0]) & set(objs[1])
+
+
+def _runner_worker(rank, world, port, q):
+    import torch.distributed as dist
+
+    from paper_1809_03745_gb300 import batch_runner as R
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        q.put((rank, R.run(count=12, solve=False, max_cells=50000)))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.timeout(120)
+def test_batch_runner_ranks_receive_and_report_their_shards():
+    """The sharded batched runner on two gloo ranks (planning and reporting;
+    the solves themselves need the GPU): every rank gets the shard that
+    shard() gives it, the reports gathered on each rank cover all instances
+    exactly once, and the job's cells are their sum."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_runner_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=100) for _ in range(2))
+    for p in procs:
+        p.join(timeout=30)
+        assert p.exitcode == 0
+    inst = W.batched_instances(count=12, max_cells=50000)
+    parts = S.shard([float(W.ncells(d)) for d, _, _ in inst], 2)
+    for rank in (0, 1):
+        out = res[rank]
+        assert out["world"] == 2
+        reps = {r["rank"]: r for r in out["reports"]}
+        assert reps[0]["instances"] == parts[0] and reps[1]["instances"] == parts[1]
+        assert sorted(reps[0]["instances"] + reps[1]["instances"]) == list(range(12))
+        assert out["cells"] == sum(W.ncells(d) for d, _, _ in inst)
+        assert reps[rank]["cells"] == sum(W.ncells(inst[i][0]) for i in parts[rank])
