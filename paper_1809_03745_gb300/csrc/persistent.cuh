@@ -16,26 +16,25 @@ constexpr int MAXLEV = 16;
 constexpr int PT = 512;                          // threads per CTA of the persistent kernel
 constexpr long long BAR_WAIT_CYCLES = 4000000000LL;  // ~2 s of SM clock: a barrier wait gives up after this
 
-// Tile-streamed sweep of large 3D levels (sweep3d.cuh): tiles of SW_TX x ty
-// cells, boxes with a halo of SW_HX cells in x (16 bytes of 4-byte data, the
-// TMA alignment of the x coordinate), SW_HY in y, flags boxes SW_FBX bytes
-// wide from SW_FHX cells left of the tile (16-byte alignment of bytes).
-constexpr int SW_TX = 32, SW_HX = 4, SW_BX = SW_TX + 2 * SW_HX, SW_HY = 2, SW_FHX = 16, SW_FBX = 64;
-constexpr int SW_NS = 8;          // ring slots: four planes in use, four in flight
-constexpr int SW_NS_MAX = 16;     // ring slots the shared-memory head has room for
-constexpr int SW_MASK_MAX = 256;  // words of the per-item dielectric mask (8192 tiles x chunks)
-constexpr int SW_HEAD = ((8 * SW_NS_MAX + 4 * SW_MASK_MAX + 4 * SW_NS_MAX + 127) / 128) * 128;
+// Tile-streamed passes over large 3D levels (sweep3d.cuh): tiles of SW_TX x
+// SW_TY cells, boxes with a halo of SW_HX cells in x (16 bytes of 4-byte
+// data, the TMA alignment of the x coordinate) and SW_HY in y, flag boxes
+// SW_FBX bytes wide from SW_FHX cells left of the tile (16-byte alignment of
+// bytes); two planes per copy, a ring of SW_NS two-plane slots.
+constexpr int SW_TX = 32, SW_TY = 32, SW_HX = 4, SW_BX = SW_TX + 2 * SW_HX, SW_HY = 2, SW_FHX = 16, SW_FBX = 64;
+constexpr int SW_NS = 4, SW_NS_LOG = 2;
+constexpr int SW_HEAD = 128;  // mbarriers and a failure flag before the ring
 
 template <class T>
 struct SweepLev {
-  int on;       // 1: the level relaxes by tile-streamed sweeps, x -> alt
-  int ty;       // tile rows (16 or 32)
-  int zc;       // planes per z-chunk
-  int ntx, nty, nzc, nitems;  // tiles per axis, z-chunks, work items (tile x chunk)
+  int on;       // 1: the level relaxes and restricts by tile-streamed passes, x -> alt
+  int zc;       // planes per z-chunk (a multiple of 4)
+  int ntx, nty, nzc, nitems;  // tiles per axis, z-chunks, gas-phase work items (tile x chunk)
+  int n1items;  // dielectric-phase work items: the items whose boxes hold dielectric unknowns
   int par;      // 0: x holds the iterate; 1: alt does (this CTA's copy, flipped per sweep)
   T* alt[2];    // the second buffer per phase
-  const void* maps;      // 7 tensor maps (128 bytes each): x[buf][phase] (buf 0 = x, 1 = alt), b[phase], flags
-  const unsigned* has1;  // bit per item: dielectric unknowns in the item's boxes
+  const void* maps;    // 7 tensor maps (128 bytes each): x[buf][phase] (buf 0 = x, 1 = alt), b[phase], flags
+  const int* list1;    // [n1items] item indices of the dielectric-phase items
 };
 
 template <class T>
@@ -58,7 +57,6 @@ struct Hier {
   // offsets of row_ptr, col, val, diag, irr_cell, irr_of_cell, and the entry count
   int srows[MAXLEV], off_rp[MAXLEV], off_col[MAXLEV], off_val[MAXLEV], off_dg[MAXLEV], off_ic[MAXLEV],
       off_io[MAXLEV], rnnz[MAXLEV];
-  int sw_ns;  // ring slots of the tile-streamed sweeps
   Op<T> op[MAXLEV];
   SweepLev<T> sw[MAXLEV];
 };
@@ -1317,23 +1315,34 @@ __global__ void __launch_bounds__(PT, 1) k_solve_batch(const BatchItem<T>* __res
   solve_group(it.H, it.F, it.ctl, it.B, (int)blockIdx.x - it.start, it.size);
 }
 
-// Setup of the tile-streamed sweep: bit `it` of has1 is set when the boxes
+// Setup of the tile-streamed passes: bit `it` of has1 is set when the boxes
 // item `it` loads (its tile with the halo, planes z0 - 2 .. z1 + 1) hold a
-// dielectric unknown; one CTA per item.
-__global__ void k_sweep_has1(const uint8_t* __restrict__ flags, int n0, int n1, int n2, int ntx, int nty, int ty,
-                             int zc, int nitems, unsigned* has1) {
+// dielectric unknown, or when the coarse cells it restricts onto do (cflags
+// of the level below, may be null); one CTA per item.
+__global__ void k_sweep_has1(const uint8_t* __restrict__ flags, int n0, int n1, int n2, int ntx, int nty, int zc,
+                             int nitems, const uint8_t* __restrict__ cflags, int cn0, int cn1, int cn2,
+                             unsigned* has1) {
   const int it = blockIdx.x;
   if (it >= nitems) return;
   const int tx = it % ntx, r = it / ntx;
-  const int x0 = tx * SW_TX, y0 = (r % nty) * ty, z0 = (r / nty) * zc, z1 = min(z0 + zc, n2);
+  const int x0 = tx * SW_TX, y0 = (r % nty) * SW_TY, z0 = (r / nty) * zc, z1 = min(z0 + zc, n2);
   const int xa = max(x0 - SW_HX, 0), xb = min(x0 + SW_TX + SW_HX, n0);
-  const int ya = max(y0 - SW_HY, 0), yb = min(y0 + ty + SW_HY, n1);
+  const int ya = max(y0 - SW_HY, 0), yb = min(y0 + SW_TY + SW_HY, n1);
   const int za = max(z0 - 2, 0), zb = min(z1 + 2, n2);
   const long long nx = xb - xa, ny = yb - ya, nz = zb - za;
   int found = 0;
   for (long long e = threadIdx.x; e < nx * ny * nz && !found; e += blockDim.x) {
     const long long x = xa + e % nx, y = ya + (e / nx) % ny, z = za + e / (nx * ny);
     if (flags[(z * n1 + y) * n0 + x] & 2) found = 1;
+  }
+  if (cflags) {
+    const int cxa = x0 / 2, cxb = min((x0 + SW_TX) / 2, cn0), cya = y0 / 2, cyb = min((y0 + SW_TY) / 2, cn1);
+    const int cza = z0 / 2, czb = min(z1 / 2, cn2);
+    const long long mx = max(cxb - cxa, 0), my = max(cyb - cya, 0), mz = max(czb - cza, 0);
+    for (long long e = threadIdx.x; e < mx * my * mz && !found; e += blockDim.x) {
+      const long long x = cxa + e % mx, y = cya + (e / mx) % my, z = cza + e / (mx * my);
+      if (cflags[(z * cn1 + y) * cn0 + x] & 2) found = 1;
+    }
   }
   if (__syncthreads_or(found) && threadIdx.x == 0) atomicOr(&has1[it >> 5], 1u << (it & 31));
 }

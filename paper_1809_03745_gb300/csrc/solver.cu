@@ -459,87 +459,71 @@ static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
   return fn;
 }
 
-// a 3D tensor map over one level array (x fastest), boxes of bx x by x 1
+// a 3D tensor map over one level array (x fastest), boxes of bx x by x bz
 static bool tmap3(CUtensorMap* m, CUtensorMapDataType type, int esize, const void* base, const int n[3], int bx,
-                  int by) {
+                  int by, int bz) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
   if (!enc) return false;
   cuuint64_t dim[3] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2]};
   cuuint64_t str[2] = {(cuuint64_t)n[0] * esize, (cuuint64_t)n[0] * n[1] * esize};
-  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
   cuuint32_t es[3] = {1, 1, 1};
   return enc(m, type, 3, const_cast<void*>(base), dim, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-static constexpr long long SW_MIN_CELLS = 1LL << 21;  // levels from 128^3 up stream their sweeps
+static constexpr long long SW_MIN_CELLS = 1LL << 21;  // levels from 128^3 up stream their passes
 
-// Tile rows and z-chunk of a level for `workers` CTAs: the least of
-// (rounds of items per CTA) x (planes per item) x (bytes of a plane's boxes
-// + a fixed cost per step), over ty in {16, 32} and chunks of 4..n2 planes.
-static void sweep_shape(const int n[3], int workers, int* ty_out, int* zc_out) {
-  double best = 1e300;
-  *ty_out = 32;
-  *zc_out = n[2];
-  for (int ty : {32, 16}) {
-    const long long ntx = (n[0] + SW_TX - 1) / SW_TX, nty = (n[1] + ty - 1) / ty;
-    for (int zc = 4; zc <= n[2]; zc += 4) {
-      const long long nzc = (n[2] + zc - 1) / zc, items = ntx * nty * nzc;
-      if (items > 32LL * SW_MASK_MAX) continue;
-      const long long rounds = (items + workers - 1) / workers;
-      const double plane = (double)SW_BX * (ty + 2 * SW_HY) * 9.6 + 2048.0;
-      const double cost = (double)rounds * (zc + 4) * plane;
-      if (cost < best * (1.0 - 1e-9)) {
-        best = cost;
-        *ty_out = ty;
-        *zc_out = zc;
-      }
+// z-chunk of a level for `workers` CTAs: the least of (rounds of items per
+// CTA) x (steps per item: two planes each, two more for the ends), over
+// chunks of 4..n2 planes in steps of 4.
+static int sweep_chunk(const int n[3], int workers) {
+  const long long ntx = (n[0] + SW_TX - 1) / SW_TX, nty = (n[1] + SW_TY - 1) / SW_TY;
+  long long best = -1;
+  int zc_best = 4;
+  for (int zc = 4; zc <= n[2] + 3; zc += 4) {
+    const long long nzc = (n[2] + zc - 1) / zc, items = ntx * nty * nzc;
+    const long long rounds = (items + workers - 1) / workers;
+    const long long cost = rounds * (zc / 2 + 2);
+    if (best < 0 || cost < best) {
+      best = cost;
+      zc_best = zc;
     }
   }
+  return zc_best;
 }
 
-// Marks the FP32 3D grid levels of at least SW_MIN_CELLS cells (x extent a
-// multiple of 16) for tile-streamed sweeps: a second x buffer per phase,
-// tensor maps of x, the second buffer, b and the flags, the per-item
-// dielectric mask.  Levels stay on the colour passes when any of it fails or
-// the shared memory cannot hold six ring slots.
+// Marks the FP32 3D grid levels of at least SW_MIN_CELLS cells (each extent
+// a multiple of 4, x a multiple of 16) for tile-streamed passes: a second x
+// buffer per phase, tensor maps of x, the second buffer, b and the flags with
+// two-plane boxes, and the list of items that hold dielectric unknowns.
+// Levels stay on the colour passes when any of it fails.
 template <class T>
 static eb_status setup_sweeps(eb_poisson* P, std::vector<Op<T>>& ops, Hier<T>& H, int smem_cap) {
   if (!std::is_same<T, float>::value) return EB_OK;
   if (const char* env = std::getenv("EBP_SWEEP"))
     if (std::atoi(env) == 0) return EB_OK;
+  if (SW_HEAD + 128 + SW_NS * SwSlot<T>::BYTES > smem_cap) return EB_OK;
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->G->device);
   const int workers = std::max(1, nsm - 1);
   long long min_cells = SW_MIN_CELLS;  // EBP_SWEEP_MIN_CELLS lowers it (tests run small grids through the path)
   if (const char* env = std::getenv("EBP_SWEEP_MIN_CELLS")) min_cells = std::max(1LL, std::atoll(env));
-  int slot_max = 0;
-  std::vector<int> cand;
-  for (int l = 0; l < H.lc; ++l) {
-    const Op<T>& o = ops[l];
-    if (o.D != 3 || o.ncell < min_cells || (o.n[0] % 16) != 0) continue;
-    int ty = 32, zc = 4;
-    sweep_shape(o.n, workers, &ty, &zc);
-    H.sw[l].ty = ty;
-    H.sw[l].zc = zc;
-    SweepSlot<T> L(ty, o.x[1] != nullptr);
-    slot_max = std::max(slot_max, L.bytes);
-    cand.push_back(l);
-  }
-  if (cand.empty()) return EB_OK;
-  if ((smem_cap - SW_HEAD - 128) / slot_max < SW_NS) return EB_OK;
   eb_status st = EB_OK;
-  for (int l : cand) {
+  for (int l = 0; l < H.lc; ++l) {
     Op<T>& o = ops[l];
+    if (o.D != 3 || o.ncell < min_cells || (o.n[0] % 16) || (o.n[1] % 4) || (o.n[2] % 4)) continue;
     SweepLev<T>& sw = H.sw[l];
     const DevLevel& Lv = P->G->L[l];
     const int two = o.x[1] != nullptr;
+    sw.zc = sweep_chunk(o.n, workers);
     sw.ntx = (o.n[0] + SW_TX - 1) / SW_TX;
-    sw.nty = (o.n[1] + sw.ty - 1) / sw.ty;
+    sw.nty = (o.n[1] + SW_TY - 1) / SW_TY;
     sw.nzc = (o.n[2] + sw.zc - 1) / sw.zc;
     sw.nitems = sw.ntx * sw.nty * sw.nzc;
-    if (sw.nitems > 32 * SW_MASK_MAX) continue;  // more items than the mask in shared memory holds
+    CUtensorMap maps[7];
+    std::memset(maps, 0, sizeof(maps));
     for (int p = 0; p < 2; ++p) {
       sw.alt[p] = nullptr;
       if (o.x[p]) {
@@ -547,39 +531,56 @@ static eb_status setup_sweeps(eb_poisson* P, std::vector<Op<T>>& ops, Hier<T>& H
         if (st == EB_OK) cudaMemsetAsync(sw.alt[p], 0, sizeof(T) * (size_t)o.ncell, P->s);
       }
     }
-    const int nw = (sw.nitems + 31) / 32;
-    unsigned* has1 = (unsigned*)dev_alloc(P->allocs, sizeof(unsigned) * nw, &P->bytes, &st);
     CUtensorMap* dmaps = (CUtensorMap*)dev_alloc(P->allocs, sizeof(CUtensorMap) * 7, &P->bytes, &st);
     if (st != EB_OK) return st;
-    CUtensorMap maps[7];
-    std::memset(maps, 0, sizeof(maps));
-    const int by = sw.ty + 2 * SW_HY;
+    const int by = SW_TY + 2 * SW_HY;
     const CUtensorMapDataType ft = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    bool ok = tmap3(&maps[0], ft, 4, o.x[0], o.n, SW_BX, by) && tmap3(&maps[2], ft, 4, sw.alt[0], o.n, SW_BX, by) &&
-              tmap3(&maps[4], ft, 4, o.b[0], o.n, SW_BX, by) &&
-              tmap3(&maps[6], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, Lv.flags, o.n, SW_FBX, by);
+    bool ok = tmap3(&maps[0], ft, 4, o.x[0], o.n, SW_BX, by, 2) && tmap3(&maps[2], ft, 4, sw.alt[0], o.n, SW_BX, by, 2) &&
+              tmap3(&maps[4], ft, 4, o.b[0], o.n, SW_BX, by, 2) &&
+              tmap3(&maps[6], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, Lv.flags, o.n, SW_FBX, by, 2);
     if (ok && two)
-      ok = tmap3(&maps[1], ft, 4, o.x[1], o.n, SW_BX, by) && tmap3(&maps[3], ft, 4, sw.alt[1], o.n, SW_BX, by) &&
-           tmap3(&maps[5], ft, 4, o.b[1], o.n, SW_BX, by);
+      ok = tmap3(&maps[1], ft, 4, o.x[1], o.n, SW_BX, by, 2) && tmap3(&maps[3], ft, 4, sw.alt[1], o.n, SW_BX, by, 2) &&
+           tmap3(&maps[5], ft, 4, o.b[1], o.n, SW_BX, by, 2);
     if (!ok) continue;  // this level keeps the colour passes
-    cudaMemsetAsync(has1, 0, sizeof(unsigned) * nw, P->s);
-    if (two)
-      k_sweep_has1<<<sw.nitems, 256, 0, P->s>>>(Lv.flags, o.n[0], o.n[1], o.n[2], sw.ntx, sw.nty, sw.ty, sw.zc,
-                                                sw.nitems, has1);
-    cudaError_t e = cudaMemcpyAsync(dmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, P->s);
+    // the items whose boxes (or coarse cells) hold dielectric unknowns
+    std::vector<int> list1;
+    if (two) {
+      const int nw = (sw.nitems + 31) / 32;
+      std::vector<void*> tmp;
+      unsigned* d_has1 = (unsigned*)dev_alloc(tmp, sizeof(unsigned) * nw, nullptr, &st);
+      if (st != EB_OK) return st;
+      cudaMemsetAsync(d_has1, 0, sizeof(unsigned) * nw, P->s);
+      const uint8_t* cfl = l + 1 < (int)P->G->L.size() ? P->G->L[l + 1].flags : nullptr;
+      const int* cn = l + 1 < (int)P->G->L.size() ? P->G->L[l + 1].g.n : o.n;
+      k_sweep_has1<<<sw.nitems, 256, 0, P->s>>>(Lv.flags, o.n[0], o.n[1], o.n[2], sw.ntx, sw.nty, sw.zc, sw.nitems,
+                                                cfl, cn[0], cn[1], cn[2], d_has1);
+      std::vector<unsigned> h(nw);
+      cudaError_t e = cudaMemcpyAsync(h.data(), d_has1, sizeof(unsigned) * nw, cudaMemcpyDeviceToHost, P->s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
+      for (void* q : tmp) cudaFree(q);
+      if (e != cudaSuccess) return cuda_fail(e, "sweep setup");
+      for (int it = 0; it < sw.nitems; ++it)
+        if ((h[it >> 5] >> (it & 31)) & 1u) list1.push_back(it);
+    }
+    int* dlist = (int*)dev_alloc(P->allocs, sizeof(int) * std::max<size_t>(list1.size(), 1), &P->bytes, &st);
+    if (st != EB_OK) return st;
+    cudaError_t e = cudaSuccess;
+    if (!list1.empty())
+      e = cudaMemcpyAsync(dlist, list1.data(), sizeof(int) * list1.size(), cudaMemcpyHostToDevice, P->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, P->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
     if (e != cudaSuccess) return cuda_fail(e, "sweep setup");
     sw.maps = dmaps;
-    sw.has1 = has1;
+    sw.list1 = dlist;
+    sw.n1items = (int)list1.size();
     sw.par = 0;
     sw.on = 1;
     ++P->sweep_levels;
     if (P->sweep_first < 0) P->sweep_first = l;
   }
   if (P->sweep_levels) {
-    H.sw_ns = SW_NS;
     P->sweep_ns = SW_NS;
-    P->sweep_bytes = SW_HEAD + 128 + SW_NS * slot_max;
+    P->sweep_bytes = SW_HEAD + 128 + SW_NS * SwSlot<T>::BYTES;
   }
   return EB_OK;
 }

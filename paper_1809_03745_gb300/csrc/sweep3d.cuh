@@ -5,18 +5,24 @@
 //
 // A classic colour pass reads the whole level and writes half of it, so a
 // sweep moves about twice the bytes the method needs.  Here a CTA owns an
-// x-y tile of 32 x TY cells and streams it along z through shared memory:
-// TMA (cp.async.bulk.tensor) brings in, per plane, the tile with a halo of
-// x, b and the cell flags, several planes ahead of use, each plane completing
-// an mbarrier.  At step zs the CTA relaxes the red regular cells of plane zs
-// on the tile plus a one-cell ring (reading black values of planes zs-1..zs+1,
-// not yet updated), then the black regular cells of plane zs-1 on the tile
-// (reading the new red values of planes zs-2..zs), then stores plane zs-1.
-// The ring's red values equal those the neighbouring tile computes, because
-// every read comes from the previous iterate: the sweep is out of place,
-// x -> alt, and the two buffers swap roles afterwards.  Cut cells (sparse
-// rows) are not touched here: their new values were written into x before
-// the sweep, so the regular cells already see them.
+// x-y tile of 32 x 32 cells of one phase and streams it along z through
+// shared memory: TMA (cp.async.bulk.tensor) brings in the tile with a halo
+// of x, b and the cell flags two planes per copy, a ring of four two-plane
+// slots, each copy completing an mbarrier.  Step s relaxes the red regular
+// cells of two planes on the tile plus a one-cell ring (reading black values
+// not yet updated), then, after one block barrier, the black regular cells
+// of the two planes below (reading the new red values), and stores the two
+// planes below those, final since the previous step.  The ring's red values
+// equal those the neighbouring tile computes, because every read comes from
+// the previous iterate: the sweep is out of place, x -> alt, and the two
+// buffers swap roles afterwards.  Cut cells (sparse rows) are not touched
+// here: their new values were written into x before the pass.  The regular
+// cells of the two phases couple only through cut cells, so the dielectric
+// phase streams in items of its own, only over the tiles that hold it.
+//
+// Moving two planes per step matters more than the ring depth: the pass is
+// bound by the fixed cost of a pipeline step (the wait, the barrier, the
+// copy issue), not by the bytes in flight.
 //
 // Every load and store stays inside the arrays: the TMA unit clips the boxes
 // to the tensor (zero fill outside), and stores are masked to the grid.
@@ -75,42 +81,32 @@ __device__ __forceinline__ void tma_load3(unsigned dst, const void* map, int x, 
       : "memory");
 }
 
-// byte offsets of one ring slot's buffers (x[0], x[1], b[0], b[1], flags),
-// each a multiple of 128 bytes
+// Byte layout of one ring slot: x of two planes [2][by][SW_BX], b likewise,
+// the flags [2][by][SW_FBX]; every part a multiple of 128 bytes.
 template <class T>
-struct SweepSlot {
-  int xb, fb, bytes;  // bytes of one x or b box, of the flags box, of the slot
-  __device__ __host__ SweepSlot(int ty, int two) {
-    const int by = ty + 2 * SW_HY;
-    xb = SW_BX * by * (int)sizeof(T);
-    fb = SW_FBX * by;
-    bytes = (two ? 4 : 2) * xb + fb;
-  }
+struct SwSlot {
+  static constexpr int BY = SW_TY + 2 * SW_HY;
+  static constexpr int XB = SW_BX * BY * (int)sizeof(T);  // one plane of x or b
+  static constexpr int FB = SW_FBX * BY;                  // one plane of flags
+  static constexpr int BYTES = 4 * XB + 2 * FB;
 };
 
-// The level's constants, held in registers for the streamed passes (the
-// hierarchy itself sits in shared memory, where every field read is a load).
+// The level's constants for one phase, held in registers for the streamed
+// passes (the hierarchy itself sits in shared memory, where every field
+// read is a load).
 template <class T>
 struct SwGrid {
   int n0, n1, n2;
-  unsigned bcm;          // bit s set: Dirichlet wall on side s (xlo, xhi, ylo, yhi, zlo, zhi)
-  T h2e0, h2e1, ceps0, ceps1;
-  int xb, fo, bo;        // bytes of an x/b box, offset of the flags box, of phase 0's b box
-  int slot;              // bytes of a ring slot
-  __device__ SwGrid(const Op<T>& o, const SweepSlot<T>& L, int two) {
+  unsigned bcm;  // bit s set: Dirichlet wall on side s (xlo, xhi, ylo, yhi, zlo, zhi)
+  T h2e, ceps;
+  __device__ SwGrid(const Op<T>& o, int p) {
     n0 = o.n[0];
     n1 = o.n[1];
     n2 = o.n[2];
     bcm = 0u;
     for (int q = 0; q < 6; ++q) bcm |= (o.bc[q] ? 1u : 0u) << q;
-    h2e0 = o.h2e[0];
-    h2e1 = o.h2e[1];
-    ceps0 = o.ceps[0];
-    ceps1 = o.ceps[1];
-    xb = L.xb;
-    fo = (two ? 4 : 2) * L.xb;
-    bo = (two ? 2 : 1) * L.xb;
-    slot = L.bytes;
+    h2e = o.h2e[p];
+    ceps = o.ceps[p];
   }
 };
 
@@ -168,168 +164,229 @@ __device__ __noinline__ void sw_wall_stencil(const SwGrid<T>& g, const T* Xm, co
   dg_out = dg;
 }
 
-// Relaxes cell (i, j, k) at box position (lx, ly) of the planes P0 (k), Pm
-// (k - 1), Pp (k + 1) when it is a regular cell of the level; kin: k is not
-// on a wall plane.  Cells off the grid, cut cells and cells without an
-// unknown are left alone.
+// Relaxes cell (i, j, k) at box position (lx, ly) of planes Xc (k), Xm, Xp
+// with right-hand side B and flags F when it is a regular cell of phase p
+// (flag value pbit = 1 << p); kin: k is not on a wall plane.  Cells off the
+// grid, cut cells and cells of the other phase or without an unknown are
+// left alone.
 template <class T>
-__device__ __forceinline__ void sw_relax(const SwGrid<T>& g, unsigned char* P0, const unsigned char* Pm,
-                                         const unsigned char* Pp, int i, int j, int k, bool kin, int lx, int ly) {
+__device__ __forceinline__ void sw_relax(const SwGrid<T>& g, T* Xc, const T* Xm, const T* Xp, const T* B,
+                                         const unsigned char* F, unsigned pbit, int i, int j, int k, bool kin, int lx,
+                                         int ly) {
   if ((unsigned)i >= (unsigned)g.n0 || (unsigned)j >= (unsigned)g.n1) return;
-  const unsigned f = P0[g.fo + ly * SW_FBX + lx + (SW_FHX - SW_HX)] & 7u;
-  if (f - 1u > 1u) return;  // regular: exactly one phase, no sparse row
-  const int po = f == 2u ? g.xb : 0;
-  T* Xc = (T*)(P0 + po);
-  const T* Xm = (const T*)(Pm + po);
-  const T* Xp = (const T*)(Pp + po);
+  if ((F[ly * SW_FBX + lx + (SW_FHX - SW_HX)] & 7u) != pbit) return;  // regular: one phase, no sparse row
   const int e = ly * SW_BX + lx;
-  const T bcell = ((const T*)(P0 + g.bo + po))[e];
-  const T h2e = f == 2u ? g.h2e1 : g.h2e0;
   if (kin && (unsigned)(i - 1) < (unsigned)(g.n0 - 2) && (unsigned)(j - 1) < (unsigned)(g.n1 - 2)) {
     const T sum = ((((Xc[e - 1] + Xc[e + 1]) + Xc[e - SW_BX]) + Xc[e + SW_BX]) + Xm[e]) + Xp[e];
-    Xc[e] = (h2e * bcell + sum) * inv_count(6, T(0));
+    Xc[e] = (g.h2e * B[e] + sum) * inv_count(6, T(0));
     return;
   }
   T sum;
   int dg;
   sw_wall_stencil(g, Xm, Xc, Xp, e, i, j, k, sum, dg);
-  Xc[e] = (h2e * bcell + sum) * inv_count(dg, T(0));
+  Xc[e] = (g.h2e * B[e] + sum) * inv_count(dg, T(0));
+}
+
+// Residual b - A x of the regular cell (i, j, k) at box position (lx, ly),
+// with the terms and order of cell_residual.
+template <class T>
+__device__ __forceinline__ T sw_resid(const SwGrid<T>& g, const T* Xc, const T* Xm, const T* Xp, const T* B, int i,
+                                      int j, int k, bool kin, int lx, int ly) {
+  const int e = ly * SW_BX + lx;
+  if (kin && (unsigned)(i - 1) < (unsigned)(g.n0 - 2) && (unsigned)(j - 1) < (unsigned)(g.n1 - 2)) {
+    const T sum = ((((Xc[e - 1] + Xc[e + 1]) + Xc[e - SW_BX]) + Xc[e + SW_BX]) + Xm[e]) + Xp[e];
+    return B[e] - g.ceps * ((T)6 * Xc[e] - sum);
+  }
+  T sum;
+  int dg;
+  sw_wall_stencil(g, Xm, Xc, Xp, e, i, j, k, sum, dg);
+  return B[e] - g.ceps * ((T)dg * Xc[e] - sum);
+}
+
+// The work items of a streamed pass over level l: item index r < nitems is
+// tile (r % ntx, (r / ntx) % nty) and z-chunk r / (ntx nty) in the gas phase;
+// r >= nitems is the item list1[r - nitems] in the dielectric phase.
+template <class T>
+struct SwItem {
+  int x0, y0, z0, z1, p;
+  __device__ void at(const SweepLev<T>& sw, int n2, int r) {
+    int it = r;
+    p = 0;
+    if (r >= sw.nitems) {
+      it = sw.list1[r - sw.nitems];
+      p = 1;
+    }
+    const int tx = it % sw.ntx, q = it / sw.ntx;
+    x0 = tx * SW_TX;
+    y0 = (q % sw.nty) * SW_TY;
+    z0 = (q / sw.nty) * sw.zc;
+    z1 = min(z0 + sw.zc, n2);
+  }
+};
+
+// The shared-memory head: SW_NS mbarriers, then a failure flag; the ring
+// starts at SW_HEAD, on a 128-byte boundary (the host adds 128 bytes of slack).
+__device__ __forceinline__ unsigned char* sw_ring(unsigned char* dyn) {
+  return dyn + SW_HEAD + ((128u - (smem_u32(dyn + SW_HEAD) & 127u)) & 127u);
+}
+
+// Issues the two-plane copies of a streamed pass in order (thread 0 only):
+// loads iq < limit, item by item, `groups(item)` copies each starting at
+// plane z0 - 2.  The cursor (item ik, copy ig within it) advances without
+// divisions; an item's geometry is computed when the cursor reaches it.
+template <class T>
+struct SwIssue {
+  int ik, ig, iq, K, ng;
+  SwItem<T> it;
+  const void *mx, *mb, *mf;
+  __device__ void start(const SweepLev<T>& sw, int n2, int w, int nw, int k_total, const unsigned char* maps,
+                        int lead) {
+    ik = 0;
+    ig = 0;
+    iq = 0;
+    K = k_total;
+    if (K > 0) load_item(sw, n2, w, nw, maps, lead);
+  }
+  __device__ void load_item(const SweepLev<T>& sw, int n2, int w, int nw, const unsigned char* maps, int lead) {
+    it.at(sw, n2, w + ik * nw);
+    ng = (it.z1 - it.z0 + 2 * lead) >> 1;
+    mx = maps + 128 * (2 * sw.par + it.p);
+    mb = maps + 128 * (4 + it.p);
+    mf = maps + 128 * 6;
+  }
+  __device__ void run(const SweepLev<T>& sw, int n2, int w, int nw, const unsigned char* maps, unsigned char* ring,
+                      unsigned bar0, int limit, int lead) {
+    using L = SwSlot<T>;
+    while (iq < limit && ik < K) {
+      const int s = iq & (SW_NS - 1);
+      const unsigned bar = bar0 + 8 * s;
+      const unsigned base = smem_u32(ring + s * L::BYTES);
+      const int z = it.z0 - lead + 2 * ig;
+      mbar_expect_tx(bar, (unsigned)L::BYTES);
+      tma_load3(base, mx, it.x0 - SW_HX, it.y0 - SW_HY, z, bar);
+      tma_load3(base + 2 * L::XB, mb, it.x0 - SW_HX, it.y0 - SW_HY, z, bar);
+      tma_load3(base + 4 * L::XB, mf, it.x0 - SW_FHX, it.y0 - SW_HY, z, bar);
+      ++iq;
+      if (++ig == ng) {
+        ig = 0;
+        if (++ik < K) load_item(sw, n2, w, nw, maps, lead);
+      }
+    }
+  }
+};
+
+// Waits (bounded) until loads up to index `need` have landed; false on expiry.
+__device__ __forceinline__ bool sw_wait_upto(unsigned bar0, int& waited, int need) {
+  for (; waited <= need; ++waited)
+    if (!mbar_wait(bar0 + 8 * (waited & (SW_NS - 1)), (unsigned)((waited >> SW_NS_LOG) & 1))) return false;
+  return true;
+}
+
+// After a failure: raise the grid's error word and let this CTA's copies in
+// flight land (bounded), so that none writes into shared memory after return.
+__device__ __forceinline__ void sw_drain(const Ctx& c, unsigned bar0, int waited, int issued) {
+  if (threadIdx.x == 0) {
+    if (c.B.err) atomicOr(c.B.err, 1);
+    for (; waited < issued; ++waited)
+      if (!mbar_wait(bar0 + 8 * (waited & (SW_NS - 1)), (unsigned)((waited >> SW_NS_LOG) & 1))) break;
+  }
 }
 
 // One fused pass over the regular cells of grid level l (SweepLev on),
 // x -> alt, then x and alt swap in this CTA's copy of the hierarchy.  CTA 0
 // of the group keeps the coarse levels in its shared memory and sits the
-// pass out; the other CTAs take the tiles round-robin.  `dyn` is the
-// dynamic shared memory.
+// pass out; the other CTAs take the items round-robin.
 //
-// Step zs of an item: wait for plane zs + 1; red cells of plane zs (tile
-// and ring); one block barrier; black cells of plane zs - 1 (tile); store
-// plane zs - 2, final since the barrier; refill the slot of plane zs - 3,
-// which nothing reads any more.  The ring has SW_NS slots: four planes in
-// use, four in flight.
+// Item with planes [z0, z1): copy g holds planes z0 - 2 + 2g and the next;
+// step s (s = 0 .. Z/2 + 1, Z = z1 - z0) relaxes red on planes a, a + 1
+// (a = z0 - 1 + 2s; within [z0 - 1, z1], the ring plane at each end
+// included), block barrier, black on planes a - 1, a (within [z0, z1)),
+// stores planes a - 3, a - 2 (within [z0, z1)), then refills the slots of
+// the copies below g = s - 1, which no later step reads.
 template <class T>
-__device__ bool ph_sweep3d(const Hier<T>& Hc, int l, const Ctx& c, unsigned char* dyn) {
+__device__ __noinline__ bool ph_sweep3d(const Hier<T>& Hc, int l, const Ctx& c, unsigned char* dyn) {
+  using L = SwSlot<T>;
   Hier<T>& H = const_cast<Hier<T>&>(Hc);
   Op<T>& o = H.op[l];
   SweepLev<T>& sw = H.sw[l];
-  const int two = o.x[1] != nullptr;
-  const int ty = sw.ty;
-  const SweepSlot<T> L(ty, two);
   const int nw = c.gsize - 1, w = c.gcta - 1;
-  const int n0 = o.n[0], n1 = o.n[1], n2 = o.n[2];
-  const int K = (w >= 0 && sw.nitems > w) ? (sw.nitems - 1 - w) / nw + 1 : 0;
-  // layout: SW_NS mbarriers, item mask words, SW_NS has1 flags, a fail flag, then the ring
+  const int n2 = o.n[2];
+  const int ntot = sw.nitems + sw.n1items;
+  const int K = (w >= 0 && ntot > w) ? (ntot - 1 - w) / nw + 1 : 0;
   unsigned long long* bars = (unsigned long long*)dyn;
-  unsigned* mask = (unsigned*)(dyn + 8 * SW_NS_MAX);
-  int* slot1 = (int*)(dyn + 8 * SW_NS_MAX + 4 * SW_MASK_MAX);
-  volatile int* sfail = slot1 + SW_NS_MAX;
-  // the ring starts on a 128-byte boundary of the shared window (the host
-  // reserves 128 bytes of slack for this)
-  unsigned char* ring = dyn + SW_HEAD + ((128u - (smem_u32(dyn + SW_HEAD) & 127u)) & 127u);
+  volatile int* sfail = (volatile int*)(dyn + 8 * SW_NS);
+  unsigned char* ring = sw_ring(dyn);
   const unsigned bar0 = smem_u32(bars);
   bool ok = true;
   if (K > 0) {
-    const int nwords = (sw.nitems + 31) >> 5;
-    for (int q = threadIdx.x; q < nwords; q += blockDim.x) mask[q] = two ? sw.has1[q] : 0u;
     if (threadIdx.x == 0) {
       for (int s = 0; s < SW_NS; ++s) mbar_init(bar0 + 8 * s, 1);
       fence_mbar_init();
       *sfail = 0;
     }
     __syncthreads();
-    const int ntx = sw.ntx, nty = sw.nty, zc = sw.zc;
-    const unsigned char* mp = (const unsigned char*)sw.maps;  // 7 tensor maps of 128 bytes
-    const void* mx0 = mp + 128 * (2 * sw.par + 0);
-    const void* mx1 = mp + 128 * (2 * sw.par + 1);
-    const void* mb0 = mp + 128 * 4;
-    const void* mb1 = mp + 128 * 5;
-    const void* mf = mp + 128 * 6;
-    auto geom = [&](int k, int& x0, int& y0, int& z0, int& z1, int& h1) {
-      const int it = w + k * nw;
-      const int tx = it % ntx, r = it / ntx;
-      x0 = tx * SW_TX;
-      y0 = (r % nty) * ty;
-      z0 = (r / nty) * zc;
-      z1 = min(z0 + zc, n2);
-      h1 = (mask[it >> 5] >> (it & 31)) & 1;
-    };
-    // issue cursor (thread 0): item ik and its geometry, plane index itp, load index iq
-    int ik = 0, itp = 0, iq = 0;
-    int gx0 = 0, gy0 = 0, gz0 = 0, gz1 = 0, gh1 = 0;
-    if (threadIdx.x == 0) geom(0, gx0, gy0, gz0, gz1, gh1);
-    auto issue = [&](int limit) {
-      while (iq < limit && ik < K) {
-        const int s = iq & (SW_NS - 1);
-        const unsigned bar = bar0 + 8 * s;
-        const unsigned base = smem_u32(ring + s * L.bytes);
-        const int z = gz0 - 2 + itp;
-        slot1[s] = gh1;
-        mbar_expect_tx(bar, (unsigned)((gh1 ? 4 : 2) * L.xb + L.fb));
-        tma_load3(base, mx0, gx0 - SW_HX, gy0 - SW_HY, z, bar);
-        tma_load3(base + (two ? 2 : 1) * L.xb, mb0, gx0 - SW_HX, gy0 - SW_HY, z, bar);
-        if (gh1) {
-          tma_load3(base + L.xb, mx1, gx0 - SW_HX, gy0 - SW_HY, z, bar);
-          tma_load3(base + 3 * L.xb, mb1, gx0 - SW_HX, gy0 - SW_HY, z, bar);
-        }
-        tma_load3(base + (two ? 4 : 2) * L.xb, mf, gx0 - SW_FHX, gy0 - SW_HY, z, bar);
-        ++iq;
-        if (++itp == gz1 - gz0 + 4) {
-          itp = 0;
-          if (++ik < K) geom(ik, gx0, gy0, gz0, gz1, gh1);
-        }
-      }
-    };
+    const unsigned char* maps = (const unsigned char*)sw.maps;
+    SwIssue<T> iss;
     if (threadIdx.x == 0) {
+      iss.start(sw, n2, w, nw, K, maps, 2);
       fence_async_global();  // x was last written by generic stores of other CTAs
-      issue(SW_NS);
+      iss.run(sw, n2, w, nw, maps, ring, bar0, SW_NS, 2);
     }
-    // thread mapping: the tile's cells of one colour, 16 per row (t < 16 ty);
-    // the ring's red cells (2 rows of 17, one per tile row) by the last
-    // ty + 34 threads, away from warp 0, which issues the loads
+    // thread mapping: the tile's cells of one colour, 16 per row; the ring's
+    // red cells of two planes (2 x (2 rows of 17 + 32 row ends)) by the last
+    // 132 threads, away from warp 0, which issues the copies
     const int t = threadIdx.x;
     const int tr = t >> 4, tm = t & 15;
-    const bool tin = t < 16 * ty;
     const int tring = (int)blockDim.x - 1 - t;
-    const SwGrid<T> g(o, L, two);
-    T* const alt0 = sw.alt[0];
-    T* const alt1 = sw.alt[1];
     int qb = 0, waited = 0;
     for (int k = 0; k < K && ok; ++k) {
-      int x0, y0, z0, z1, h1;
-      geom(k, x0, y0, z0, z1, h1);
-      for (int zs = z0 - 1; zs <= z1 + 1; ++zs) {
-        // planes up to zs + 1 (the item's last is z1 + 1) have landed
-        const int need = qb + min(zs + 1, z1 + 1) - (z0 - 2);
-        for (; waited <= need; ++waited)
-          if (!mbar_wait(bar0 + 8 * (waited & (SW_NS - 1)), (unsigned)((waited / SW_NS) & 1))) {
-            *sfail = 1;
-            break;
-          }
-        const int q0 = qb + zs - z0 + 2;  // load index of plane zs
-        unsigned char* const Pm2 = ring + ((q0 - 2) & (SW_NS - 1)) * g.slot;
-        unsigned char* const Pm = ring + ((q0 - 1) & (SW_NS - 1)) * g.slot;
-        unsigned char* const P0 = ring + (q0 & (SW_NS - 1)) * g.slot;
-        unsigned char* const Pp = ring + ((q0 + 1) & (SW_NS - 1)) * g.slot;
-        // red cells of plane zs on the tile and its one-cell ring
-        if (zs <= z1 && zs >= 0 && zs < n2) {
-          const bool kin = zs > 0 && zs < n2 - 1;
-          if (tin) {
+      SwItem<T> it;
+      it.at(sw, n2, w + k * nw);
+      const SwGrid<T> g(o, it.p);
+      const unsigned pbit = 1u << it.p;
+      T* const alt = sw.alt[it.p];
+      const int x0 = it.x0, y0 = it.y0, z0 = it.z0, z1 = it.z1;
+      const int G = (z1 - z0 + 4) >> 1, S = ((z1 - z0) >> 1) + 2;
+      // plane z of this item: its x, b and flag boxes in the ring
+      auto PX = [&](int z) -> T* {
+        const int tz = z - z0 + 2;
+        return (T*)(ring + ((qb + (tz >> 1)) & (SW_NS - 1)) * L::BYTES + (tz & 1) * L::XB);
+      };
+      auto PB = [&](int z) -> const T* { return (const T*)((const unsigned char*)PX(z) + 2 * L::XB - 0); };
+      auto PF = [&](int z) -> const unsigned char* {
+        const int tz = z - z0 + 2;
+        return ring + ((qb + (tz >> 1)) & (SW_NS - 1)) * L::BYTES + 4 * L::XB + (tz & 1) * L::FB;
+      };
+      for (int s = 0; s < S; ++s) {
+        if (!sw_wait_upto(bar0, waited, qb + min(s + 1, G - 1))) *sfail = 1;
+        const int a = z0 - 1 + 2 * s;
+        // red cells of planes a, a + 1 on the tile and its ring
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = a + h;
+          if (r > z1 || r < 0 || r >= n2) continue;
+          T* Xc = PX(r);
+          const T *Xm = PX(r - 1), *Xp = PX(r + 1), *B = PB(r);
+          const unsigned char* F = PF(r);
+          const bool kin = r > 0 && r < n2 - 1;
+          {
             const int j = y0 + tr;
-            const int lx = SW_HX + ((j + zs) & 1) + 2 * tm;
-            sw_relax(g, P0, Pm, Pp, x0 - SW_HX + lx, j, zs, kin, lx, SW_HY + tr);
+            const int lx = SW_HX + ((j + r) & 1) + 2 * tm;
+            sw_relax(g, Xc, Xm, Xp, B, F, pbit, x0 - SW_HX + lx, j, r, kin, lx, SW_HY + tr);
           }
-          if (tring < ty + 34) {
+          const int tq = tring - 66 * h;
+          if (tq >= 0 && tq < 66) {
             int j, lx, ly;
-            if (tring < 34) {  // ring rows above and below the tile
-              ly = tring < 17 ? SW_HY - 1 : SW_HY + ty;
+            if (tq < 34) {  // ring rows above and below the tile
+              ly = tq < 17 ? SW_HY - 1 : SW_HY + SW_TY;
               j = y0 - SW_HY + ly;
-              lx = SW_HX - 1 + ((j + zs + 1) & 1) + 2 * (tring < 17 ? tring : tring - 17);
+              lx = SW_HX - 1 + ((j + r + 1) & 1) + 2 * (tq < 17 ? tq : tq - 17);
             } else {  // the ring cell at the left or right end of a tile row
-              ly = SW_HY + tring - 34;
+              ly = SW_HY + tq - 34;
               j = y0 - SW_HY + ly;
-              lx = ((j + zs) & 1) ? SW_HX - 1 : SW_HX + SW_TX;
+              lx = ((j + r) & 1) ? SW_HX - 1 : SW_HX + SW_TX;
             }
-            sw_relax(g, P0, Pm, Pp, x0 - SW_HX + lx, j, zs, kin, lx, ly);
+            sw_relax(g, Xc, Xm, Xp, B, F, pbit, x0 - SW_HX + lx, j, r, kin, lx, ly);
           }
         }
         fence_async_smem();
@@ -338,47 +395,42 @@ __device__ bool ph_sweep3d(const Hier<T>& Hc, int l, const Ctx& c, unsigned char
           ok = false;
           break;
         }
-        // black cells of plane zs - 1 on the tile
-        const int zw = zs - 1;
-        if (zw >= z0 && zw < z1 && tin) {
+        // black cells of planes a - 1, a on the tile
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int q = a - 1 + h;
+          if (q < z0 || q >= z1) continue;
           const int j = y0 + tr;
-          const int lx = SW_HX + ((j + zw + 1) & 1) + 2 * tm;
-          sw_relax(g, Pm, Pm2, P0, x0 - SW_HX + lx, j, zw, zw > 0 && zw < n2 - 1, lx, SW_HY + tr);
+          const int lx = SW_HX + ((j + q + 1) & 1) + 2 * tm;
+          sw_relax(g, PX(q), PX(q - 1), PX(q + 1), PB(q), PF(q), pbit, x0 - SW_HX + lx, j, q,
+                   q > 0 && q < n2 - 1, lx, SW_HY + tr);
         }
-        // store plane zs - 2: the tile's unknowns, both colours, cut cells as given
-        const int zo = zs - 2;
-        if (zo >= z0 && zo < z1) {
-          const unsigned char* F = Pm2 + g.fo;
-          const int h1w = slot1[(q0 - 2) & (SW_NS - 1)];
-          const T* X0 = (const T*)Pm2;
-          const T* X1 = (const T*)(Pm2 + g.xb);
+        // store planes a - 3, a - 2 (final since the last step): the tile's
+        // unknowns of this phase, both colours, cut cells as given
+        {
           const int rx = t & 31, i = x0 + rx;
-          if (i < n0)
-            for (int ry = t >> 5; ry < ty; ry += (int)(blockDim.x >> 5)) {
-              const int j = y0 + ry;
-              if (j >= n1) break;
-              const int ly = SW_HY + ry, lx = SW_HX + rx;
-              const unsigned f = F[ly * SW_FBX + lx + (SW_FHX - SW_HX)];
-              const long long cc = ((long long)zo * n1 + j) * n0 + i;
-              const int e = ly * SW_BX + lx;
-              if (f & 1u) alt0[cc] = X0[e];
-              if ((f & 2u) && h1w) alt1[cc] = X1[e];
+          if (i < g.n0)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int q = a - 3 + h;
+              if (q < z0 || q >= z1) continue;
+              const T* X = PX(q);
+              const unsigned char* F = PF(q);
+              for (int ry = t >> 5; ry < SW_TY; ry += (int)(blockDim.x >> 5)) {
+                const int j = y0 + ry;
+                if (j >= g.n1) break;
+                const int ly = SW_HY + ry, lx = SW_HX + rx;
+                if (F[ly * SW_FBX + lx + (SW_FHX - SW_HX)] & pbit)
+                  alt[((long long)q * g.n1 + j) * g.n0 + i] = X[ly * SW_BX + lx];
+              }
             }
         }
-        // the slots of planes up to zs - 3 are free (their last readers ran
-        // before the barrier): refill them
-        if (t == 0) issue(qb + max(0, zs - z0) + SW_NS);
+        // copies below s - 1 are read by no later step: refill their slots
+        if (t == 0) iss.run(sw, n2, w, nw, maps, ring, bar0, qb + max(0, s - 1) + SW_NS, 2);
       }
-      qb += z1 - z0 + 4;
+      qb += G;
     }
-    if (!ok) {
-      // give up: raise the error word, then let this CTA's copies in flight land
-      if (t == 0) {
-        atomicOr(c.B.err, 1);
-        for (; waited < iq; ++waited)
-          if (!mbar_wait(bar0 + 8 * (waited & (SW_NS - 1)), (unsigned)((waited / SW_NS) & 1))) break;
-      }
-    }
+    if (!ok) sw_drain(c, bar0, waited, t == 0 ? iss.iq : 0);
     __syncthreads();
     if (t == 0)
       for (int s = 0; s < SW_NS; ++s) mbar_inval(bar0 + 8 * s);
@@ -395,196 +447,118 @@ __device__ bool ph_sweep3d(const Hier<T>& Hc, int l, const Ctx& c, unsigned char
   return ok;
 }
 
-// Residual b - A x of the regular cell (i, j, k) at box position (lx, ly) of
-// the planes P0 (k), Pm, Pp in phase p (po: its byte offset), with the terms
-// and order of cell_residual.
-template <class T>
-__device__ __forceinline__ T sw_resid(const SwGrid<T>& g, const unsigned char* P0, const unsigned char* Pm,
-                                      const unsigned char* Pp, int po, T ceps, int i, int j, int k, bool kin, int lx,
-                                      int ly) {
-  const T* Xc = (const T*)(P0 + po);
-  const T* Xm = (const T*)(Pm + po);
-  const T* Xp = (const T*)(Pp + po);
-  const int e = ly * SW_BX + lx;
-  const T bcell = ((const T*)(P0 + g.bo + po))[e];
-  if (kin && (unsigned)(i - 1) < (unsigned)(g.n0 - 2) && (unsigned)(j - 1) < (unsigned)(g.n1 - 2)) {
-    const T sum = ((((Xc[e - 1] + Xc[e + 1]) + Xc[e - SW_BX]) + Xc[e + SW_BX]) + Xm[e]) + Xp[e];
-    return bcell - ceps * ((T)6 * Xc[e] - sum);
-  }
-  T sum;
-  int dg;
-  sw_wall_stencil(g, Xm, Xc, Xp, e, i, j, k, sum, dg);
-  return bcell - ceps * ((T)dg * Xc[e] - sum);
-}
-
 // Residual + restriction of grid level l (SweepLev on) onto level l + 1
 // (half the cells per axis): coarse b = mean of the children's residuals
-// (cut children from the sparse residual rows in tmp), coarse x = 0.  The
-// level streams through the same ring as the sweep; a step computes the
-// residuals of one plane, pairs of x neighbours combine by a shuffle and
-// pairs of planes in registers, and the coarse plane is stored after the
-// odd one.  One block barrier per step.
+// (cut children from the sparse residual rows in tmp), coarse x = 0, per
+// phase.  The level streams through the same ring: copy g holds planes
+// z0 - 2 + 2g and the next; step s forms the residuals of planes z0 + 2s and
+// z0 + 2s + 1, which are the children of one coarse plane: pairs of x
+// neighbours combine by a shuffle, the coarse plane is stored, and after the
+// step's block barrier the slots of the copies below g = s + 1 are refilled.
 template <class T>
-__device__ bool ph_restrict3d(const Hier<T>& Hc, int l, const Ctx& c, unsigned char* dyn) {
+__device__ __noinline__ bool ph_restrict3d(const Hier<T>& Hc, int l, const Ctx& c, unsigned char* dyn) {
+  using L = SwSlot<T>;
   const Hier<T>& H = Hc;
   const Op<T>& o = H.op[l];
   const Op<T>& co = H.op[l + 1];
   const SweepLev<T>& sw = H.sw[l];
-  const int two = o.x[1] != nullptr;
-  const int ty = sw.ty;
-  const SweepSlot<T> L(ty, two);
   const int nw = c.gsize - 1, w = c.gcta - 1;
-  const int n0 = o.n[0], n1 = o.n[1], n2 = o.n[2];
-  const int K = (w >= 0 && sw.nitems > w) ? (sw.nitems - 1 - w) / nw + 1 : 0;
+  const int n2 = o.n[2];
+  const int ntot = sw.nitems + sw.n1items;
+  const int K = (w >= 0 && ntot > w) ? (ntot - 1 - w) / nw + 1 : 0;
   unsigned long long* bars = (unsigned long long*)dyn;
-  unsigned* mask = (unsigned*)(dyn + 8 * SW_NS_MAX);
-  int* slot1 = (int*)(dyn + 8 * SW_NS_MAX + 4 * SW_MASK_MAX);
-  volatile int* sfail = slot1 + SW_NS_MAX;
-  unsigned char* ring = dyn + SW_HEAD + ((128u - (smem_u32(dyn + SW_HEAD) & 127u)) & 127u);
+  volatile int* sfail = (volatile int*)(dyn + 8 * SW_NS);
+  unsigned char* ring = sw_ring(dyn);
   const unsigned bar0 = smem_u32(bars);
   bool ok = true;
   if (K > 0) {
-    const int nwords = (sw.nitems + 31) >> 5;
-    for (int q = threadIdx.x; q < nwords; q += blockDim.x) mask[q] = two ? sw.has1[q] : 0u;
     if (threadIdx.x == 0) {
       for (int s = 0; s < SW_NS; ++s) mbar_init(bar0 + 8 * s, 1);
       fence_mbar_init();
       *sfail = 0;
     }
     __syncthreads();
-    const int ntx = sw.ntx, nty = sw.nty, zc = sw.zc;
-    const unsigned char* mp = (const unsigned char*)sw.maps;
-    const void* mx0 = mp + 128 * (2 * sw.par + 0);
-    const void* mx1 = mp + 128 * (2 * sw.par + 1);
-    const void* mb0 = mp + 128 * 4;
-    const void* mb1 = mp + 128 * 5;
-    const void* mf = mp + 128 * 6;
-    auto geom = [&](int k, int& x0, int& y0, int& z0, int& z1, int& h1) {
-      const int it = w + k * nw;
-      const int tx = it % ntx, r = it / ntx;
-      x0 = tx * SW_TX;
-      y0 = (r % nty) * ty;
-      z0 = (r / nty) * zc;
-      z1 = min(z0 + zc, n2);
-      h1 = (mask[it >> 5] >> (it & 31)) & 1;
-    };
-    // loads: planes z0 - 1 .. z1 of each item
-    int ik = 0, itp = 0, iq = 0;
-    int gx0 = 0, gy0 = 0, gz0 = 0, gz1 = 0, gh1 = 0;
-    if (threadIdx.x == 0) geom(0, gx0, gy0, gz0, gz1, gh1);
-    auto issue = [&](int limit) {
-      while (iq < limit && ik < K) {
-        const int s = iq & (SW_NS - 1);
-        const unsigned bar = bar0 + 8 * s;
-        const unsigned base = smem_u32(ring + s * L.bytes);
-        const int z = gz0 - 1 + itp;
-        slot1[s] = gh1;
-        mbar_expect_tx(bar, (unsigned)((gh1 ? 4 : 2) * L.xb + L.fb));
-        tma_load3(base, mx0, gx0 - SW_HX, gy0 - SW_HY, z, bar);
-        tma_load3(base + (two ? 2 : 1) * L.xb, mb0, gx0 - SW_HX, gy0 - SW_HY, z, bar);
-        if (gh1) {
-          tma_load3(base + L.xb, mx1, gx0 - SW_HX, gy0 - SW_HY, z, bar);
-          tma_load3(base + 3 * L.xb, mb1, gx0 - SW_HX, gy0 - SW_HY, z, bar);
-        }
-        tma_load3(base + (two ? 4 : 2) * L.xb, mf, gx0 - SW_FHX, gy0 - SW_HY, z, bar);
-        ++iq;
-        if (++itp == gz1 - gz0 + 2) {
-          itp = 0;
-          if (++ik < K) geom(ik, gx0, gy0, gz0, gz1, gh1);
-        }
-      }
-    };
+    const unsigned char* maps = (const unsigned char*)sw.maps;
+    SwIssue<T> iss;
     if (threadIdx.x == 0) {
-      fence_async_global();  // x was last written by generic stores of other CTAs
-      issue(SW_NS);
+      iss.start(sw, n2, w, nw, K, maps, 2);
+      fence_async_global();
+      iss.run(sw, n2, w, nw, maps, ring, bar0, SW_NS, 2);
     }
-    // thread t: fine cells (2 cx + h, 2 cy + v) of coarse cell (cx, cy), h = t & 1,
-    // for the plane's two child rows v = 0, 1; coarse cells 16 per row
+    // thread t: fine cells (2 cx + h, 2 cy + v), v = 0, 1, of coarse cell
+    // (cx, cy) = ((t >> 1) & 15, t >> 5) in both planes of a step
     const int t = threadIdx.x;
     const int hx = t & 1, ccx = (t >> 1) & 15, ccy = t >> 5;
-    const bool tin = ccy < (ty >> 1);
-    const SwGrid<T> g(o, L, two);
+    const bool tin = ccy < (SW_TY >> 1);
     const T scale = T(1) / T(8);
     const int cn0 = co.n[0], cn1 = co.n[1];
-    const long long csxy = (long long)cn0 * cn1;
     int qb = 0, waited = 0;
-    T acc[2] = {T(0), T(0)};
     for (int k = 0; k < K && ok; ++k) {
-      int x0, y0, z0, z1, h1;
-      geom(k, x0, y0, z0, z1, h1);
-      for (int zs = z0; zs < z1; ++zs) {
-        const int need = qb + zs + 1 - (z0 - 1);
-        for (; waited <= need; ++waited)
-          if (!mbar_wait(bar0 + 8 * (waited & (SW_NS - 1)), (unsigned)((waited / SW_NS) & 1))) {
-            *sfail = 1;
-            break;
-          }
-        const int q0 = qb + zs - (z0 - 1);
-        const unsigned char* const Pm = ring + ((q0 - 1) & (SW_NS - 1)) * g.slot;
-        const unsigned char* const P0 = ring + (q0 & (SW_NS - 1)) * g.slot;
-        const unsigned char* const Pp = ring + ((q0 + 1) & (SW_NS - 1)) * g.slot;
-        const unsigned char* F = P0 + g.fo;
-        const int h1s = slot1[q0 & (SW_NS - 1)];
-        const bool kin = zs > 0 && zs < n2 - 1;
+      SwItem<T> it;
+      it.at(sw, n2, w + k * nw);
+      const SwGrid<T> g(o, it.p);
+      const int p = it.p;
+      const unsigned pbit = 1u << p;
+      const int x0 = it.x0, y0 = it.y0, z0 = it.z0, z1 = it.z1;
+      const int G = (z1 - z0 + 4) >> 1, S = (z1 - z0) >> 1;
+      T* const cb = co.b[p];
+      T* const cx = co.x[p];
+      for (int s = 0; s < S; ++s) {
+        if (!sw_wait_upto(bar0, waited, qb + min(s + 2, G - 1))) *sfail = 1;
+        T acc = T(0);
         if (tin) {
 #pragma unroll
-          for (int v = 0; v < 2; ++v) {
-            const int rx = 2 * ccx + hx, ry = 2 * ccy + v;
-            const int i = x0 + rx, j = y0 + ry;
-            if (i >= n0 || j >= n1) continue;
-            const int ly = SW_HY + ry, lx = SW_HX + rx;
-            const unsigned f = F[ly * SW_FBX + lx + (SW_FHX - SW_HX)];
-            if (!(f & 3u)) continue;
-            if (f & F_IRR) {
-              const long long cc = ((long long)zs * n1 + j) * n0 + i;
-              const long long r2 = 2 * (long long)o.irr_of_cell[cc];
-              if (f & 1u) acc[0] += o.tmp[r2];
-              if (f & 2u) acc[1] += o.tmp[r2 + 1];
-              continue;
-            }
-            if (f & 1u) {
-              acc[0] += sw_resid(g, P0, Pm, Pp, 0, g.ceps0, i, j, zs, kin, lx, ly);
-            } else if (h1s) {  // (a box without dielectric unknowns has no phase-1 cell)
-              acc[1] += sw_resid(g, P0, Pm, Pp, g.xb, g.ceps1, i, j, zs, kin, lx, ly);
+          for (int h = 0; h < 2; ++h) {
+            const int z = z0 + 2 * s + h;
+            auto base = [&](int zz) {
+              const int tz = zz - z0 + 2;
+              return ring + ((qb + (tz >> 1)) & (SW_NS - 1)) * L::BYTES + (tz & 1) * L::XB;
+            };
+            const T* Xc = (const T*)base(z);
+            const T* Xm = (const T*)base(z - 1);
+            const T* Xp = (const T*)base(z + 1);
+            const T* B = (const T*)(base(z) + 2 * L::XB);
+            const int tz = z - z0 + 2;
+            const unsigned char* F = ring + ((qb + (tz >> 1)) & (SW_NS - 1)) * L::BYTES + 4 * L::XB + (tz & 1) * L::FB;
+            const bool kin = z > 0 && z < n2 - 1;
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+              const int rx = 2 * ccx + hx, ry = 2 * ccy + v;
+              const int i = x0 + rx, j = y0 + ry;
+              if (i >= g.n0 || j >= g.n1) continue;
+              const int ly = SW_HY + ry, lx = SW_HX + rx;
+              const unsigned f = F[ly * SW_FBX + lx + (SW_FHX - SW_HX)];
+              if (!(f & pbit)) continue;
+              if (f & F_IRR) {
+                const long long cc = ((long long)z * g.n1 + j) * g.n0 + i;
+                acc += o.tmp[2 * (long long)o.irr_of_cell[cc] + p];
+                continue;
+              }
+              acc += sw_resid(g, Xc, Xm, Xp, B, i, j, z, kin, lx, ly);
             }
           }
         }
-        // after the odd plane: the pair of x neighbours of one coarse cell sits
-        // in lanes t, t ^ 1 (each lane holds its column of both planes)
-        if ((zs & 1) == 1) {
-          acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
-          acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], 1);
-        }
-        if ((zs & 1) == 1 && tin && hx == 0) {
-          const int ci = (x0 >> 1) + ccx, cj = (y0 >> 1) + ccy, ck = zs >> 1;
+        // the pair of x neighbours of one coarse cell sits in lanes t, t ^ 1
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (tin && hx == 0) {
+          const int ci = (x0 >> 1) + ccx, cj = (y0 >> 1) + ccy, ck = (z0 >> 1) + s;
           if (ci < cn0 && cj < cn1) {
-            const long long C = (long long)ck * csxy + (long long)cj * cn0 + ci;
-            const unsigned cfl = co.flags[C];
-            for (int p = 0; p < 2; ++p) {
-              if (co.b[p] == nullptr) continue;
-              co.b[p][C] = ((cfl >> p) & 1u) ? acc[p] * scale : T(0);
-              co.x[p][C] = T(0);
-            }
+            const long long C = ((long long)ck * cn1 + cj) * cn0 + ci;
+            cb[C] = ((co.flags[C] >> p) & 1u) ? acc * scale : T(0);
+            cx[C] = T(0);
           }
         }
-        if ((zs & 1) == 1) acc[0] = acc[1] = T(0);
         __syncthreads();
         if (*sfail) {
           ok = false;
           break;
         }
-        // plane zs - 1 is read by no later step: its slot takes the next load
-        if (t == 0) issue(q0 - 1 + 1 + SW_NS);
+        // copies below s + 1 are read by no later step: refill their slots
+        if (t == 0) iss.run(sw, n2, w, nw, maps, ring, bar0, qb + s + 1 + SW_NS, 2);
       }
-      qb += z1 - z0 + 2;
+      qb += G;
     }
-    if (!ok) {
-      if (t == 0) {
-        atomicOr(c.B.err, 1);
-        for (; waited < iq; ++waited)
-          if (!mbar_wait(bar0 + 8 * (waited & (SW_NS - 1)), (unsigned)((waited / SW_NS) & 1))) break;
-      }
-    }
+    if (!ok) sw_drain(c, bar0, waited, t == 0 ? iss.iq : 0);
     __syncthreads();
     if (t == 0)
       for (int s = 0; s < SW_NS; ++s) mbar_inval(bar0 + 8 * s);
