@@ -291,6 +291,13 @@ eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, double* ms_per
  * returns EB_ERR_TIMEOUT with ms_per_launch the kernel's duration, and the
  * context stays usable. */
 
+/* Benchmark hook (no counterpart in the paper): the device's measured rate
+ * of fused multiply-adds in FP64 and in FP32, in TFLOP/s (two flops per
+ * FMA): eight independent FMA chains per thread over eight CTAs of 256
+ * threads per SM, timed with CUDA events.  The roofline of an FP64 kernel is
+ * the lesser of the memory bound and this rate times its flops per byte. */
+eb_status eb_device_fma_rates(int device, double* fp64_tflops, double* fp32_tflops);
+
 /* Diagnostics (no counterpart in the paper): the phases of the first V-cycle
  * of the last persistent solve.  out[0] = number of phases m; then for each
  * phase i, out[1+2i] = its code ((level << 4) | kind; kinds 1 red regular

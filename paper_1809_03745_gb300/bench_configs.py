@@ -19,6 +19,7 @@ summed per level and phase kind, and the grid-barrier cost.
 
 Usage: python -m paper_1809_03745_gb300.bench_configs [--only C1 C2 C3 C4]
        python -m paper_1809_03745_gb300.bench_configs --trace c2 [--n N] [--precision mixed|fp64]
+       python -m paper_1809_03745_gb300.bench_configs --peaks   (measured FP64 / FP32 FMA rates)
 """
 from __future__ import annotations
 
@@ -152,8 +153,13 @@ def main():
     ap.add_argument("--trace", choices=["c1", "c2", "c3"], default=None)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--peaks", action="store_true")
     args = ap.parse_args()
     E.load()
+    if args.peaks:
+        f64, f32 = E.device_fma_rates(torch.cuda.current_device())
+        print(json.dumps({"fp64_fma_tflops": f64, "fp32_fma_tflops": f32}), flush=True)
+        return
     if args.trace:
         trace(args.trace, args.n, args.precision)
         return

@@ -22,7 +22,7 @@ constexpr long long BAR_WAIT_CYCLES = 4000000000LL;  // ~2 s of SM clock: a barr
 // SW_FBX bytes wide from SW_FHX cells left of the tile (16-byte alignment of
 // bytes); two planes per copy, a ring of SW_NS two-plane slots.
 constexpr int SW_TX = 32, SW_TY = 32, SW_HX = 4, SW_BX = SW_TX + 2 * SW_HX, SW_HY = 2, SW_FHX = 16, SW_FBX = 64;
-constexpr int SW_NS = 4, SW_NS_LOG = 2;
+constexpr int SW_NS = 6;  // three slots in use, three copies in flight
 constexpr int SW_HEAD = 128;  // mbarriers and a failure flag before the ring
 
 template <class T>

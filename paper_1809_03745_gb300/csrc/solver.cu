@@ -1577,6 +1577,65 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
   return EB_OK;
 }
 
+// ------------------------------------------------------- arithmetic peaks
+
+// 8 independent fused multiply-add chains per thread, `iters` steps each;
+// the result is stored so that no chain is dead code
+template <class T>
+__global__ void k_fma_rate(T* out, int iters, T a, T b) {
+  T v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = (T)(threadIdx.x + k) * (T)1e-3;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = fma(v[k], a, b);
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += v[k];
+  out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <class T>
+static eb_status fma_rate(int device, double* tflops) {
+  int nsm = 0, dev0 = 0;
+  cudaGetDevice(&dev0);
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+  const int blocks = nsm * 8, threads = 256, iters = 1 << 14;
+  T* out = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(T) * (size_t)blocks * threads);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float ms = 0.0f;
+  if (e == cudaSuccess) {
+    k_fma_rate<T><<<blocks, threads>>>(out, iters, (T)0.999999, (T)1e-7);
+    cudaEventRecord(e0);
+    for (int r = 0; r < 5; ++r) k_fma_rate<T><<<blocks, threads>>>(out, iters, (T)0.999999, (T)1e-7);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (out) cudaFree(out);
+  cudaSetDevice(dev0);
+  if (e != cudaSuccess) return cuda_fail(e, "arithmetic rate");
+  // two flops per fused multiply-add
+  *tflops = 2.0 * 8.0 * iters * (double)blocks * threads * 5.0 / (ms * 1e-3) / 1e12;
+  return EB_OK;
+}
+
+extern "C" eb_status eb_device_fma_rates(int device, double* fp64_tflops, double* fp32_tflops) {
+  if (!fp64_tflops || !fp32_tflops) {
+    set_error("null argument");
+    return EB_ERR_INVALID;
+  }
+  eb_status st = fma_rate<double>(device, fp64_tflops);
+  if (st == EB_OK) st = fma_rate<float>(device, fp32_tflops);
+  return st;
+}
+
 extern "C" eb_status eb_poisson_trace(eb_poisson* P, double* out, int n) {
   if (!P || !out || n < 1) {
     set_error("invalid argument");

@@ -258,7 +258,7 @@ struct SwIssue {
                       unsigned bar0, int limit, int lead) {
     using L = SwSlot<T>;
     while (iq < limit && ik < K) {
-      const int s = iq & (SW_NS - 1);
+      const int s = iq % SW_NS;
       const unsigned bar = bar0 + 8 * s;
       const unsigned base = smem_u32(ring + s * L::BYTES);
       const int z = it.z0 - lead + 2 * ig;
@@ -278,7 +278,7 @@ struct SwIssue {
 // Waits (bounded) until loads up to index `need` have landed; false on expiry.
 __device__ __forceinline__ bool sw_wait_upto(unsigned bar0, int& waited, int need) {
   for (; waited <= need; ++waited)
-    if (!mbar_wait(bar0 + 8 * (waited & (SW_NS - 1)), (unsigned)((waited >> SW_NS_LOG) & 1))) return false;
+    if (!mbar_wait(bar0 + 8 * (waited % SW_NS), (unsigned)((waited / SW_NS) & 1))) return false;
   return true;
 }
 
@@ -288,7 +288,7 @@ __device__ __forceinline__ void sw_drain(const Ctx& c, unsigned bar0, int waited
   if (threadIdx.x == 0) {
     if (c.B.err) atomicOr(c.B.err, 1);
     for (; waited < issued; ++waited)
-      if (!mbar_wait(bar0 + 8 * (waited & (SW_NS - 1)), (unsigned)((waited >> SW_NS_LOG) & 1))) break;
+      if (!mbar_wait(bar0 + 8 * (waited % SW_NS), (unsigned)((waited / SW_NS) & 1))) break;
   }
 }
 
@@ -350,12 +350,12 @@ __device__ __noinline__ bool ph_sweep3d(const Hier<T>& Hc, int l, const Ctx& c, 
       // plane z of this item: its x, b and flag boxes in the ring
       auto PX = [&](int z) -> T* {
         const int tz = z - z0 + 2;
-        return (T*)(ring + ((qb + (tz >> 1)) & (SW_NS - 1)) * L::BYTES + (tz & 1) * L::XB);
+        return (T*)(ring + ((qb + (tz >> 1)) % SW_NS) * L::BYTES + (tz & 1) * L::XB);
       };
       auto PB = [&](int z) -> const T* { return (const T*)((const unsigned char*)PX(z) + 2 * L::XB - 0); };
       auto PF = [&](int z) -> const unsigned char* {
         const int tz = z - z0 + 2;
-        return ring + ((qb + (tz >> 1)) & (SW_NS - 1)) * L::BYTES + 4 * L::XB + (tz & 1) * L::FB;
+        return ring + ((qb + (tz >> 1)) % SW_NS) * L::BYTES + 4 * L::XB + (tz & 1) * L::FB;
       };
       for (int s = 0; s < S; ++s) {
         if (!sw_wait_upto(bar0, waited, qb + min(s + 1, G - 1))) *sfail = 1;
@@ -512,14 +512,14 @@ __device__ __noinline__ bool ph_restrict3d(const Hier<T>& Hc, int l, const Ctx& 
             const int z = z0 + 2 * s + h;
             auto base = [&](int zz) {
               const int tz = zz - z0 + 2;
-              return ring + ((qb + (tz >> 1)) & (SW_NS - 1)) * L::BYTES + (tz & 1) * L::XB;
+              return ring + ((qb + (tz >> 1)) % SW_NS) * L::BYTES + (tz & 1) * L::XB;
             };
             const T* Xc = (const T*)base(z);
             const T* Xm = (const T*)base(z - 1);
             const T* Xp = (const T*)base(z + 1);
             const T* B = (const T*)(base(z) + 2 * L::XB);
             const int tz = z - z0 + 2;
-            const unsigned char* F = ring + ((qb + (tz >> 1)) & (SW_NS - 1)) * L::BYTES + 4 * L::XB + (tz & 1) * L::FB;
+            const unsigned char* F = ring + ((qb + (tz >> 1)) % SW_NS) * L::BYTES + 4 * L::XB + (tz & 1) * L::FB;
             const bool kin = z > 0 && z < n2 - 1;
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
@@ -553,8 +553,9 @@ __device__ __noinline__ bool ph_restrict3d(const Hier<T>& Hc, int l, const Ctx& 
           ok = false;
           break;
         }
-        // copies below s + 1 are read by no later step: refill their slots
-        if (t == 0) iss.run(sw, n2, w, nw, maps, ring, bar0, qb + s + 1 + SW_NS, 2);
+        // copies below s + 1 (all of the item's after its last step) are read
+        // by no later step: refill their slots
+        if (t == 0) iss.run(sw, n2, w, nw, maps, ring, bar0, qb + (s == S - 1 ? G : s + 1) + SW_NS, 2);
       }
       qb += G;
     }

@@ -90,7 +90,7 @@ EXPORTS = ["eb_status_str", "eb_last_error", "eb_geom_build", "eb_geom_query", "
            "eb_poisson_residual_noalloc", "eb_poisson_solve_batched", "eb_server_opts_default", "eb_server_create",
            "eb_server_submit", "eb_server_poll", "eb_server_wait", "eb_server_query", "eb_server_destroy",
            "eb_amr_setup", "eb_amr_query", "eb_amr_residual", "eb_amr_solve", "eb_amr_kernel_stats",
-           "eb_amr_destroy"]
+           "eb_amr_destroy", "eb_device_fma_rates"]
 
 
 def lib_path() -> str:
@@ -151,6 +151,8 @@ def load(build_if_missing: bool = False):
         lib.eb_amr_destroy.argtypes = [P]
         lib.eb_amr_kernel_stats.restype = C.c_int
         lib.eb_amr_kernel_stats.argtypes = [P, C.POINTER(C.c_double)]
+        lib.eb_device_fma_rates.restype = C.c_int
+        lib.eb_device_fma_rates.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         lib.eb_server_opts_default.argtypes = [C.POINTER(ServerOpts)]
         lib.eb_server_create.restype = C.c_int
         lib.eb_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(P)]
@@ -282,6 +284,13 @@ def eb_poisson_solve(handle, rhs, sigma, phi, stream=None) -> dict:
                 bnorm=info.bnorm, kernel_launches=info.kernel_launches, kernel_ms=info.kernel_ms,
                 bottom=BOTTOM_NAMES.get(info.bottom, "none"), levels=info.levels,
                 sweep_levels=info.sweep_levels)
+
+
+def device_fma_rates(device: int = 0):
+    """Measured FP64 and FP32 fused multiply-add rates of a device, TFLOP/s."""
+    f64, f32 = C.c_double(), C.c_double()
+    _check(load().eb_device_fma_rates(int(device), C.byref(f64), C.byref(f32)), "eb_device_fma_rates")
+    return f64.value, f32.value
 
 
 def eb_poisson_profile(handle, kernel: int, reps: int, stream=None):
