@@ -164,18 +164,17 @@ __device__ __noinline__ void sw_wall_stencil(const SwGrid<T>& g, const T* Xm, co
   dg_out = dg;
 }
 
-// Relaxes cell (i, j, k) at box position (lx, ly) of planes Xc (k), Xm, Xp
-// with right-hand side B and flags F when it is a regular cell of phase p
-// (flag value pbit = 1 << p); kin: k is not on a wall plane.  Cells off the
-// grid, cut cells and cells of the other phase or without an unknown are
-// left alone.
+// Relaxes cell (i, j, k), at index e of the x / b boxes and ef of the flag
+// box, of planes Xc (k), Xm, Xp with right-hand side B and flags F when it
+// is a regular cell of phase p (flag value pbit = 1 << p); kin: k is not on
+// a wall plane.  Cells off the grid, cut cells and cells of the other phase
+// or without an unknown are left alone.
 template <class T>
-__device__ __forceinline__ void sw_relax(const SwGrid<T>& g, T* Xc, const T* Xm, const T* Xp, const T* B,
-                                         const unsigned char* F, unsigned pbit, int i, int j, int k, bool kin, int lx,
-                                         int ly) {
+__device__ __forceinline__ void sw_relax_at(const SwGrid<T>& g, T* Xc, const T* Xm, const T* Xp, const T* B,
+                                            const unsigned char* F, unsigned pbit, int i, int j, int k, bool kin,
+                                            int e, int ef) {
   if ((unsigned)i >= (unsigned)g.n0 || (unsigned)j >= (unsigned)g.n1) return;
-  if ((F[ly * SW_FBX + lx + (SW_FHX - SW_HX)] & 7u) != pbit) return;  // regular: one phase, no sparse row
-  const int e = ly * SW_BX + lx;
+  if ((F[ef] & 7u) != pbit) return;  // regular: one phase, no sparse row
   if (kin && (unsigned)(i - 1) < (unsigned)(g.n0 - 2) && (unsigned)(j - 1) < (unsigned)(g.n1 - 2)) {
     const T sum = ((((Xc[e - 1] + Xc[e + 1]) + Xc[e - SW_BX]) + Xc[e + SW_BX]) + Xm[e]) + Xp[e];
     Xc[e] = (g.h2e * B[e] + sum) * inv_count(6, T(0));
@@ -338,6 +337,24 @@ __device__ __noinline__ bool ph_sweep3d(const Hier<T>& Hc, int l, const Ctx& c, 
     const int t = threadIdx.x;
     const int tr = t >> 4, tm = t & 15;
     const int tring = (int)blockDim.x - 1 - t;
+    const int ly_in = SW_HY + tr;                         // this thread's tile row in the boxes
+    const int e_in = ly_in * SW_BX + SW_HX + 2 * tm;      // its even-parity cell of the row
+    const int f_in = ly_in * SW_FBX + SW_FHX + 2 * tm;    // the same in the flag box
+    // the ring cell of this thread, if any: box position without the colour offset
+    int rq_ly = 0, rq_lx = 0, rq_h = -1;
+    {
+      const int tq = tring < 66 ? tring : tring - 66;
+      if (tring < 132) {
+        rq_h = tring < 66 ? 0 : 1;
+        if (tq < 34) {  // ring rows above and below the tile, 17 red cells each
+          rq_ly = tq < 17 ? SW_HY - 1 : SW_HY + SW_TY;
+          rq_lx = SW_HX - 1 + 2 * (tq < 17 ? tq : tq - 17);  // lx = rq_lx + ((j + r + 1) & 1)
+        } else {       // the ring cell at the left or right end of a tile row
+          rq_ly = SW_HY + tq - 34;
+          rq_lx = -1;  // lx = 3 or 36 by the colour
+        }
+      }
+    }
     int qb = 0, waited = 0;
     for (int k = 0; k < K && ok; ++k) {
       SwItem<T> it;
@@ -347,46 +364,39 @@ __device__ __noinline__ bool ph_sweep3d(const Hier<T>& Hc, int l, const Ctx& c, 
       T* const alt = sw.alt[it.p];
       const int x0 = it.x0, y0 = it.y0, z0 = it.z0, z1 = it.z1;
       const int G = (z1 - z0 + 4) >> 1, S = ((z1 - z0) >> 1) + 2;
-      // plane z of this item: its x, b and flag boxes in the ring
-      auto PX = [&](int z) -> T* {
-        const int tz = z - z0 + 2;
-        return (T*)(ring + ((qb + (tz >> 1)) % SW_NS) * L::BYTES + (tz & 1) * L::XB);
-      };
-      auto PB = [&](int z) -> const T* { return (const T*)((const unsigned char*)PX(z) + 2 * L::XB - 0); };
-      auto PF = [&](int z) -> const unsigned char* {
-        const int tz = z - z0 + 2;
-        return ring + ((qb + (tz >> 1)) % SW_NS) * L::BYTES + 4 * L::XB + (tz & 1) * L::FB;
-      };
+      const int j_in = y0 + tr;
+      const int i_even = x0 + 2 * tm;  // the cell at e_in
+      const int rq_j = y0 - SW_HY + rq_ly;
+      // copy g of this item sits in slot (qb + g) % SW_NS; slot pointers of
+      // copies s - 1, s, s + 1 rotate by one per step
+      int sl0 = (qb + SW_NS - 1) % SW_NS, sl1 = qb % SW_NS, sl2 = (qb + 1) % SW_NS;
       for (int s = 0; s < S; ++s) {
         if (!sw_wait_upto(bar0, waited, qb + min(s + 1, G - 1))) *sfail = 1;
         const int a = z0 - 1 + 2 * s;
-        // red cells of planes a, a + 1 on the tile and its ring
+        // planes a - 3, a - 2 in copy s - 1; a - 1, a in copy s; a + 1, a + 2 in copy s + 1
+        unsigned char* const C0 = ring + sl0 * L::BYTES;
+        unsigned char* const C1 = ring + sl1 * L::BYTES;
+        unsigned char* const C2 = ring + sl2 * L::BYTES;
+        // red cells of planes a (copy s, second plane) and a + 1 (copy s + 1, first)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int r = a + h;
           if (r > z1 || r < 0 || r >= n2) continue;
-          T* Xc = PX(r);
-          const T *Xm = PX(r - 1), *Xp = PX(r + 1), *B = PB(r);
-          const unsigned char* F = PF(r);
+          unsigned char* const Pc = h == 0 ? C1 + L::XB : C2;
+          const unsigned char* const Pm = h == 0 ? C1 : C1 + L::XB;
+          const unsigned char* const Pp = h == 0 ? C2 : C2 + L::XB;
+          const unsigned char* const F = h == 0 ? C1 + 4 * L::XB + L::FB : C2 + 4 * L::XB;
+          T* Xc = (T*)Pc;
+          const T *Xm = (const T*)Pm, *Xp = (const T*)Pp, *B = (const T*)(Pc + 2 * L::XB);
           const bool kin = r > 0 && r < n2 - 1;
           {
-            const int j = y0 + tr;
-            const int lx = SW_HX + ((j + r) & 1) + 2 * tm;
-            sw_relax(g, Xc, Xm, Xp, B, F, pbit, x0 - SW_HX + lx, j, r, kin, lx, SW_HY + tr);
+            const int o1 = (j_in + r) & 1;
+            sw_relax_at(g, Xc, Xm, Xp, B, F, pbit, i_even + o1, j_in, r, kin, e_in + o1, f_in + o1);
           }
-          const int tq = tring - 66 * h;
-          if (tq >= 0 && tq < 66) {
-            int j, lx, ly;
-            if (tq < 34) {  // ring rows above and below the tile
-              ly = tq < 17 ? SW_HY - 1 : SW_HY + SW_TY;
-              j = y0 - SW_HY + ly;
-              lx = SW_HX - 1 + ((j + r + 1) & 1) + 2 * (tq < 17 ? tq : tq - 17);
-            } else {  // the ring cell at the left or right end of a tile row
-              ly = SW_HY + tq - 34;
-              j = y0 - SW_HY + ly;
-              lx = ((j + r) & 1) ? SW_HX - 1 : SW_HX + SW_TX;
-            }
-            sw_relax(g, Xc, Xm, Xp, B, F, pbit, x0 - SW_HX + lx, j, r, kin, lx, ly);
+          if (rq_h == h) {
+            const int lx = rq_lx >= 0 ? rq_lx + ((rq_j + r + 1) & 1) : (((rq_j + r) & 1) ? SW_HX - 1 : SW_HX + SW_TX);
+            sw_relax_at(g, Xc, Xm, Xp, B, F, pbit, x0 - SW_HX + lx, rq_j, r, kin, rq_ly * SW_BX + lx,
+                        rq_ly * SW_FBX + lx + (SW_FHX - SW_HX));
           }
         }
         fence_async_smem();
@@ -395,18 +405,21 @@ __device__ __noinline__ bool ph_sweep3d(const Hier<T>& Hc, int l, const Ctx& c, 
           ok = false;
           break;
         }
-        // black cells of planes a - 1, a on the tile
+        // black cells of planes a - 1 (copy s, first plane) and a (copy s, second)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int q = a - 1 + h;
           if (q < z0 || q >= z1) continue;
-          const int j = y0 + tr;
-          const int lx = SW_HX + ((j + q + 1) & 1) + 2 * tm;
-          sw_relax(g, PX(q), PX(q - 1), PX(q + 1), PB(q), PF(q), pbit, x0 - SW_HX + lx, j, q,
-                   q > 0 && q < n2 - 1, lx, SW_HY + tr);
+          unsigned char* const Pc = h == 0 ? C1 : C1 + L::XB;
+          const unsigned char* const Pm = h == 0 ? C0 + L::XB : C1;
+          const unsigned char* const Pp = h == 0 ? C1 + L::XB : C2;
+          const unsigned char* const F = C1 + 4 * L::XB + h * L::FB;
+          const int o1 = (j_in + q + 1) & 1;
+          sw_relax_at(g, (T*)Pc, (const T*)Pm, (const T*)Pp, (const T*)(Pc + 2 * L::XB), F, pbit, i_even + o1, j_in,
+                      q, q > 0 && q < n2 - 1, e_in + o1, f_in + o1);
         }
-        // store planes a - 3, a - 2 (final since the last step): the tile's
-        // unknowns of this phase, both colours, cut cells as given
+        // store planes a - 3, a - 2 (copy s - 1; final since the last step):
+        // the tile's unknowns of this phase, both colours, cut cells as given
         {
           const int rx = t & 31, i = x0 + rx;
           if (i < g.n0)
@@ -414,19 +427,21 @@ __device__ __noinline__ bool ph_sweep3d(const Hier<T>& Hc, int l, const Ctx& c, 
             for (int h = 0; h < 2; ++h) {
               const int q = a - 3 + h;
               if (q < z0 || q >= z1) continue;
-              const T* X = PX(q);
-              const unsigned char* F = PF(q);
+              const T* X = (const T*)(C0 + h * L::XB);
+              const unsigned char* F = C0 + 4 * L::XB + h * L::FB;
+              T* dst = alt + ((long long)q * g.n1 + y0) * g.n0 + i;
               for (int ry = t >> 5; ry < SW_TY; ry += (int)(blockDim.x >> 5)) {
-                const int j = y0 + ry;
-                if (j >= g.n1) break;
-                const int ly = SW_HY + ry, lx = SW_HX + rx;
-                if (F[ly * SW_FBX + lx + (SW_FHX - SW_HX)] & pbit)
-                  alt[((long long)q * g.n1 + j) * g.n0 + i] = X[ly * SW_BX + lx];
+                if (y0 + ry >= g.n1) break;
+                const int ly = SW_HY + ry;
+                if (F[ly * SW_FBX + SW_FHX + rx] & pbit) dst[(long long)ry * g.n0] = X[ly * SW_BX + SW_HX + rx];
               }
             }
         }
         // copies below s - 1 are read by no later step: refill their slots
         if (t == 0) iss.run(sw, n2, w, nw, maps, ring, bar0, qb + max(0, s - 1) + SW_NS, 2);
+        sl0 = sl1;
+        sl1 = sl2;
+        sl2 = sl2 + 1 == SW_NS ? 0 : sl2 + 1;
       }
       qb += G;
     }
@@ -503,23 +518,27 @@ __device__ __noinline__ bool ph_restrict3d(const Hier<T>& Hc, int l, const Ctx& 
       const int G = (z1 - z0 + 4) >> 1, S = (z1 - z0) >> 1;
       T* const cb = co.b[p];
       T* const cx = co.x[p];
+      // copies s, s + 1, s + 2 hold planes z0 + 2s - 2 .. z0 + 2s + 3
+      int sl0 = qb % SW_NS, sl1 = (qb + 1) % SW_NS, sl2 = (qb + 2) % SW_NS;
       for (int s = 0; s < S; ++s) {
         if (!sw_wait_upto(bar0, waited, qb + min(s + 2, G - 1))) *sfail = 1;
+        const unsigned char* const C0 = ring + sl0 * L::BYTES;
+        const unsigned char* const C1 = ring + sl1 * L::BYTES;
+        const unsigned char* const C2 = ring + sl2 * L::BYTES;
         T acc = T(0);
         if (tin) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
+            // plane z0 + 2s (copy s + 1, first) then z0 + 2s + 1 (copy s + 1, second)
             const int z = z0 + 2 * s + h;
-            auto base = [&](int zz) {
-              const int tz = zz - z0 + 2;
-              return ring + ((qb + (tz >> 1)) % SW_NS) * L::BYTES + (tz & 1) * L::XB;
-            };
-            const T* Xc = (const T*)base(z);
-            const T* Xm = (const T*)base(z - 1);
-            const T* Xp = (const T*)base(z + 1);
-            const T* B = (const T*)(base(z) + 2 * L::XB);
-            const int tz = z - z0 + 2;
-            const unsigned char* F = ring + ((qb + (tz >> 1)) % SW_NS) * L::BYTES + 4 * L::XB + (tz & 1) * L::FB;
+            const unsigned char* const Pc = C1 + h * L::XB;
+            const unsigned char* const Pm = h == 0 ? C0 + L::XB : C1;
+            const unsigned char* const Pp = h == 0 ? C1 + L::XB : C2;
+            const T* Xc = (const T*)Pc;
+            const T* Xm = (const T*)Pm;
+            const T* Xp = (const T*)Pp;
+            const T* B = (const T*)(Pc + 2 * L::XB);
+            const unsigned char* F = C1 + 4 * L::XB + h * L::FB;
             const bool kin = z > 0 && z < n2 - 1;
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
@@ -542,7 +561,7 @@ __device__ __noinline__ bool ph_restrict3d(const Hier<T>& Hc, int l, const Ctx& 
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         if (tin && hx == 0) {
           const int ci = (x0 >> 1) + ccx, cj = (y0 >> 1) + ccy, ck = (z0 >> 1) + s;
-          if (ci < cn0 && cj < cn1) {
+          if (ci < cn0 && cj < cn1 && cb) {
             const long long C = ((long long)ck * cn1 + cj) * cn0 + ci;
             cb[C] = ((co.flags[C] >> p) & 1u) ? acc * scale : T(0);
             cx[C] = T(0);
@@ -556,6 +575,9 @@ __device__ __noinline__ bool ph_restrict3d(const Hier<T>& Hc, int l, const Ctx& 
         // copies below s + 1 (all of the item's after its last step) are read
         // by no later step: refill their slots
         if (t == 0) iss.run(sw, n2, w, nw, maps, ring, bar0, qb + (s == S - 1 ? G : s + 1) + SW_NS, 2);
+        sl0 = sl1;
+        sl1 = sl2;
+        sl2 = sl2 + 1 == SW_NS ? 0 : sl2 + 1;
       }
       qb += G;
     }
