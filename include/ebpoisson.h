@@ -189,9 +189,12 @@ typedef struct {
                        events on the stream they ran on; 0 on the multi-launch paths */
   int bottom;       /* how the coarsest level was solved: EB_BOTTOM_* */
   int levels;       /* multigrid levels of the V-cycle */
-  int sweep_levels; /* levels relaxed by tile-streamed sweeps (FP32 3D levels from 128^3 cells with an x
-                       extent a multiple of 16: both colours in one pass over the level, tiles staged
-                       in shared memory by TMA); the others use one pass per colour */
+  int sweep_levels; /* levels relaxed by tile-streamed sweeps (FP32 3D levels of at least 2^25 cells,
+                       x extent a multiple of 16, y and z multiples of 4: both colours in one pass
+                       over the level, tiles staged in shared memory by TMA); the others use one
+                       pass per colour.  The environment variable EBP_SWEEP=0 turns them off,
+                       EBP_SWEEP_MIN_CELLS=n moves the threshold, EBP_SWEEP_RESTRICT=1 also
+                       restricts these levels by a tile-streamed residual + restriction pass */
 } eb_solve_info;
 
 /* Bottom solves of the V-cycle (Sec. 3.3.2 solves the coarsest level directly

@@ -23,11 +23,15 @@ constexpr long long BAR_WAIT_CYCLES = 4000000000LL;  // ~2 s of SM clock: a barr
 // bytes); two planes per copy, a ring of SW_NS two-plane slots.
 constexpr int SW_TX = 32, SW_TY = 32, SW_HX = 4, SW_BX = SW_TX + 2 * SW_HX, SW_HY = 2, SW_FHX = 16, SW_FBX = 64;
 constexpr int SW_NS = 6;  // three slots in use, three copies in flight
-constexpr int SW_HEAD = 128;  // mbarriers and a failure flag before the ring
+// shared-memory head before the ring: SW_NS mbarriers, a failure flag, and
+// from SW_QOFF a queue of SW_QN item indices (the order the items arrive in)
+constexpr int SW_QOFF = 64, SW_QN = 8, SW_HEAD = 128;
+static_assert(8 * SW_NS + 4 <= SW_QOFF && SW_QOFF + 4 * SW_QN <= SW_HEAD, "sweep head layout");
 
 template <class T>
 struct SweepLev {
-  int on;       // 1: the level relaxes and restricts by tile-streamed passes, x -> alt
+  int on;       // 1: the level relaxes by tile-streamed sweeps, x -> alt
+  int rs;       // 1: and restricts by the tile-streamed residual + restriction
   int zc;       // planes per z-chunk (a multiple of 4)
   int ntx, nty, nzc, nitems;  // tiles per axis, z-chunks, gas-phase work items (tile x chunk)
   int n1items;  // dielectric-phase work items: the items whose boxes hold dielectric unknowns
@@ -35,6 +39,10 @@ struct SweepLev {
   T* alt[2];    // the second buffer per phase
   const void* maps;    // 7 tensor maps (128 bytes each): x[buf][phase] (buf 0 = x, 1 = alt), b[phase], flags
   const int* list1;    // [n1items] item indices of the dielectric-phase items
+  // per pass kind (0: sweep, 1: residual + restriction) a ticket counter
+  // handing out the pass's items and a count of the CTAs done with it; both
+  // zero between passes (the last CTA done resets them)
+  int* tick;    // [4]: ticket 0, done 0, ticket 1, done 1
 };
 
 template <class T>
@@ -810,7 +818,6 @@ template <class T>
 __device__ bool ph_smooth_grid(const Hier<T>& H, int l, int nu, const Ctx& c) {
   const Op<T>& o = H.op[l];
   if (!H.sw[l].on || c.local || c.gsize < 2) return ph_smooth(o, nu, c, l);
-  extern __shared__ __align__(128) unsigned char sw_dyn[];
   const long long rr = 2 * o.nirr_red, rn = 2 * o.nirr;
   for (int s = 0; s < nu; ++s) {
     if (rr > 0) {
@@ -819,7 +826,7 @@ __device__ bool ph_smooth_grid(const Hier<T>& H, int l, int nu, const Ctx& c) {
       ph_write(o, 0, rr, c);
       if (!c.sync((l << 4) | 4)) return false;
     }
-    if (!ph_sweep3d(H, l, c, sw_dyn)) return false;
+    if (!ph_sweep3d(H, l, c)) return false;
     if (!c.sync((l << 4) | 13)) return false;
     if (rn > rr) {
       ph_rows(H.op[l], rr, rn, 0, c);  // H.op[l]: the swapped view, x now the new iterate
@@ -1089,10 +1096,9 @@ __device__ bool vcycle_dev(const Hier<T>& H, const Op<T>* lop, const Ctx& G) {
       ph_rows(o, 0, 2 * o.nirr, 1, G);
       if (!G.sync((l << 4) | 5)) return false;
     }
-    if (H.sw[l].on && G.gsize >= 2 && o.n[0] == 2 * H.op[l + 1].n[0] && o.n[1] == 2 * H.op[l + 1].n[1] &&
+    if (H.sw[l].on && H.sw[l].rs && G.gsize >= 2 && o.n[0] == 2 * H.op[l + 1].n[0] && o.n[1] == 2 * H.op[l + 1].n[1] &&
         o.n[2] == 2 * H.op[l + 1].n[2]) {
-      extern __shared__ __align__(128) unsigned char rs_dyn[];
-      if (!ph_restrict3d(H, l, G, rs_dyn)) return false;
+      if (!ph_restrict3d(H, l, G)) return false;
     } else {
       ph_restrict(o, H.op[l + 1], G);
     }
@@ -1315,36 +1321,35 @@ __global__ void __launch_bounds__(PT, 1) k_solve_batch(const BatchItem<T>* __res
   solve_group(it.H, it.F, it.ctl, it.B, (int)blockIdx.x - it.start, it.size);
 }
 
-// Setup of the tile-streamed passes: bit `it` of has1 is set when the boxes
-// item `it` loads (its tile with the halo, planes z0 - 2 .. z1 + 1) hold a
-// dielectric unknown, or when the coarse cells it restricts onto do (cflags
-// of the level below, may be null); one CTA per item.
-__global__ void k_sweep_has1(const uint8_t* __restrict__ flags, int n0, int n1, int n2, int ntx, int nty, int zc,
-                             int nitems, const uint8_t* __restrict__ cflags, int cn0, int cn1, int cn2,
-                             unsigned* has1) {
-  const int it = blockIdx.x;
-  if (it >= nitems) return;
-  const int tx = it % ntx, r = it / ntx;
-  const int x0 = tx * SW_TX, y0 = (r % nty) * SW_TY, z0 = (r / nty) * zc, z1 = min(z0 + zc, n2);
-  const int xa = max(x0 - SW_HX, 0), xb = min(x0 + SW_TX + SW_HX, n0);
-  const int ya = max(y0 - SW_HY, 0), yb = min(y0 + SW_TY + SW_HY, n1);
-  const int za = max(z0 - 2, 0), zb = min(z1 + 2, n2);
-  const long long nx = xb - xa, ny = yb - ya, nz = zb - za;
+// Setup of the tile-streamed passes: one CTA per (tile, plane).  Entry
+// t * n2 + z of has1 is set when the tile's box (the tile with the halo) holds
+// a dielectric unknown in fine plane z; entry ntiles * n2 + t * cn2 + z when
+// the coarse cells under the tile do in coarse plane z (cflags of the level
+// below, may be null).  The host ORs the planes of each item from these.
+__global__ void k_sweep_has1(const uint8_t* __restrict__ flags, int n0, int n1, int n2, int ntx, int nty,
+                             const uint8_t* __restrict__ cflags, int cn0, int cn1, int cn2, uint8_t* has1) {
+  const int ntiles = ntx * nty;
+  const long long nfine = (long long)ntiles * n2;
+  const long long b = blockIdx.x;
   int found = 0;
-  for (long long e = threadIdx.x; e < nx * ny * nz && !found; e += blockDim.x) {
-    const long long x = xa + e % nx, y = ya + (e / nx) % ny, z = za + e / (nx * ny);
-    if (flags[(z * n1 + y) * n0 + x] & 2) found = 1;
-  }
-  if (cflags) {
+  if (b < nfine) {
+    const int t = (int)(b / n2), z = (int)(b % n2);
+    const int x0 = (t % ntx) * SW_TX, y0 = (t / ntx) * SW_TY;
+    const int xa = max(x0 - SW_HX, 0), xb = min(x0 + SW_TX + SW_HX, n0);
+    const int ya = max(y0 - SW_HY, 0), yb = min(y0 + SW_TY + SW_HY, n1);
+    const int nx = xb - xa, ny = yb - ya;
+    for (int e = threadIdx.x; e < nx * ny && !found; e += blockDim.x)
+      if (flags[((long long)z * n1 + ya + e / nx) * n0 + xa + e % nx] & 2) found = 1;
+  } else if (cflags) {
+    const long long r = b - nfine;
+    const int t = (int)(r / cn2), z = (int)(r % cn2);
+    const int x0 = (t % ntx) * SW_TX, y0 = (t / ntx) * SW_TY;
     const int cxa = x0 / 2, cxb = min((x0 + SW_TX) / 2, cn0), cya = y0 / 2, cyb = min((y0 + SW_TY) / 2, cn1);
-    const int cza = z0 / 2, czb = min(z1 / 2, cn2);
-    const long long mx = max(cxb - cxa, 0), my = max(cyb - cya, 0), mz = max(czb - cza, 0);
-    for (long long e = threadIdx.x; e < mx * my * mz && !found; e += blockDim.x) {
-      const long long x = cxa + e % mx, y = cya + (e / mx) % my, z = cza + e / (mx * my);
-      if (cflags[(z * cn1 + y) * cn0 + x] & 2) found = 1;
-    }
+    const int mx = max(cxb - cxa, 0), my = max(cyb - cya, 0);
+    for (int e = threadIdx.x; e < mx * my && !found; e += blockDim.x)
+      if (cflags[((long long)z * cn1 + cya + e / mx) * cn0 + cxa + e % mx] & 2) found = 1;
   }
-  if (__syncthreads_or(found) && threadIdx.x == 0) atomicOr(&has1[it >> 5], 1u << (it & 31));
+  if (__syncthreads_or(found) && threadIdx.x == 0) has1[b] = 1;
 }
 
 // ------------------------------------------------------------ bottom inverse
@@ -1608,7 +1613,6 @@ __global__ void __launch_bounds__(PT) k_dense_phase(Op<T> o, int colour) {
 template <class T>
 __global__ void __launch_bounds__(PT, 1) k_sweep_phase(const Hier<T>* __restrict__ Hg, int l, int* err) {
   __shared__ Hier<T> H;
-  extern __shared__ __align__(128) unsigned char dyn[];
   const int* src = (const int*)Hg;
   int* dst = (int*)&H;
   for (int i = threadIdx.x; i < (int)(sizeof(Hier<T>) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
@@ -1617,7 +1621,7 @@ __global__ void __launch_bounds__(PT, 1) k_sweep_phase(const Hier<T>* __restrict
   c.gsize = (int)gridDim.x;
   c.gcta = (int)blockIdx.x;
   c.B.err = err;
-  ph_sweep3d(H, l, c, dyn);
+  ph_sweep3d(H, l, c);
 }
 
 // the streamed residual + restriction of level l on its own (cut-cell
@@ -1625,7 +1629,6 @@ __global__ void __launch_bounds__(PT, 1) k_sweep_phase(const Hier<T>* __restrict
 template <class T>
 __global__ void __launch_bounds__(PT, 1) k_restrict3d_phase(const Hier<T>* __restrict__ Hg, int l, int* err) {
   __shared__ Hier<T> H;
-  extern __shared__ __align__(128) unsigned char dyn[];
   const int* src = (const int*)Hg;
   int* dst = (int*)&H;
   for (int i = threadIdx.x; i < (int)(sizeof(Hier<T>) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
@@ -1634,7 +1637,7 @@ __global__ void __launch_bounds__(PT, 1) k_restrict3d_phase(const Hier<T>* __res
   c.gsize = (int)gridDim.x;
   c.gcta = (int)blockIdx.x;
   c.B.err = err;
-  ph_restrict3d(H, l, c, dyn);
+  ph_restrict3d(H, l, c);
 }
 
 template <class T>

@@ -288,6 +288,7 @@ struct eb_poisson {
   int sweep_bytes = 0;           // their shared memory per CTA
   int sweep_ns = 0;              // ring slots
   int sweep_first = -1;          // the finest of them
+  std::vector<int*> sweep_ticks;  // their ticket counters (4 ints per level)
   int smem_bytes = 0;  // dynamic shared memory of the persistent kernel
   cudaEvent_t kev[2] = {nullptr, nullptr};  // bracket the persistent kernel
   double kernel_ms = 0.0;                   // its device time in the last call
@@ -473,17 +474,47 @@ static bool tmap3(CUtensorMap* m, CUtensorMapDataType type, int esize, const voi
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-static constexpr long long SW_MIN_CELLS = 1LL << 21;  // levels from 128^3 up stream their passes
+// Levels of at least 2^25 cells (about 322^3) relax by tile-streamed sweeps:
+// measured on a GB300 at 384^3 a streamed sweep takes 0.39 ms against 0.53 ms
+// for the two colour passes, at 256^3 0.19 ms against 0.17 ms.  The streamed
+// residual + restriction is slower than the block restriction at both sizes
+// (0.36 / 0.31 ms, 0.19 / 0.10 ms) and is used only on request
+// (EBP_SWEEP_RESTRICT=1).
+static constexpr long long SW_MIN_CELLS = 1LL << 25;
+
+// Items of a level cut into z-chunks of zc planes: tile t = it % ntiles,
+// chunk it / ntiles.  An item holds dielectric unknowns when its tile's box
+// does in one of the planes it loads (z0 - 2 .. z1 + 1) or the coarse cells
+// under it do in one of its coarse planes (z0 / 2 .. z1 / 2 - 1); plane1
+// gives that per (tile, plane), fine planes first (ntiles x n2), then coarse
+// (ntiles x cn2, cn2 = 0 without a coarse level).
+static std::vector<int> sweep_items1(const std::vector<uint8_t>& plane1, int ntiles, int n2, int cn2, int zc) {
+  std::vector<int> out;
+  const int nzc = (n2 + zc - 1) / zc;
+  for (int q = 0; q < nzc; ++q) {
+    const int z0 = q * zc, z1 = std::min(z0 + zc, n2);
+    for (int t = 0; t < ntiles; ++t) {
+      bool has = false;
+      for (int z = std::max(z0 - 2, 0); z < std::min(z1 + 2, n2) && !has; ++z) has = plane1[(size_t)t * n2 + z] != 0;
+      for (int z = z0 / 2; z < std::min(z1 / 2, cn2) && !has; ++z)
+        has = plane1[(size_t)ntiles * n2 + (size_t)t * cn2 + z] != 0;
+      if (has) out.push_back(q * ntiles + t);
+    }
+  }
+  return out;
+}
 
 // z-chunk of a level for `workers` CTAs: the least of (rounds of items per
-// CTA) x (steps per item: two planes each, two more for the ends), over
-// chunks of 4..n2 planes in steps of 4.
-static int sweep_chunk(const int n[3], int workers) {
+// CTA, the dielectric phase's items included) x (steps per item: two planes
+// each, two more for the ends), over chunks of 4..n2 planes in steps of 4.
+static int sweep_chunk(const int n[3], int workers, const std::vector<uint8_t>* plane1, int cn2) {
   const long long ntx = (n[0] + SW_TX - 1) / SW_TX, nty = (n[1] + SW_TY - 1) / SW_TY;
   long long best = -1;
   int zc_best = 4;
   for (int zc = 4; zc <= n[2] + 3; zc += 4) {
-    const long long nzc = (n[2] + zc - 1) / zc, items = ntx * nty * nzc;
+    const long long nzc = (n[2] + zc - 1) / zc;
+    long long items = ntx * nty * nzc;
+    if (plane1) items += (long long)sweep_items1(*plane1, (int)(ntx * nty), n[2], cn2, zc).size();
     const long long rounds = (items + workers - 1) / workers;
     const long long cost = rounds * (zc / 2 + 2);
     if (best < 0 || cost < best) {
@@ -510,6 +541,8 @@ static eb_status setup_sweeps(eb_poisson* P, std::vector<Op<T>>& ops, Hier<T>& H
   const int workers = std::max(1, nsm - 1);
   long long min_cells = SW_MIN_CELLS;  // EBP_SWEEP_MIN_CELLS lowers it (tests run small grids through the path)
   if (const char* env = std::getenv("EBP_SWEEP_MIN_CELLS")) min_cells = std::max(1LL, std::atoll(env));
+  int restrict_streamed = 0;
+  if (const char* env = std::getenv("EBP_SWEEP_RESTRICT")) restrict_streamed = std::atoi(env) != 0;
   eb_status st = EB_OK;
   for (int l = 0; l < H.lc; ++l) {
     Op<T>& o = ops[l];
@@ -517,9 +550,30 @@ static eb_status setup_sweeps(eb_poisson* P, std::vector<Op<T>>& ops, Hier<T>& H
     SweepLev<T>& sw = H.sw[l];
     const DevLevel& Lv = P->G->L[l];
     const int two = o.x[1] != nullptr;
-    sw.zc = sweep_chunk(o.n, workers);
     sw.ntx = (o.n[0] + SW_TX - 1) / SW_TX;
     sw.nty = (o.n[1] + SW_TY - 1) / SW_TY;
+    // where the dielectric phase's unknowns sit, per (tile, plane)
+    std::vector<uint8_t> plane1;
+    const bool has_c = l + 1 < (int)P->G->L.size();
+    const int cn2 = has_c ? P->G->L[l + 1].g.n[2] : 0;
+    if (two) {
+      const int ntiles = sw.ntx * sw.nty;
+      const size_t nb = (size_t)ntiles * (o.n[2] + cn2);
+      std::vector<void*> tmp;
+      uint8_t* d_p1 = (uint8_t*)dev_alloc(tmp, nb, nullptr, &st);
+      if (st != EB_OK) return st;
+      cudaMemsetAsync(d_p1, 0, nb, P->s);
+      const uint8_t* cfl = has_c ? P->G->L[l + 1].flags : nullptr;
+      const int* cn = has_c ? P->G->L[l + 1].g.n : o.n;
+      k_sweep_has1<<<(unsigned)(cfl ? nb : (size_t)ntiles * o.n[2]), 256, 0, P->s>>>(
+          Lv.flags, o.n[0], o.n[1], o.n[2], sw.ntx, sw.nty, cfl, cn[0], cn[1], cn2, d_p1);
+      plane1.resize(nb);
+      cudaError_t e = cudaMemcpyAsync(plane1.data(), d_p1, nb, cudaMemcpyDeviceToHost, P->s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
+      for (void* q : tmp) cudaFree(q);
+      if (e != cudaSuccess) return cuda_fail(e, "sweep setup");
+    }
+    sw.zc = sweep_chunk(o.n, workers, two ? &plane1 : nullptr, cn2);
     sw.nzc = (o.n[2] + sw.zc - 1) / sw.zc;
     sw.nitems = sw.ntx * sw.nty * sw.nzc;
     CUtensorMap maps[7];
@@ -533,6 +587,10 @@ static eb_status setup_sweeps(eb_poisson* P, std::vector<Op<T>>& ops, Hier<T>& H
     }
     CUtensorMap* dmaps = (CUtensorMap*)dev_alloc(P->allocs, sizeof(CUtensorMap) * 7, &P->bytes, &st);
     if (st != EB_OK) return st;
+    sw.tick = (int*)dev_alloc(P->allocs, 4 * sizeof(int), &P->bytes, &st);
+    if (st != EB_OK) return st;
+    cudaMemsetAsync(sw.tick, 0, 4 * sizeof(int), P->s);
+    P->sweep_ticks.push_back(sw.tick);
     const int by = SW_TY + 2 * SW_HY;
     const CUtensorMapDataType ft = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     bool ok = tmap3(&maps[0], ft, 4, o.x[0], o.n, SW_BX, by, 2) && tmap3(&maps[2], ft, 4, sw.alt[0], o.n, SW_BX, by, 2) &&
@@ -543,25 +601,8 @@ static eb_status setup_sweeps(eb_poisson* P, std::vector<Op<T>>& ops, Hier<T>& H
            tmap3(&maps[5], ft, 4, o.b[1], o.n, SW_BX, by, 2);
     if (!ok) continue;  // this level keeps the colour passes
     // the items whose boxes (or coarse cells) hold dielectric unknowns
-    std::vector<int> list1;
-    if (two) {
-      const int nw = (sw.nitems + 31) / 32;
-      std::vector<void*> tmp;
-      unsigned* d_has1 = (unsigned*)dev_alloc(tmp, sizeof(unsigned) * nw, nullptr, &st);
-      if (st != EB_OK) return st;
-      cudaMemsetAsync(d_has1, 0, sizeof(unsigned) * nw, P->s);
-      const uint8_t* cfl = l + 1 < (int)P->G->L.size() ? P->G->L[l + 1].flags : nullptr;
-      const int* cn = l + 1 < (int)P->G->L.size() ? P->G->L[l + 1].g.n : o.n;
-      k_sweep_has1<<<sw.nitems, 256, 0, P->s>>>(Lv.flags, o.n[0], o.n[1], o.n[2], sw.ntx, sw.nty, sw.zc, sw.nitems,
-                                                cfl, cn[0], cn[1], cn[2], d_has1);
-      std::vector<unsigned> h(nw);
-      cudaError_t e = cudaMemcpyAsync(h.data(), d_has1, sizeof(unsigned) * nw, cudaMemcpyDeviceToHost, P->s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
-      for (void* q : tmp) cudaFree(q);
-      if (e != cudaSuccess) return cuda_fail(e, "sweep setup");
-      for (int it = 0; it < sw.nitems; ++it)
-        if ((h[it >> 5] >> (it & 31)) & 1u) list1.push_back(it);
-    }
+    const std::vector<int> list1 =
+        two ? sweep_items1(plane1, sw.ntx * sw.nty, o.n[2], cn2, sw.zc) : std::vector<int>();
     int* dlist = (int*)dev_alloc(P->allocs, sizeof(int) * std::max<size_t>(list1.size(), 1), &P->bytes, &st);
     if (st != EB_OK) return st;
     cudaError_t e = cudaSuccess;
@@ -575,6 +616,7 @@ static eb_status setup_sweeps(eb_poisson* P, std::vector<Op<T>>& ops, Hier<T>& H
     sw.n1items = (int)list1.size();
     sw.par = 0;
     sw.on = 1;
+    sw.rs = restrict_streamed;
     ++P->sweep_levels;
     if (P->sweep_first < 0) P->sweep_first = l;
   }
@@ -583,6 +625,12 @@ static eb_status setup_sweeps(eb_poisson* P, std::vector<Op<T>>& ops, Hier<T>& H
     P->sweep_bytes = SW_HEAD + 128 + SW_NS * SwSlot<T>::BYTES;
   }
   return EB_OK;
+}
+
+// After a launch in which a wait gave up, the streamed passes' ticket
+// counters may be left in the middle of a pass: zero them for the next one.
+static void sweep_reset(eb_poisson* P, cudaStream_t s) {
+  for (int* t : P->sweep_ticks) cudaMemsetAsync(t, 0, 4 * sizeof(int), s);
 }
 
 template <class T>
@@ -874,6 +922,7 @@ static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cyc
   *iters = P->h_out[1];
   *cycles = P->h_out[2];
   *status = bar[2] ? EB_ERR_TIMEOUT : P->h_out[0];
+  if (bar[2]) sweep_reset(P, s);
   return EB_OK;
 }
 
@@ -1365,7 +1414,10 @@ eb_status batch_step(eb_poisson* const* P, int n, const double* const* rhs, cons
   }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return e == cudaSuccess ? EB_OK : cuda_fail(e, "batched solve");
+  if (e != cudaSuccess) return cuda_fail(e, "batched solve");
+  for (int i = 0; i < n; ++i)
+    if (P[i]->h_out[0] == EB_ERR_TIMEOUT) sweep_reset(P[i], s);
+  return EB_OK;
 }
 
 void batch_info(eb_poisson* Q, eb_solve_info* inf) {
@@ -1523,6 +1575,7 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
     if (e == cudaSuccess) e = cudaMemcpy(bar, P->d_bar, sizeof(bar), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "sweep profile");
     if (bar[2]) {
+      sweep_reset(P, s);
       set_error("a sweep wait gave up");
       return EB_ERR_TIMEOUT;
     }

@@ -134,13 +134,16 @@ def test_pin_plane_128_solution_satisfies_oracle_system():
     assert rel <= 2e-10, rel
 
 
+@pytest.mark.parametrize("restrict", ["0", "1"], ids=["block_restriction", "streamed_restriction"])
 @pytest.mark.parametrize("case", CASES[:2], ids=IDS[:2])
-def test_solve_parity_3d_tile_streamed_sweeps(case, oracles, monkeypatch):
+def test_solve_parity_3d_tile_streamed_sweeps(case, restrict, oracles, monkeypatch):
     """The 32^3 cases with the finest level relaxed by tile-streamed sweeps
-    (TMA-staged, both colours per pass; the default applies them from 128^3):
-    the FP32 V-cycles in FP64 defect correction still reach the oracle's
-    solution."""
+    (TMA-staged, both colours per pass; the default applies them from 2^25
+    cells), restricted by the block restriction or by the tile-streamed
+    residual + restriction: the FP32 V-cycles in FP64 defect correction still
+    reach the oracle's solution."""
     monkeypatch.setenv("EBP_SWEEP_MIN_CELLS", "1")
+    monkeypatch.setenv("EBP_SWEEP_RESTRICT", restrict)
     name, d, S, sig = case
     og, ophi = oracles[name][:2]
     g = E.Geometry(d)
