@@ -14,7 +14,10 @@ Problem description (a plain dict, the same one the CUDA binding accepts):
     dim, n (3 ints), lo (3 floats), h,
     prims: list of (kind, params[<=10]), nodes: list of (op, a, b),
     root_E, root_D (-1 = none), eps (gas, dielectric), bc (6 ints, 0 Neumann
-    1 Dirichlet per side xlo,xhi,ylo,yhi,zlo,zhi), phi_E, phi_wall (6 floats).
+    1 Dirichlet, 2 Robin per side xlo,xhi,ylo,yhi,zlo,zhi), phi_E, phi_wall (6 floats).
+Helmholtz and Robin (optional keys): lam (2 floats, the shift alpha a per phase),
+    robin (6 pairs a1, a2 for the Robin sides; phi_wall then holds a3), eb_robin
+    (a pair a1, a2: electrodes carry a1 phi + a2 dphi/dn = a3 with phi_E as a3).
 """
 from __future__ import annotations
 
@@ -55,7 +58,8 @@ class _Desc(C.Structure):
                 ("n_prims", C.c_int), ("prim_kind", C.POINTER(C.c_int)), ("prim_par", C.POINTER(C.c_double)),
                 ("n_nodes", C.c_int), ("node_op", C.POINTER(C.c_int)), ("node_a", C.POINTER(C.c_int)),
                 ("node_b", C.POINTER(C.c_int)), ("root_E", C.c_int), ("root_D", C.c_int),
-                ("eps", C.c_double * 2), ("bc", C.c_int * 6)]
+                ("eps", C.c_double * 2), ("bc", C.c_int * 6), ("robin", C.c_double * 12),
+                ("eb_robin", C.c_int), ("eb_robin_a", C.c_double * 2), ("lam", C.c_double * 2)]
 
 
 class _Data(C.Structure):
@@ -162,6 +166,16 @@ class Geometry:
         d.eps[0], d.eps[1] = float(eps[0]), float(eps[1])
         for k in range(6):
             d.bc[k] = int(desc["bc"][k])
+        rob = desc.get("robin")
+        if rob is not None:
+            for k in range(6):
+                d.robin[2 * k], d.robin[2 * k + 1] = float(rob[k][0]), float(rob[k][1])
+        ebr = desc.get("eb_robin")
+        if ebr is not None:
+            d.eb_robin = 1
+            d.eb_robin_a[0], d.eb_robin_a[1] = float(ebr[0]), float(ebr[1])
+        lam = desc.get("lam", (0.0, 0.0))
+        d.lam[0], d.lam[1] = float(lam[0]), float(lam[1])
         self._d = d
         st = C.c_int(0)
         self._g = lib.or_geom_build(C.byref(d), C.byref(st))

@@ -17,6 +17,14 @@
  *     Dirichlet fluxes, ray-cast EB normal-derivative stencils with first-order
  *     and least-squares fallbacks, and the multifluid matching condition
  *     Eq. (matching) with the boundary state eliminated  [Sec. 3.3, 3.3.1]
+ *   - the Helmholtz generalisation alpha a phi - div(eps grad phi) = rho with
+ *     a constant shift lam = alpha a per phase, entering each cell's balance
+ *     as kappa lam phi  [Sec. 3.3, Eq. helmholtz, with beta b = -eps]
+ *   - Robin conditions a1 phi + a2 dphi/dn = a3 (n out of the fluid) on
+ *     domain walls and on electrode boundaries, imposed by extrapolating phi
+ *     to the boundary with the same one-sided wall formula or ray-cast EB
+ *     stencil the Dirichlet condition uses and eliminating the boundary value
+ *     [Sec. 3.3.1, Eq. robin; the outflow condition of Eq. (RTE robin)]
  *   - the cell-centred field E = -grad(phi)  [Sec. 2.1]
  * The linear system is handed back as COO triplets; the caller solves it with
  * a library sparse direct solver.
@@ -24,7 +32,10 @@
  * Every part is pinned by the tests' closed forms, exactness, conservation
  * and symmetry checks; the least-squares fallback of the EB normal-derivative
  * stencil by linear exactness at the apex of acute fluid wedges, where
- * neither ray stencil finds its cells.
+ * neither ray stencil finds its cells; the Helmholtz shift and the Robin
+ * conditions by quadratic exactness (Robin walls; a Robin electrode on grid
+ * faces), their reduction to the Dirichlet and Neumann branches, and
+ * second-order convergence on a curved Robin electrode.
  *
  * Everything is written dimension-generic over D = 2 or 3, one cell or face
  * at a time, with no blocking or fusion.  Compile with -ffp-contract=off so
@@ -45,7 +56,10 @@
  *   5  the first-order EB stencil divided by h instead of the ray length
  *   6  the least-squares EB stencil with the boundary weight's sign dropped
  *   7  the least-squares fit taken about the cell centre instead of the EB centroid
- *   8  no unknown on a fragment of zero volume (treated as covered) */
+ *   8  no unknown on a fragment of zero volume (treated as covered)
+ *   9  the Robin wall elimination with a2 entering with the wrong sign
+ *  10  the Helmholtz shift without the volume fraction (lam instead of kappa lam)
+ *  11  the Robin EB elimination with the inward derivative taken as outward */
 #ifndef OR_PLANT
 #define OR_PLANT 0
 #endif
@@ -76,7 +90,11 @@ typedef struct {
   int root_E; /* -1: no electrode */
   int root_D; /* -1: no dielectric */
   double eps[2]; /* relative permittivity of gas (phase 0) and dielectric (phase 1) */
-  int bc[6];     /* per domain side 2*d+hi: 0 homogeneous Neumann, 1 Dirichlet */
+  int bc[6];     /* per domain side 2*d+hi: 0 homogeneous Neumann, 1 Dirichlet, 2 Robin */
+  double robin[6][2]; /* Robin sides: a1, a2 of a1 phi + a2 dphi/dn_out = a3 (a3: the wall data) */
+  int eb_robin;       /* 1: electrode boundaries carry a Robin condition instead of Dirichlet */
+  double eb_robin_a[2]; /* its a1, a2 (a3: the electrode data, per cell) */
+  double lam[2];      /* Helmholtz shift per phase: kappa lam phi joins each cell's balance */
 } or_desc;
 
 /* one EB normal-derivative stencil: dphi/dn_in = w0*phi_B + sum w[k]*phi[cell[k]] */
@@ -559,7 +577,7 @@ static int open_face(const or_geom* g, const long I[3], int p)
       if (!(cell_face_alpha(g, I, a, s, p) > 0.0)) continue;
       long wall = s ? (I[a] == g->d.n[a] - 1) : (I[a] == 0);
       if (!wall) return 1;
-      if (g->d.bc[2 * a + s] == 1) return 1;
+      if (g->d.bc[2 * a + s] == 1 || g->d.bc[2 * a + s] == 2) return 1;
     }
   return 0;
 }
@@ -952,8 +970,12 @@ static long wall_total(const or_geom* g)
  * faces with Dirichlet data phi0: the outward derivative
  * (8 phi0 - 9 phi1 + phi2)/(3h) (phi1 adjacent, phi2 next inward; Sec. 3.3.1
  * with the indices put in the order that makes it second order), or
- * 2(phi0 - phi1)/h when phi2 is unavailable.  Returns 0 when the face carries
- * no flux for phase p. */
+ * 2(phi0 - phi1)/h when phi2 is unavailable.  Robin walls (a1 phi0 + a2
+ * dphi/dn_out = a3, a3 the wall data): the same formula written as
+ * dphi/dn_out = Aw phi0 + R (Aw = 8/(3h) or 2/h), solved with the condition
+ * for the wall value phi0 = (a3 - a2 R) / (a1 + a2 Aw), so that
+ * dphi/dn_out = (Aw a3 + a1 R) / (a1 + a2 Aw).  Returns 0 when the face
+ * carries no flux for phase p. */
 static int centred_flux(const or_geom* g, const or_data* dt, int a, const long J[3], int p, lform* F)
 {
   lf_zero(F);
@@ -975,7 +997,8 @@ static int centred_flux(const or_geom* g, const or_data* dt, int a, const long J
     return 1;
   }
   int hi = hi_wall;
-  if (g->d.bc[2 * a + hi] != 1) return 0;
+  const int bct = g->d.bc[2 * a + hi];
+  if (bct != 1 && bct != 2) return 0;
   long C[3] = {J[0], J[1], J[2]}, C2[3];
   if (hi) C[a] -= 1;
   long d1 = dof_of(g, C, p);
@@ -989,7 +1012,25 @@ static int centred_flux(const or_geom* g, const or_data* dt, int a, const long J
   double phi0 = dt->phidom[(long)p * wall_total(g) + wall_index(g, a, hi, C)];
   lform O;
   lf_zero(&O);
-  if (d2 >= 0 && OR_PLANT != 1) {
+  if (bct == 2) {
+    /* R and Aw of the one-sided formula, then the Robin elimination */
+    lform R;
+    lf_zero(&R);
+    double Aw;
+    if (d2 >= 0) {
+      lf_add(&R, d1, -9.0 / (3.0 * h));
+      lf_add(&R, d2, 1.0 / (3.0 * h));
+      Aw = 8.0 / (3.0 * h);
+    } else {
+      lf_add(&R, d1, -2.0 / h);
+      Aw = 2.0 / h;
+    }
+    const double a1 = g->d.robin[2 * a + hi][0];
+    const double a2 = (OR_PLANT == 9 ? -1.0 : 1.0) * g->d.robin[2 * a + hi][1];
+    const double den = a1 + a2 * Aw; /* phi0 is the Robin data a3 here */
+    lf_axpy(&O, eps * a1 / den, &R);
+    O.c = eps * Aw * phi0 / den;
+  } else if (d2 >= 0 && OR_PLANT != 1) {
     lf_add(&O, d1, -9.0 * eps / (3.0 * h));
     lf_add(&O, d2, eps / (3.0 * h));
     O.c = 8.0 * eps * phi0 / (3.0 * h);
@@ -1072,11 +1113,23 @@ static void stencil_form(const or_geom* g, const or_stencil* S, int p, lform* f)
 
 /* dphi/dn_in for fragment (c, p) with the boundary value substituted:
  * electrode -> phi_E; interface -> phi_B eliminated from
- * eps_g dphi/dn_g + eps_d dphi/dn_d = -sigma (Eq. matching, physical sign) */
+ * eps_g dphi/dn_g + eps_d dphi/dn_d = -sigma (Eq. matching, physical sign).
+ * A Robin electrode (a1 phi_B + a2 dphi/dn_out = a3, a3 the electrode data,
+ * dn_out = -dn_in): with dphi/dn_in = w0 phi_B + S, the condition gives
+ * phi_B = (a3 + a2 S) / (a1 - a2 w0), so dphi/dn_in = (w0 a3 + a1 S) / (a1 - a2 w0). */
 static void eb_dphidn(const or_geom* g, const or_data* dt, long c, int p, lform* out)
 {
   lform S;
   stencil_form(g, &g->st[p][c], p, &S);
+  if (g->ebkind[c] == EB_ELECTRODE && g->d.eb_robin) {
+    const double w0 = g->st[p][c].w0, a1 = g->d.eb_robin_a[0];
+    const double a2 = (OR_PLANT == 11 ? -1.0 : 1.0) * g->d.eb_robin_a[1];
+    const double den = a1 - a2 * w0;
+    lf_zero(out);
+    lf_axpy(out, a1 / den, &S);
+    out->c = out->c + w0 * dt->phiE[c] / den;
+    return;
+  }
   if (g->ebkind[c] == EB_ELECTRODE) {
     lf_zero(out);
     lf_axpy(out, 1.0, &S);
@@ -1097,7 +1150,8 @@ static void eb_dphidn(const or_geom* g, const or_data* dt, long c, int p, lform*
   lf_axpy(out, g->st[p][c].w0, &phiB);
 }
 
-/* (L phi)_c for phase p: (1/h^D)[sum_faces alpha_f h^{D-1} F_out + alpha_EB h^{D-1} F_EB] */
+/* (L phi)_c for phase p: (1/h^D)[sum_faces alpha_f h^{D-1} F_out + alpha_EB h^{D-1} F_EB]
+ * - kappa lam phi_c */
 static void row_form(const or_geom* g, const or_data* dt, long c, int p, lform* L)
 {
   long I[3];
@@ -1120,6 +1174,9 @@ static void row_form(const or_geom* g, const or_data* dt, long c, int p, lform* 
     /* F_EB = eps dphi/dn_out = -eps dphi/dn_in */
     lf_axpy(L, -g->d.eps[p] * g->eba[c] / h, &dn);
   }
+  /* the Helmholtz shift: kappa lam phi, (1/h^D)(kappa h^D lam phi); L holds
+   * minus the operator's linear part */
+  if (g->d.lam[p] != 0.0) lf_add(L, g->dof[p][c], -(OR_PLANT == 10 ? 1.0 : g->kappa[p][c]) * g->d.lam[p]);
 }
 
 /* Assemble A phi = b with A = -(linear part of L) and b = kappa s + (data part
