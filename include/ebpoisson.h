@@ -72,7 +72,7 @@ enum {
   EB_PRIM_BOX = 5        /* p = [lox, loy, loz, hix, hiy, hiz]: max_k max(lo_k - x_k, x_k - hi_k) */
 };
 enum { EB_CSG_PRIM = 0, EB_CSG_UNION = 1, EB_CSG_INTERSECT = 2, EB_CSG_NEGATE = 3 };
-enum { EB_BC_NEUMANN = 0, EB_BC_DIRICHLET = 1 };
+enum { EB_BC_NEUMANN = 0, EB_BC_DIRICHLET = 1, EB_BC_ROBIN = 2 };
 
 #define EB_MAX_PRIMS 32
 #define EB_MAX_NODES 64
@@ -104,7 +104,18 @@ typedef struct {
   int dielectric_root;                      /* node whose negative set is the dielectric, -1 = none */
   double eps_gas, eps_diel;                 /* relative permittivities */
   int bc_type[6];     /* EB_BC_* per wall: xlo, xhi, ylo, yhi, zlo, zhi */
-  double bc_value[6]; /* Dirichlet value per wall (Neumann walls are homogeneous) */
+  double bc_value[6]; /* Dirichlet value per wall, or a3 of a Robin wall (Neumann walls are homogeneous) */
+  /* Helmholtz and Robin terms (Sec. 3.3, Eq. helmholtz; Sec. 3.3.1, Eq. robin); all zero gives the
+   * Poisson problem.  The operator becomes lam_p phi - div(eps grad phi) in phase p (each cell's
+   * balance gains kappa lam_p phi).  A Robin wall imposes a1 phi + a2 dphi/dn = a3 with n out of the
+   * domain; Robin electrodes impose the same with n into the electrode, electrode_phi giving each
+   * electrode's a3.  The boundary value is eliminated through the one-sided wall formula or the EB
+   * ray stencil that the Dirichlet condition uses.  Coefficients >= 0, a1 + a2 > 0, lam >= 0;
+   * EB_ERR_INVALID otherwise. */
+  double bc_robin[6][2];       /* a1, a2 per Robin wall */
+  int electrode_robin;         /* 1: every electrode carries the Robin condition instead of a potential */
+  double electrode_robin_a[2]; /* its a1, a2 */
+  double helmholtz_lam[2];     /* lam per phase (gas, dielectric) */
 } eb_geom_desc;
 
 typedef struct eb_geom eb_geom;

@@ -57,9 +57,13 @@ struct Grid {
   double lo[3];
   double h;
   long long ncell;
-  int bc[6];        // 1 = Dirichlet wall
-  double bcv[6];    // Dirichlet values (finest level only; 0 on coarse levels)
+  int bc[6];        // 0 = Neumann wall (homogeneous), 1 = Dirichlet, 2 = Robin
+  double bcv[6];    // Dirichlet values, or a3 of a Robin wall (finest level only; 0 on coarse levels)
   double eps[2];
+  double rob[6][2];  // Robin walls: a1, a2 of a1 phi + a2 dphi/dn_out = a3
+  double lam[2];     // Helmholtz shift per phase: kappa lam phi joins each cell's balance
+  int eb_robin;      // 1: electrode boundaries carry a1 phi + a2 dphi/dn_out = a3 (a3 in phiE)
+  double eb_ra[2];   // their a1, a2
 };
 
 EBP_HD long long cell_index(const Grid& g, int i, int j, int k) {

@@ -382,10 +382,16 @@ __device__ __forceinline__ void rhs_cell(const LevelGeom& L, long long c, const 
         int I[3];
         cell_ijk(g, c, I);
         double e = g.eps[p], h2 = g.h * g.h;
-        for (int a = 0; a < g.D; ++a) {
-          if (I[a] == 0 && g.bc[2 * a]) v = v + 8.0 * e * g.bcv[2 * a] / (3.0 * h2);
-          if (I[a] == g.n[a] - 1 && g.bc[2 * a + 1]) v = v + 8.0 * e * g.bcv[2 * a + 1] / (3.0 * h2);
-        }
+        // wall data: Dirichlet 8 eps phi0 / (3 h^2); Robin the same with a3
+        // divided by a1 + 8 a2 / (3h) (the wall value eliminated)
+        for (int a = 0; a < g.D; ++a)
+          for (int hi = 0; hi < 2; ++hi) {
+            const int sd = 2 * a + hi;
+            if (I[a] != (hi ? g.n[a] - 1 : 0) || !g.bc[sd]) continue;
+            double d = 8.0 * e * g.bcv[sd] / (3.0 * h2);
+            if (g.bc[sd] == 2) d = d / (g.rob[sd][0] + g.rob[sd][1] * 8.0 / (3.0 * g.h));
+            v = v + d;
+          }
       }
     }
     b[p * g.ncell + c] = v;

@@ -36,7 +36,11 @@ struct Op {
   int D;
   int n[3];
   long long ncell;
-  int bc[6];
+  // wall weight per side (xlo, xhi, ylo, yhi, zlo, zhi): 1 on a Dirichlet
+  // wall, 0 on a Neumann wall, a1 / (a1 + 8 a2 / (3h)) on a Robin wall
+  T wr[6];
+  T lh[2];   // the Helmholtz shift per phase in the stencil's units: lam_p h^2 / eps_p
+  T idg[2];  // 1 / (2D + lh[p]): the reciprocal diagonal of a cell away from the walls
   T* x[2];  // unknown per phase
   T* b[2];  // right-hand side per phase
   const uint8_t* flags;
@@ -52,52 +56,42 @@ struct Op {
   T h2e[2];   // h^2 / eps_p
 };
 
-__device__ __forceinline__ float inv_count(int d, float) { return 1.0f / (float)d; }
-__device__ __forceinline__ double inv_count(int d, double) {
-  // reciprocals of the possible diagonal counts (faces + 3 per Dirichlet wall face)
-  switch (d) {
-    case 1: return 1.0;
-    case 2: return 0.5;
-    case 3: return 1.0 / 3.0;
-    case 4: return 0.25;
-    case 5: return 0.2;
-    case 6: return 1.0 / 6.0;
-    case 7: return 1.0 / 7.0;
-    case 8: return 0.125;
-    case 9: return 1.0 / 9.0;
-    case 10: return 0.1;
-    case 11: return 1.0 / 11.0;
-    case 12: return 1.0 / 12.0;
-    default: return 1.0 / (double)d;
-  }
-}
-
-// Implicit stencil of a regular cell: A x = (eps/h^2)(dg x_c - sum); a
-// Dirichlet wall face adds 3 to dg and x_inward/3 to sum (one-sided second
-// order wall flux), a Neumann wall face adds nothing.
+// Implicit stencil of a regular cell: A x = (eps/h^2)((dg + lh) x_c - sum).
+// Every open face adds 1 to dg and its neighbour to sum.  A wall face with
+// weight w adds 3w to dg and w x_inward / 3 to sum.  This is the one-sided
+// second-order wall flux: w = 1 for Dirichlet; for Robin the wall value is
+// eliminated through the same formula.  A Neumann wall face (w = 0) adds
+// nothing.
 template <class T>
-__device__ __forceinline__ void reg_stencil(const Op<T>& o, const T* x, const int I[3], long long c, T& sum, int& dg) {
+__device__ __forceinline__ void reg_stencil(const Op<T>& o, const T* x, const int I[3], long long c, T& sum, T& dg) {
   sum = T(0);
-  dg = 0;
+  dg = T(0);
   long long st = 1;
   const T third = T(1) / T(3);
   for (int a = 0; a < o.D; ++a) {
     if (I[a] > 0) {
       sum += x[c - st];
-      dg += 1;
-    } else if (o.bc[2 * a]) {
-      sum += x[c + st] * third;
-      dg += 3;
+      dg += T(1);
+    } else if (o.wr[2 * a] != T(0)) {
+      sum += x[c + st] * (o.wr[2 * a] * third);
+      dg += T(3) * o.wr[2 * a];
     }
     if (I[a] < o.n[a] - 1) {
       sum += x[c + st];
-      dg += 1;
-    } else if (o.bc[2 * a + 1]) {
-      sum += x[c - st] * third;
-      dg += 3;
+      dg += T(1);
+    } else if (o.wr[2 * a + 1] != T(0)) {
+      sum += x[c - st] * (o.wr[2 * a + 1] * third);
+      dg += T(3) * o.wr[2 * a + 1];
     }
     st *= o.n[a];
   }
+}
+
+// 1 / (dg + lh[p]), the reciprocal diagonal of a regular cell of phase p
+// whose stencil gave dg: the stored value for a cell away from the walls.
+template <class T>
+__device__ __forceinline__ T diag_inv(const Op<T>& o, int p, T dg) {
+  return dg == T(2 * o.D) ? o.idg[p] : T(1) / (dg + o.lh[p]);
 }
 
 template <class T>
@@ -127,10 +121,9 @@ __global__ void k_smooth_dense(Op<T> o, int colour) {
   int p = (f & 1) ? 0 : 1;
   T* x = o.x[p];
   int I[3] = {i, j, k};
-  T sum;
-  int dg;
+  T sum, dg;
   reg_stencil(o, x, I, c, sum, dg);
-  x[c] = (o.h2e[p] * o.b[p][c] + sum) * inv_count(dg, T(0));
+  x[c] = (o.h2e[p] * o.b[p][c] + sum) * diag_inv(o, p, dg);
 }
 
 // sum over the off-diagonal entries of sparse row r; entries are taken eight
@@ -203,10 +196,9 @@ template <class T>
 __device__ __forceinline__ T cell_residual(const Op<T>& o, long long c, int p, const int I[3]) {
   uint8_t f = o.flags[c];
   if (f & F_IRR) return o.tmp[2 * (long long)o.irr_of_cell[c] + p];
-  T sum;
-  int dg;
+  T sum, dg;
   reg_stencil(o, o.x[p], I, c, sum, dg);
-  return o.b[p][c] - o.ceps[p] * ((T)dg * o.x[p][c] - sum);
+  return o.b[p][c] - o.ceps[p] * ((dg + o.lh[p]) * o.x[p][c] - sum);
 }
 
 // r = b - A x on the fine level, averaged over the 2^D children into the
@@ -312,10 +304,9 @@ __global__ void k_bottom(Op<T> o, int sweeps) {
         if ((f & F_IRR) || !(f & 3)) continue;
         int p = (f & 1) ? 0 : 1;
         int I[3] = {i, j, k};
-        T sum;
-        int dg;
+        T sum, dg;
         reg_stencil(o, o.x[p], I, c, sum, dg);
-        o.x[p][c] = (o.h2e[p] * o.b[p][c] + sum) * inv_count(dg, T(0));
+        o.x[p][c] = (o.h2e[p] * o.b[p][c] + sum) * diag_inv(o, p, dg);
       }
       __syncthreads();
       long long rb = colour == 0 ? 0 : 2 * o.nirr_red, re = colour == 0 ? 2 * o.nirr_red : 2 * o.nirr;

@@ -198,10 +198,9 @@ __device__ __forceinline__ void ph_dense_scalar(const Op<T>& o, int colour, cons
     for (int u = 0; u < U; ++u) {
       val[u] = T(0);
       if (act[u]) {
-        T sum;
-        int dg;
+        T sum, dg;
         reg_stencil(o, o.x[pp[u]], I[u], cc[u], sum, dg);
-        val[u] = (o.h2e[pp[u]] * o.b[pp[u]][cc[u]] + sum) * inv_count(dg, T(0));
+        val[u] = (o.h2e[pp[u]] * o.b[pp[u]][cc[u]] + sum) * diag_inv(o, pp[u], dg);
       }
     }
 #pragma unroll
@@ -235,52 +234,52 @@ __device__ __forceinline__ T relax4(const Op<T>& o, int p, int i, int j, int k, 
                                     const T ym[4], const T yp[4], const T zm[4], const T zp[4], const T bv[4]) {
   const T third = T(1) / T(3);
   T sum = T(0);
-  int dg = 0;
+  T dg = T(0);
   if (i > 0) {
     sum += E > 0 ? xc[E > 0 ? E - 1 : 0] : xl;
-    dg += 1;
-  } else if (o.bc[0]) {
-    sum += xc[E < 3 ? E + 1 : 3] * third;
-    dg += 3;
+    dg += T(1);
+  } else if (o.wr[0] != T(0)) {
+    sum += xc[E < 3 ? E + 1 : 3] * (o.wr[0] * third);
+    dg += T(3) * o.wr[0];
   }
   if (i < o.n[0] - 1) {
     sum += E < 3 ? xc[E < 3 ? E + 1 : 3] : xr;
-    dg += 1;
-  } else if (o.bc[1]) {
-    sum += xc[E > 0 ? E - 1 : 0] * third;
-    dg += 3;
+    dg += T(1);
+  } else if (o.wr[1] != T(0)) {
+    sum += xc[E > 0 ? E - 1 : 0] * (o.wr[1] * third);
+    dg += T(3) * o.wr[1];
   }
   if (j > 0) {
     sum += ym[E];
-    dg += 1;
-  } else if (o.bc[2]) {
-    sum += yp[E] * third;
-    dg += 3;
+    dg += T(1);
+  } else if (o.wr[2] != T(0)) {
+    sum += yp[E] * (o.wr[2] * third);
+    dg += T(3) * o.wr[2];
   }
   if (j < o.n[1] - 1) {
     sum += yp[E];
-    dg += 1;
-  } else if (o.bc[3]) {
-    sum += ym[E] * third;
-    dg += 3;
+    dg += T(1);
+  } else if (o.wr[3] != T(0)) {
+    sum += ym[E] * (o.wr[3] * third);
+    dg += T(3) * o.wr[3];
   }
   if (o.D == 3) {
     if (k > 0) {
       sum += zm[E];
-      dg += 1;
-    } else if (o.bc[4]) {
-      sum += zp[E] * third;
-      dg += 3;
+      dg += T(1);
+    } else if (o.wr[4] != T(0)) {
+      sum += zp[E] * (o.wr[4] * third);
+      dg += T(3) * o.wr[4];
     }
     if (k < o.n[2] - 1) {
       sum += zp[E];
-      dg += 1;
-    } else if (o.bc[5]) {
-      sum += zm[E] * third;
-      dg += 3;
+      dg += T(1);
+    } else if (o.wr[5] != T(0)) {
+      sum += zm[E] * (o.wr[5] * third);
+      dg += T(3) * o.wr[5];
     }
   }
-  return (o.h2e[p] * bv[E] + sum) * inv_count(dg, T(0));
+  return (o.h2e[p] * bv[E] + sum) * diag_inv(o, p, dg);
 }
 
 // Relaxed value of one regular cell by the scalar stencil (a group whose two
@@ -288,10 +287,9 @@ __device__ __forceinline__ T relax4(const Op<T>& o, int p, int i, int j, int k, 
 template <class T>
 __device__ __noinline__ T relax1(const Op<T>& o, int q, int i, int j, int k, long long cc) {
   int I[3] = {i, j, k};
-  T sum;
-  int dg;
+  T sum, dg;
   reg_stencil(o, o.x[q], I, cc, sum, dg);
-  return (o.h2e[q] * o.b[q][cc] + sum) * inv_count(dg, T(0));
+  return (o.h2e[q] * o.b[q][cc] + sum) * diag_inv(o, q, dg);
 }
 
 // One colour on regular cells, four x cells per work item (two of the
@@ -538,8 +536,7 @@ __device__ __forceinline__ void ph_restrict_blk(const Op<T>& f, const Op<T>& co,
           continue;
         }
 #define EBP_PIX(du, dv, dw) (((ku) + (du) + 1) + 4 * ((kv) + (dv) + 1) + 16 * ((kw) + (dw) + 1))
-        T sum = T(0);
-        int dg = 0;
+        T sum = T(0), dg = T(0);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           const int e0 = a == 0, e1 = a == 1, e2 = a == 2;
@@ -547,23 +544,23 @@ __device__ __forceinline__ void ph_restrict_blk(const Op<T>& f, const Op<T>& co,
           const T hi = P[D == 3 ? EBP_PIX(e0, e1, e2) : EBP_PIX(e0, e1, 0) - 16];
           if (I[a] > 0) {
             sum += lo;
-            dg += 1;
-          } else if (f.bc[2 * a]) {
-            sum += hi * third;
-            dg += 3;
+            dg += T(1);
+          } else if (f.wr[2 * a] != T(0)) {
+            sum += hi * (f.wr[2 * a] * third);
+            dg += T(3) * f.wr[2 * a];
           }
           if (I[a] < f.n[a] - 1) {
             sum += hi;
-            dg += 1;
-          } else if (f.bc[2 * a + 1]) {
-            sum += lo * third;
-            dg += 3;
+            dg += T(1);
+          } else if (f.wr[2 * a + 1] != T(0)) {
+            sum += lo * (f.wr[2 * a + 1] * third);
+            dg += T(3) * f.wr[2 * a + 1];
           }
         }
         const T xc = P[D == 3 ? EBP_PIX(0, 0, 0) : EBP_PIX(0, 0, 0) - 16];
 #undef EBP_PIX
         (void)loc;
-        acc[q] += bv[k] - f.ceps[q] * ((T)dg * xc - sum);
+        acc[q] += bv[k] - f.ceps[q] * ((dg + f.lh[q]) * xc - sum);
       }
     }
     for (int p = 0; p < 2; ++p) {
@@ -998,10 +995,9 @@ __device__ __forceinline__ void bot_matvec_grid(const Op<T>& o, const T* y, T* z
         } else {
           int I[3];
           ijk(o, cc, I);
-          T sum;
-          int dg;
+          T sum, dg;
           reg_stencil(o, y + p * n, I, cc, sum, dg);
-          acc = o.ceps[p] * ((T)dg * y[p * n + cc] - sum);
+          acc = o.ceps[p] * ((dg + o.lh[p]) * y[p * n + cc] - sum);
         }
       }
       z[p * n + cc] = acc;
@@ -1383,20 +1379,22 @@ __global__ void k_bottom_matrix(Op<T> o, double ceps0, double ceps1, int m, doub
   int I[3];
   ijk(o, c, I);
   long long st = 1;
+  row[i] += ce * (double)o.lh[p];  // the Helmholtz shift
   for (int a = 0; a < o.D; ++a) {
+    const double wl = (double)o.wr[2 * a], wh = (double)o.wr[2 * a + 1];
     if (I[a] > 0) {
       row[i - st] -= ce;
       row[i] += ce;
-    } else if (o.bc[2 * a]) {
-      row[i + st] -= ce / 3.0;
-      row[i] += 3.0 * ce;
+    } else if (wl != 0.0) {
+      row[i + st] -= wl * ce / 3.0;
+      row[i] += 3.0 * wl * ce;
     }
     if (I[a] < o.n[a] - 1) {
       row[i + st] -= ce;
       row[i] += ce;
-    } else if (o.bc[2 * a + 1]) {
-      row[i - st] -= ce / 3.0;
-      row[i] += 3.0 * ce;
+    } else if (wh != 0.0) {
+      row[i - st] -= wh * ce / 3.0;
+      row[i] += 3.0 * wh * ce;
     }
     st *= o.n[a];
   }

@@ -105,8 +105,22 @@ static eb_status validate(const eb_geom_desc* d) {
     if (d->electrode_node[e] < 0 || d->electrode_node[e] >= d->n_nodes) return bad("electrode node out of range");
   if (d->electrode_root >= 0 && d->n_electrodes == 0) return bad("an electrode root needs at least one electrode");
   if (!(d->eps_gas > 0.0) || (d->dielectric_root >= 0 && !(d->eps_diel > 0.0))) return bad("permittivity must be > 0");
-  for (int k = 0; k < 2 * d->dim; ++k)
-    if (d->bc_type[k] != EB_BC_NEUMANN && d->bc_type[k] != EB_BC_DIRICHLET) return bad("unknown wall type");
+  for (int k = 0; k < 2 * d->dim; ++k) {
+    if (d->bc_type[k] != EB_BC_NEUMANN && d->bc_type[k] != EB_BC_DIRICHLET && d->bc_type[k] != EB_BC_ROBIN)
+      return bad("unknown wall type");
+    if (d->bc_type[k] == EB_BC_ROBIN) {
+      const double a1 = d->bc_robin[k][0], a2 = d->bc_robin[k][1];
+      if (!(a1 >= 0.0 && a2 >= 0.0 && a1 + a2 > 0.0 && std::isfinite(a1 + a2)))
+        return bad("Robin wall coefficients must be >= 0, not both 0");
+    }
+  }
+  if (d->electrode_robin) {
+    const double a1 = d->electrode_robin_a[0], a2 = d->electrode_robin_a[1];
+    if (!(a1 >= 0.0 && a2 >= 0.0 && a1 + a2 > 0.0 && std::isfinite(a1 + a2)))
+      return bad("Robin electrode coefficients must be >= 0, not both 0");
+  }
+  for (int p = 0; p < 2; ++p)
+    if (!(d->helmholtz_lam[p] >= 0.0 && std::isfinite(d->helmholtz_lam[p]))) return bad("Helmholtz shift must be >= 0");
   return EB_OK;
 }
 
@@ -152,11 +166,18 @@ extern "C" eb_status eb_geom_build(const eb_geom_desc* d, void* stream, eb_geom*
   g.h = d->h;
   g.ncell = (long long)g.n[0] * g.n[1] * g.n[2];
   for (int k = 0; k < 6; ++k) {
-    g.bc[k] = (k < 2 * d->dim) ? (d->bc_type[k] == EB_BC_DIRICHLET) : 0;
+    g.bc[k] = (k < 2 * d->dim) ? d->bc_type[k] : 0;
     g.bcv[k] = (k < 2 * d->dim && g.bc[k]) ? d->bc_value[k] : 0.0;
+    g.rob[k][0] = g.bc[k] == EB_BC_ROBIN ? d->bc_robin[k][0] : 0.0;
+    g.rob[k][1] = g.bc[k] == EB_BC_ROBIN ? d->bc_robin[k][1] : 0.0;
   }
   g.eps[0] = d->eps_gas;
   g.eps[1] = d->dielectric_root >= 0 ? d->eps_diel : d->eps_gas;
+  g.lam[0] = d->helmholtz_lam[0];
+  g.lam[1] = d->dielectric_root >= 0 ? d->helmholtz_lam[1] : d->helmholtz_lam[0];
+  g.eb_robin = d->electrode_robin ? 1 : 0;
+  g.eb_ra[0] = g.eb_robin ? d->electrode_robin_a[0] : 0.0;
+  g.eb_ra[1] = g.eb_robin ? d->electrode_robin_a[1] : 0.0;
   G->L.push_back(L0);
   std::vector<void*> misc;
   G->d_csg = (Csg*)dev_alloc(G->L[0].allocs, sizeof(Csg), &G->bytes, &st);
@@ -308,6 +329,27 @@ extern "C" void eb_solver_opts_default(eb_solver_opts* o) {
   o->launch_mode = 0;
 }
 
+// The regular stencil's wall weights, Helmholtz shift and reciprocal
+// interior diagonal (Op::wr, lh, idg) on a level with grid g.  A Robin wall's
+// weight a1 / (a1 + 8 a2 / (3h)) is what is left of the one-sided wall
+// formula once the wall value is eliminated; it depends on the level's h.
+template <class T>
+static void set_stencil_terms(Op<T>& o, const Grid& g) {
+  for (int k = 0; k < 6; ++k) {
+    double w = 0.0;
+    if (k < 2 * g.D) {
+      if (g.bc[k] == 1) w = 1.0;
+      else if (g.bc[k] == 2) w = g.rob[k][0] / (g.rob[k][0] + g.rob[k][1] * 8.0 / (3.0 * g.h));
+    }
+    o.wr[k] = (T)w;
+  }
+  for (int p = 0; p < 2; ++p) {
+    const T lh = (T)(g.lam[p] * g.h * g.h / g.eps[p]);
+    o.lh[p] = lh;
+    o.idg[p] = T(1) / (T(2 * g.D) + lh);
+  }
+}
+
 template <class T>
 static Op<T> make_op(const DevLevel& L, std::vector<void*>& owner, long long* bytes, eb_status* st, int nphase,
                      T* x0 = nullptr, T* b0 = nullptr, T* x1 = nullptr, T* b1 = nullptr) {
@@ -320,7 +362,7 @@ static Op<T> make_op(const DevLevel& L, std::vector<void*>& owner, long long* by
   o.dhx = make_fastdiv((unsigned)((L.g.n[0] + 1) / 2));
   o.dq = make_fastdiv((unsigned)std::max(1, L.g.n[0] / 4));
   o.ncell = L.g.ncell;
-  for (int k = 0; k < 6; ++k) o.bc[k] = L.g.bc[k];
+  set_stencil_terms(o, L.g);
   size_t n = (size_t)L.g.ncell;
   o.x[0] = x0 ? x0 : (T*)dev_alloc(owner, n * sizeof(T), bytes, st);
   o.b[0] = b0 ? b0 : (T*)dev_alloc(owner, n * sizeof(T), bytes, st);
@@ -1793,7 +1835,7 @@ extern "C" eb_status eb_poisson_residual_noalloc(const eb_geom* G, const double*
   o.dhx = make_fastdiv((unsigned)((F.g.n[0] + 1) / 2));
   o.dq = make_fastdiv((unsigned)std::max(1, F.g.n[0] / 4));
   o.ncell = n;
-  for (int k = 0; k < 6; ++k) o.bc[k] = F.g.bc[k];
+  set_stencil_terms(o, F.g);
   o.x[0] = const_cast<double*>(d_phi);
   o.x[1] = const_cast<double*>(d_phi) + n;
   o.b[0] = b;

@@ -120,7 +120,10 @@ struct CFlux {
 // Interior: eps (phi_hi - phi_lo)/h.  Dirichlet wall with value phi0: the
 // outward derivative (8 phi0 - 9 phi1 + phi2)/(3h), phi1 the wall cell, phi2
 // the next cell inward (the order of indices that makes it second order), or
-// 2 (phi0 - phi1)/h when phi2 is not reachable through an open face.
+// 2 (phi0 - phi1)/h when phi2 is not reachable through an open face.  Robin
+// wall (a1 phi0 + a2 dphi/dn_out = a3, Sec. 3.3.1): the same formula, written
+// Aw phi0 + R, fixes the wall value phi0 = (a3 - a2 R) / (a1 + a2 Aw); the
+// flux is then eps (Aw a3 + a1 R) / (a1 + a2 Aw).
 EBP_HDN bool centred_flux(const LevelGeom& L, int a, const int J[3], int p, CFlux& F) {
   FaceInfo fi;
   if (!face_open(L, a, J, p, fi)) return false;
@@ -152,6 +155,23 @@ EBP_HDN bool centred_flux(const LevelGeom& L, int a, const int J[3], int p, CFlu
   double phi0 = g.bcv[2 * a + hi];
   double sgn = hi ? 1.0 : -1.0;  // outward is +e_a on the hi wall
   long long c1 = cell_index(g, C[0], C[1], C[2]);
+  if (g.bc[2 * a + hi] == 2) {
+    const double a1 = g.rob[2 * a + hi][0], a2 = g.rob[2 * a + hi][1];
+    const double Aw = has2 ? 8.0 / (3.0 * h) : 2.0 / h, den = a1 + a2 * Aw;
+    const double f = sgn * eps * a1 / den;  // phi0 holds a3 here
+    F.col[0] = col_encode(p, c1);
+    if (has2) {
+      F.n = 2;
+      F.w[0] = f * (-9.0 / (3.0 * h));
+      F.col[1] = col_encode(p, cell_index(g, C2[0], C2[1], C2[2]));
+      F.w[1] = f * (1.0 / (3.0 * h));
+    } else {
+      F.n = 1;
+      F.w[0] = f * (-2.0 / h);
+    }
+    F.c = sgn * eps * Aw * phi0 / den;
+    return true;
+  }
   if (has2) {
     F.n = 2;
     F.col[0] = col_encode(p, c1);
@@ -437,6 +457,9 @@ EBP_HD void record_nin(const LevelGeom& L, long long q, int p, double xB[3], dou
 // form over the unknowns: electrode -> phi_E; dielectric interface -> phi_B
 // eliminated from eps_g dphi/dn_g + eps_d dphi/dn_d = -sigma/eps0 (Eq.
 // matching with normals pointing into each fluid; Gauss's law fixes the sign).
+// A Robin electrode (a1 phi_B + a2 dphi/dn_out = a3, phiE holding a3; Sec.
+// 3.3.1): with the ray stencil dphi/dn_in = w0 phi_B + S and dn_out = -dn_in,
+// phi_B = (a3 + a2 S) / (a1 - a2 w0) and dphi/dn_in = (w0 a3 + a1 S) / (a1 - a2 w0).
 // Scaled by `scale` and added to R; returns a status.  `orders` gets the
 // stencil order of each phase.
 template <int N>
@@ -450,6 +473,12 @@ EBP_HDN int add_eb_dphidn(const LevelGeom& L, long long q, const int I[3], int p
     int st = build_stencil(L, I, p, xB, nin, S);
     if (st) return st;
     orders[p] = S.order;
+    if (L.g.eb_robin) {
+      const double a1 = L.g.eb_ra[0], a2 = L.g.eb_ra[1], den = a1 - a2 * S.w0;
+      for (int k = 0; k < S.n; ++k) R.add(col_encode(p, S.cell[k]), scale * (a1 / den) * S.w[k]);
+      R.c = R.c + scale * (S.w0 * phiE / den);
+      return 0;
+    }
     for (int k = 0; k < S.n; ++k) R.add(col_encode(p, S.cell[k]), scale * S.w[k]);
     R.c = R.c + scale * (S.w0 * phiE);
     return 0;
@@ -499,6 +528,11 @@ EBP_HDN int build_row_form(const LevelGeom& L, long long cell, int p, Form<N>& R
     double scale = -g.eps[p] * L.R.eba[q] / g.h;  // F_EB = -eps dphi/dn_in
     int st = add_eb_dphidn(L, q, I, p, L.R.phiE[q], scale, R, orders);
     if (st) return st;
+  }
+  // the Helmholtz shift kappa lam phi (R holds minus the operator's linear part)
+  if (g.lam[p] != 0.0) {
+    const double kap = q >= 0 ? L.R.kappa[p * L.R.ncut + q] : 1.0;
+    R.add(col_encode(p, cell), -kap * g.lam[p]);
   }
   return R.overflow ? ST_OVERFLOW : 0;
 }

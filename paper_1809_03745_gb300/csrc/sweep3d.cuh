@@ -103,68 +103,71 @@ struct SwSlot {
 template <class T>
 struct SwGrid {
   int n0, n1, n2;
-  unsigned bcm;  // bit s set: Dirichlet wall on side s (xlo, xhi, ylo, yhi, zlo, zhi)
-  T h2e, ceps;
+  T wr[6];  // wall weights (xlo, xhi, ylo, yhi, zlo, zhi), as in the level's operator
+  T h2e, ceps, lh, idg;
   __device__ SwGrid(const Op<T>& o, int p) {
     n0 = o.n[0];
     n1 = o.n[1];
     n2 = o.n[2];
-    bcm = 0u;
-    for (int q = 0; q < 6; ++q) bcm |= (o.bc[q] ? 1u : 0u) << q;
+    for (int q = 0; q < 6; ++q) wr[q] = o.wr[q];
     h2e = o.h2e[p];
     ceps = o.ceps[p];
+    lh = o.lh[p];
+    idg = o.idg[p];
   }
+  // 1 / (dg + lh) for a cell whose stencil gave dg (dg = 6 away from the walls)
+  __device__ __forceinline__ T dinv(T dg) const { return dg == T(6) ? idg : T(1) / (dg + lh); }
 };
 
 // Implicit stencil sum and diagonal count of reg_stencil, same terms in the
 // same order, at a cell next to a domain wall (box index e, planes Xm, Xc, Xp).
 template <class T>
 __device__ __noinline__ void sw_wall_stencil(const SwGrid<T>& g, const T* Xm, const T* Xc, const T* Xp, int e, int i,
-                                             int j, int k, T& sum_out, int& dg_out) {
+                                             int j, int k, T& sum_out, T& dg_out) {
   const T third = T(1) / T(3);
   T sum = T(0);
-  int dg = 0;
+  T dg = T(0);
   if (i > 0) {
     sum += Xc[e - 1];
-    dg += 1;
-  } else if (g.bcm & 1u) {
-    sum += Xc[e + 1] * third;
-    dg += 3;
+    dg += T(1);
+  } else if (g.wr[0] != T(0)) {
+    sum += Xc[e + 1] * (g.wr[0] * third);
+    dg += T(3) * g.wr[0];
   }
   if (i < g.n0 - 1) {
     sum += Xc[e + 1];
-    dg += 1;
-  } else if (g.bcm & 2u) {
-    sum += Xc[e - 1] * third;
-    dg += 3;
+    dg += T(1);
+  } else if (g.wr[1] != T(0)) {
+    sum += Xc[e - 1] * (g.wr[1] * third);
+    dg += T(3) * g.wr[1];
   }
   if (j > 0) {
     sum += Xc[e - SW_BX];
-    dg += 1;
-  } else if (g.bcm & 4u) {
-    sum += Xc[e + SW_BX] * third;
-    dg += 3;
+    dg += T(1);
+  } else if (g.wr[2] != T(0)) {
+    sum += Xc[e + SW_BX] * (g.wr[2] * third);
+    dg += T(3) * g.wr[2];
   }
   if (j < g.n1 - 1) {
     sum += Xc[e + SW_BX];
-    dg += 1;
-  } else if (g.bcm & 8u) {
-    sum += Xc[e - SW_BX] * third;
-    dg += 3;
+    dg += T(1);
+  } else if (g.wr[3] != T(0)) {
+    sum += Xc[e - SW_BX] * (g.wr[3] * third);
+    dg += T(3) * g.wr[3];
   }
   if (k > 0) {
     sum += Xm[e];
-    dg += 1;
-  } else if (g.bcm & 16u) {
-    sum += Xp[e] * third;
-    dg += 3;
+    dg += T(1);
+  } else if (g.wr[4] != T(0)) {
+    sum += Xp[e] * (g.wr[4] * third);
+    dg += T(3) * g.wr[4];
   }
   if (k < g.n2 - 1) {
     sum += Xp[e];
-    dg += 1;
-  } else if (g.bcm & 32u) {
-    sum += Xm[e] * third;
-    dg += 3;
+    dg += T(1);
+  } else if (g.wr[5] != T(0)) {
+    sum += Xm[e] * (g.wr[5] * third);
+    dg += T(3) * g.wr[5];
   }
   sum_out = sum;
   dg_out = dg;
@@ -178,7 +181,7 @@ __device__ __noinline__ void sw_wall_stencil(const SwGrid<T>& g, const T* Xm, co
 // The wall stencil of the cell at X, from indices.
 template <class T>
 __device__ __forceinline__ void sw_wall_at(const SwGrid<T>& g, const T* sm, int X, int M, int P, int i, int j, int k,
-                                           T& sum, int& dg) {
+                                           T& sum, T& dg) {
   sw_wall_stencil(g, sm + (M - X), sm, sm + (P - X), X, i, j, k, sum, dg);
 }
 
@@ -206,28 +209,26 @@ __device__ __forceinline__ void sw_pair(const SwGrid<T>& g, unsigned pbit, T* sm
   // every index here is inside the ring, whatever the cell
   const T sA = ((((sm[XA - 1] + sm[XA + 1]) + sm[XA - SW_BX]) + sm[XA + SW_BX]) + sm[MA]) + sm[PA];
   const T sB = ((((sm[XB - 1] + sm[XB + 1]) + sm[XB - SW_BX]) + sm[XB + SW_BX]) + sm[MB]) + sm[PB];
-  const T vA = (g.h2e * sm[BA] + sA) * inv_count(6, T(0));
-  const T vB = (g.h2e * sm[BB] + sB) * inv_count(6, T(0));
+  const T vA = (g.h2e * sm[BA] + sA) * g.idg;
+  const T vB = (g.h2e * sm[BB] + sB) * g.idg;
   const bool rA = actA && (sb[FA] & 7u) == pbit;
   const bool rB = actB && (sb[FB] & 7u) == pbit;
   if (rA) {
     if (fastA) {
       sm[XA] = vA;
     } else {
-      T sum;
-      int dg;
+      T sum, dg;
       sw_wall_at(g, sm, XA, MA, PA, cl.iA, j, kA, sum, dg);
-      sm[XA] = (g.h2e * sm[BA] + sum) * inv_count(dg, T(0));
+      sm[XA] = (g.h2e * sm[BA] + sum) * g.dinv(dg);
     }
   }
   if (rB) {
     if (fastB) {
       sm[XB] = vB;
     } else {
-      T sum;
-      int dg;
+      T sum, dg;
       sw_wall_at(g, sm, XB, MB, PB, cl.iB, j, kB, sum, dg);
-      sm[XB] = (g.h2e * sm[BB] + sum) * inv_count(dg, T(0));
+      sm[XB] = (g.h2e * sm[BB] + sum) * g.dinv(dg);
     }
   }
 }
@@ -243,13 +244,12 @@ __device__ __forceinline__ void sw_relax_at(const SwGrid<T>& g, unsigned pbit, T
   if ((sb[Fi] & 7u) != pbit) return;  // regular: one phase, no sparse row
   if (kin && (unsigned)(i - 1) < (unsigned)(g.n0 - 2) && (unsigned)(j - 1) < (unsigned)(g.n1 - 2)) {
     const T sum = ((((sm[X - 1] + sm[X + 1]) + sm[X - SW_BX]) + sm[X + SW_BX]) + sm[M]) + sm[P];
-    sm[X] = (g.h2e * sm[Bi] + sum) * inv_count(6, T(0));
+    sm[X] = (g.h2e * sm[Bi] + sum) * g.idg;
     return;
   }
-  T sum;
-  int dg;
+  T sum, dg;
   sw_wall_at(g, sm, X, M, P, i, j, k, sum, dg);
-  sm[X] = (g.h2e * sm[Bi] + sum) * inv_count(dg, T(0));
+  sm[X] = (g.h2e * sm[Bi] + sum) * g.dinv(dg);
 }
 
 // Residual b - A x of the regular cell (i, j, k) at indices X, M, P, Bi,
@@ -260,12 +260,11 @@ __device__ __forceinline__ T sw_resid(const SwGrid<T>& g, const T* sm, int X, in
                                       int j, int k) {
   if (fast) {
     const T sum = ((((sm[X - 1] + sm[X + 1]) + sm[X - SW_BX]) + sm[X + SW_BX]) + sm[M]) + sm[P];
-    return sm[Bi] - g.ceps * ((T)6 * sm[X] - sum);
+    return sm[Bi] - g.ceps * ((T(6) + g.lh) * sm[X] - sum);
   }
-  T sum;
-  int dg;
+  T sum, dg;
   sw_wall_at(g, sm, X, M, P, i, j, k, sum, dg);
-  return sm[Bi] - g.ceps * ((T)dg * sm[X] - sum);
+  return sm[Bi] - g.ceps * ((dg + g.lh) * sm[X] - sum);
 }
 
 // The work items of a streamed pass over level l: item index r < nitems is

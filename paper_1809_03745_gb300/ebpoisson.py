@@ -45,7 +45,9 @@ class GeomDesc(C.Structure):
                 ("prims", C.POINTER(_Prim)), ("n_prims", C.c_int), ("nodes", C.POINTER(_Csg)), ("n_nodes", C.c_int),
                 ("electrode_root", C.c_int), ("n_electrodes", C.c_int), ("electrode_node", C.c_int * 4),
                 ("electrode_phi", C.c_double * 4), ("dielectric_root", C.c_int), ("eps_gas", C.c_double),
-                ("eps_diel", C.c_double), ("bc_type", C.c_int * 6), ("bc_value", C.c_double * 6)]
+                ("eps_diel", C.c_double), ("bc_type", C.c_int * 6), ("bc_value", C.c_double * 6),
+                ("bc_robin", C.c_double * 12), ("electrode_robin", C.c_int), ("electrode_robin_a", C.c_double * 2),
+                ("helmholtz_lam", C.c_double * 2)]
 
 
 class GeomInfo(C.Structure):
@@ -225,6 +227,16 @@ def make_desc(desc: dict):
     for k in range(6):
         d.bc_type[k] = int(desc["bc"][k])
         d.bc_value[k] = float(desc.get("phi_wall", [0.0] * 6)[k])
+    rob = desc.get("robin")
+    if rob is not None:  # Robin walls: a1, a2 per side (phi_wall holds a3)
+        for k in range(6):
+            d.bc_robin[2 * k], d.bc_robin[2 * k + 1] = float(rob[k][0]), float(rob[k][1])
+    ebr = desc.get("eb_robin")
+    if ebr is not None:  # Robin electrodes: a1, a2 (the electrode values are a3)
+        d.electrode_robin = 1
+        d.electrode_robin_a[0], d.electrode_robin_a[1] = float(ebr[0]), float(ebr[1])
+    lam = desc.get("lam", (0.0, 0.0))
+    d.helmholtz_lam[0], d.helmholtz_lam[1] = float(lam[0]), float(lam[1])
     return d, (prims, nodes)
 
 

@@ -41,8 +41,16 @@ PRIM_BOX = 5        # [lox, loy, loz, hix, hiy, hiz]       max_k max(lo_k - x_k,
 
 CSG_PRIM, CSG_UNION, CSG_INTERSECT, CSG_NEGATE = 0, 1, 2, 3
 
-NEUMANN, DIRICHLET = 0, 1
+NEUMANN, DIRICHLET, ROBIN = 0, 1, 2
 SEED_BASE = 1809
+
+# Three-group photoionisation model for oxygen (the paper's photoionisation
+# table): per group lambda_gamma and A_gamma in 1/(m Pa); kappa_gamma =
+# lambda_gamma p_O2 / sqrt(3) with p_O2 = 0.2 bar; S_ph = nu_eff p_O2 sum
+# A_gamma Psi_gamma with nu_eff = 0.1.
+PHOTO_GROUPS = ((4.15e-2, 1.12e-4), (1.09e-1, 2.88e-3), (6.69e-1, 2.76e-1))
+PHOTO_P_O2 = 2.0e4
+PHOTO_NU_EFF = 0.1
 
 
 def _desc(dim, n, lo, h, prims, nodes, root_E, root_D, eps, bc, phi_E, phi_wall, electrodes=None):
@@ -281,3 +289,57 @@ def batched_instances(count=64, seed=SEED_BASE + 4, *, n2=(64, 1024), n3=(32, 19
         S[0] = s
         out.append((desc, S, np.zeros(s.size)))
     return out
+
+
+def photo_kappa(group):
+    """kappa_gamma [1/m] of photoionisation group 0, 1 or 2."""
+    return PHOTO_GROUPS[group][0] * PHOTO_P_O2 / math.sqrt(3.0)
+
+
+def rte_desc(dim, n, kappa_L):
+    """One Eddington (SP1) photon group in the stationary form of Sec. 2.3 on
+    the rod-plane (2D) or pin-plane (3D) geometry scaled to the unit box:
+    kappa Psi - div(grad Psi / (3 kappa)) = eta / c becomes, per unit length
+    L of the box and after a factor 3 kappa L^2, lam Psi - lap Psi = s with
+    lam = 3 (kappa L)^2 (eps = 1).  Photons leave through every boundary of
+    the gas: the walls, the electrode and the dielectric (merged with the
+    electrode into one solid here), with the outflow condition dPsi/dn + 3
+    kappa / 2 Psi = 0, i.e. Robin a1 = 1.5 kappa L, a2 = 1, a3 = 0."""
+    if dim == 2:
+        d = rod_plane_2d(n, dielectric=True)
+    else:
+        d = pin_plane_3d(n)
+    # the electrode and the dielectric as one solid: union of the two primitives
+    d["nodes"] = list(d["nodes"]) + [(CSG_UNION, 0, 1)]
+    d["root_E"], d["root_D"] = len(d["nodes"]) - 1, -1
+    d["electrodes"] = [(d["root_E"], 0.0)]
+    d["phi_E"] = 0.0
+    d["eps"] = (1.0, 1.0)
+    a1 = 1.5 * kappa_L
+    d["bc"] = [ROBIN] * (2 * dim) + [NEUMANN] * (6 - 2 * dim)
+    d["robin"] = [(a1, 1.0)] * 6
+    d["phi_wall"] = [0.0] * 6
+    d["eb_robin"] = (a1, 1.0)
+    d["lam"] = (3.0 * kappa_L ** 2, 0.0)
+    return d
+
+
+def photo_inputs(dim, n, L=0.02, peak=1.0):
+    """The three photon groups on an L-sized box: per group (desc, S, sigma)
+    with the source s = 3 kappa L^2 eta / c of a Gaussian emission region of
+    width 0.03 below the tip (peak eta / c = peak), and the weights w_gamma =
+    nu_eff p_O2 A_gamma of S_ph = sum w_gamma Psi_gamma."""
+    out, w = [], []
+    for gi in range(3):
+        kap = photo_kappa(gi)
+        d = rte_desc(dim, n, kap * L)
+        x, y, z = cell_centres(d)
+        if dim == 2:
+            eta = peak * np.exp(-((x - 0.5) ** 2 + (y - 0.42) ** 2) / (2 * 0.03 ** 2))
+        else:
+            eta = peak * np.exp(-((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.42) ** 2) / (2 * 0.03 ** 2))
+        S = np.zeros((2, eta.size))
+        S[0] = 3.0 * kap * L * L * eta
+        out.append((d, S, np.zeros(eta.size)))
+        w.append(PHOTO_NU_EFF * PHOTO_P_O2 * PHOTO_GROUPS[gi][1])
+    return out, w
