@@ -17,9 +17,17 @@ With --trace c1|c2|c3 it instead prints where one V-cycle's time goes: the
 persistent kernel's phase stamps of the first V-cycle (eb_poisson_trace),
 summed per level and phase kind, and the grid-barrier cost.
 
+With --composite N it runs one C3 composite solve at N^3 + (N/2)^3 (after
+the set-up, no warm-up), and with --kernels N the large-grid kernels on their
+own on the N^3 pin-plane finest level (the tile-streamed sweep, one colour
+pass, the tile-streamed and the block residual + restriction, `--reps`
+launches each): the small, bounded programs the ncu captures run.
+
 Usage: python -m paper_1809_03745_gb300.bench_configs [--only C1 C2 C3 C4]
        python -m paper_1809_03745_gb300.bench_configs --trace c2 [--n N] [--precision mixed|fp64]
        python -m paper_1809_03745_gb300.bench_configs --peaks   (measured FP64 / FP32 FMA rates)
+       python -m paper_1809_03745_gb300.bench_configs --composite 256
+       python -m paper_1809_03745_gb300.bench_configs --kernels 384 [--reps 20]
 """
 from __future__ import annotations
 
@@ -147,6 +155,29 @@ def trace(workload, n=None, precision="mixed"):
     print(f"  grid barrier: {P.profile(2, 1000)[0] * 1e3:.2f} us")
 
 
+def composite_once(n):
+    """One C3 composite solve at n^3 + (n/2)^3 right after the set-up."""
+    d, lo, hi, Sc, sc, Sf, sf = W.c3_amr_inputs(n)
+    G = E.Composite(d, lo, hi, precision="mixed", tol=1e-10, max_cycles=200)
+    args = [torch.from_numpy(a).cuda() for a in (Sc, Sf, sc, sf)]
+    _, _, info = G.solve(*args)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": f"C3 composite {n}^3 + {n // 2}^3 box, one solve", "status": info["status"],
+                      "outer_iters": info["outer_iters"], "vcycles": info["vcycles"], "rel_res": info["rel_res"],
+                      "kernel_launches": info["kernel_launches"], "kernel_stats": G.kernel_stats()}), flush=True)
+
+
+def kernels_once(n, reps):
+    """The large-grid kernels of the n^3 pin-plane finest level, each launched
+    on its own (eb_poisson_profile kernels 4, 0, 5, 1)."""
+    P = E.Poisson(E.Geometry(W.pin_plane_3d(n)), precision="mixed", tol=1e-10, max_cycles=1)
+    names = {4: "streamed sweep", 0: "colour pass", 5: "streamed residual + restriction",
+             1: "block residual + restriction"}
+    for k in (4, 0, 5, 1):
+        ms, by = P.profile(k, reps=reps)
+        print(json.dumps({"kernel": names[k], "n": n, "ms": ms, "gbs": by / ms / 1e6}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", nargs="+", default=["C1", "C2", "C3", "C4"])
@@ -154,8 +185,17 @@ def main():
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--peaks", action="store_true")
+    ap.add_argument("--composite", type=int, default=None)
+    ap.add_argument("--kernels", type=int, default=None)
+    ap.add_argument("--reps", type=int, default=20)
     args = ap.parse_args()
     E.load()
+    if args.composite:
+        composite_once(args.composite)
+        return
+    if args.kernels:
+        kernels_once(args.kernels, args.reps)
+        return
     if args.peaks:
         f64, f32 = E.device_fma_rates(torch.cuda.current_device())
         print(json.dumps({"fp64_fma_tflops": f64, "fp32_fma_tflops": f32}), flush=True)
