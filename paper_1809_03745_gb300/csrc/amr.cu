@@ -606,12 +606,18 @@ static void cv_axpby(eb_amr* A, double a, const CVec& x, double b, const CVec& y
   note_launch();
 }
 
-// h[i] = (V[i], w) for i < m, both grids, one launch per grid and one sync
-static void cv_mdot(eb_amr* A, int m, const CVec& w, double* h, cudaStream_t s) {
+// h[i] = (V[i], w) for i < m, both grids, one launch per grid and one sync;
+// with `self` also h[m] = (w, w), from the same pass over w
+static void cv_mdot(eb_amr* A, int m, const CVec& w, double* h, cudaStream_t s, bool self = false) {
   CVPtrs pc{}, pf{};
   for (int i = 0; i < m; ++i) {
     pc.v[i] = A->V[i].c;
     pf.v[i] = A->V[i].f;
+  }
+  if (self) {
+    pc.v[m] = w.c;
+    pf.v[m] = w.f;
+    ++m;
   }
   k_cv_mdot<<<DOT_BLOCKS, TBA, 0, s>>>(A->B, A->cflags, A->ncc, 1, m, pc, w.c, A->d_part);
   note_launch();
@@ -784,15 +790,24 @@ extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double
       s2 = fac_apply(A, A->V[k], A->Z[k], &cycles, s);
       if (s2 == EB_OK) s2 = op_apply(A, A->Z[k], A->V[k + 1], s);
       if (s2 != EB_OK) break;
-      // classical Gram-Schmidt twice: all k + 1 projections in one pass, twice
+      // classical Gram-Schmidt, all k + 1 projections in one pass, repeated
+      // only when the pass removed most of w (the criterion of Daniel, Gragg,
+      // Kaufman and Stewart: the new norm below 1/sqrt(2) of the old one,
+      // where cancellation may have left w short of orthogonal)
       for (int i = 0; i <= k; ++i) H[i][k] = 0.0;
-      for (int pass = 0; pass < 2; ++pass) {
-        double hp[CV_MAXV];
+      double hp[CV_MAXV];
+      cv_mdot(A, k + 1, A->V[k + 1], hp, s, true);  // (V_i, w) and (w, w)
+      const double w0 = std::sqrt(std::max(hp[k + 1], 0.0));
+      cv_maxpy(A, k + 1, hp, A->V[k + 1], s);
+      for (int i = 0; i <= k; ++i) H[i][k] += hp[i];
+      double w1 = std::sqrt(cv_dot(A, A->V[k + 1], A->V[k + 1], s));
+      if (w1 < w0 / std::sqrt(2.0)) {
         cv_mdot(A, k + 1, A->V[k + 1], hp, s);
         cv_maxpy(A, k + 1, hp, A->V[k + 1], s);
         for (int i = 0; i <= k; ++i) H[i][k] += hp[i];
+        w1 = std::sqrt(cv_dot(A, A->V[k + 1], A->V[k + 1], s));
       }
-      H[k + 1][k] = std::sqrt(cv_dot(A, A->V[k + 1], A->V[k + 1], s));
+      H[k + 1][k] = w1;
       if (H[k + 1][k] > 0.0) cv_axpby(A, 0.0, A->V[k + 1], 1.0 / H[k + 1][k], A->V[k + 1], s);
       for (int i = 0; i < k; ++i) {  // earlier rotations
         double t = cs[i] * H[i][k] + sn[i] * H[i + 1][k];

@@ -87,11 +87,16 @@ __device__ __forceinline__ void reg_stencil(const Op<T>& o, const T* x, const in
   }
 }
 
+// Correctly rounded reciprocals (the same value as 1 / x, without a general
+// division's code inlined at every call site).
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 // 1 / (dg + lh[p]), the reciprocal diagonal of a regular cell of phase p
 // whose stencil gave dg: the stored value for a cell away from the walls.
 template <class T>
 __device__ __forceinline__ T diag_inv(const Op<T>& o, int p, T dg) {
-  return dg == T(2 * o.D) ? o.idg[p] : T(1) / (dg + o.lh[p]);
+  return dg == T(2 * o.D) ? o.idg[p] : rcp_rn(dg + o.lh[p]);
 }
 
 template <class T>
@@ -149,6 +154,35 @@ __device__ __forceinline__ double row_dot(const Op<T>& o, long long r) {
     for (int k = 0; k < 8; ++k) xv[k] = (e + k < e1) ? o.x[cl[k] >> 30][cl[k] & 0x3fffffffu] : T(0);
 #pragma unroll
     for (int k = 0; k < 8; ++k) s += v[k] * (double)xv[k];
+  }
+  return s;
+}
+
+// The same sum in the arithmetic of T: the FP32 V-cycle's levels inside one
+// CTA, where a single SM does every row and FP64 issues at a small fraction
+// of the FP32 rate.  The coefficients are rounded to T on load; the result
+// is rounded to T in either case.
+template <class T>
+__device__ __forceinline__ T row_dot_t(const Op<T>& o, long long r) {
+  T s = T(0);
+  const int e0 = o.row_ptr[r], e1 = o.row_ptr[r + 1];
+  for (int e = e0; e < e1; e += 8) {
+    unsigned cl[8];
+    T v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      cl[k] = 0u;
+      v[k] = T(0);
+      if (e + k < e1) {
+        cl[k] = (unsigned)o.col[e + k];
+        v[k] = (T)o.val[e + k];
+      }
+    }
+    T xv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) xv[k] = (e + k < e1) ? o.x[cl[k] >> 30][cl[k] & 0x3fffffffu] : T(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += v[k] * xv[k];
   }
   return s;
 }

@@ -433,30 +433,47 @@ __device__ __forceinline__ void ph_rows(const Op<T>& o, long long rb, long long 
       if (d == 0.0) continue;
       long long cell = o.irr_cell[r >> 1];
       int p = (int)(r & 1);
-      double v = (double)o.b[p][cell] - row_dot(o, r);
-      o.tmp[r] = mode == 0 ? (T)(v / d) : (T)(v - d * (double)o.x[p][cell]);
+      if constexpr (sizeof(T) == 4) {  // the FP32 V-cycle: rows in FP32 on its one-SM levels
+        const T v = o.b[p][cell] - row_dot_t(o, r);
+        o.tmp[r] = mode == 0 ? v / (T)d : v - (T)d * o.x[p][cell];
+      } else {
+        double v = (double)o.b[p][cell] - row_dot(o, r);
+        o.tmp[r] = mode == 0 ? (T)(v / d) : (T)(v - d * (double)o.x[p][cell]);
+      }
     }
     return;
   }
-  const int lane = threadIdx.x & 31;
-  const long long w0 = c.local ? (threadIdx.x >> 5) : (long long)(threadIdx.x >> 5) * c.gsize + c.gcta;
-  const long long ws = c.local ? (blockDim.x >> 5) : (long long)c.gsize * (blockDim.x >> 5);
-  for (long long r = rb + w0; r < re; r += ws) {
+  // a group of 8 lanes per row, four rows per warp in flight: a row's cost
+  // is a chain of dependent loads (descriptors, entries, gathered x), so
+  // rows overlap rather than lanes splitting one row's few entries.  Lane
+  // g of a group takes the row's entries e0 + g, e0 + g + 8, ... and the
+  // group sums them in a fixed order, whatever warp takes the row.
+  constexpr int GL = 8;
+  const int g = threadIdx.x & (GL - 1);
+  const long long grp = threadIdx.x / GL, ngrp = blockDim.x / GL;
+  const long long w0 = grp * c.gsize + c.gcta, ws = (long long)c.gsize * ngrp;
+  const unsigned gmask = 0xffu << (threadIdx.x & 24);
+  const long long rend = rb + ((re - rb + ws - 1) / ws) * ws;  // every lane of a warp runs the same trips
+  for (long long r = rb + w0; r < rend; r += ws) {
+    const bool live = r < re;
     // the row's descriptors in one round of independent loads, then its
     // entries together with the cell's own b and x, then the gathered x
-    const double d = o.diag[r];
-    const int e0 = o.row_ptr[r], e1 = o.row_ptr[r + 1];
-    const long long cell = o.irr_cell[r >> 1];
-    if (d == 0.0) continue;
+    const double d = live ? o.diag[r] : 0.0;
+    const int e0 = live ? o.row_ptr[r] : 0, e1 = live ? o.row_ptr[r + 1] : 0;
+    const long long cell = live ? o.irr_cell[r >> 1] : 0;
+    const bool act = d != 0.0;
     const int p = (int)(r & 1);
-    const double bc = (double)o.b[p][cell], xc = (double)o.x[p][cell];
-    double s = 0.0;
-    for (int e = e0 + lane; e < e1; e += 32) {
-      unsigned cl = (unsigned)o.col[e];
-      s += o.val[e] * (double)o.x[cl >> 30][cl & 0x3fffffffu];
+    double bc = 0.0, xc = 0.0, s = 0.0;
+    if (act) {
+      bc = (double)o.b[p][cell];
+      xc = (double)o.x[p][cell];
+      for (int e = e0 + g; e < e1; e += GL) {
+        unsigned cl = (unsigned)o.col[e];
+        s += o.val[e] * (double)o.x[cl >> 30][cl & 0x3fffffffu];
+      }
     }
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) {
+    for (int off = GL / 2; off > 0; off >>= 1) s += __shfl_xor_sync(gmask, s, off);
+    if (act && g == 0) {
       double v = bc - s;
       o.tmp[r] = mode == 0 ? (T)(v / d) : (T)(v - d * xc);
     }
@@ -811,10 +828,13 @@ __device__ bool ph_smooth(const Op<T>& o, int nu, const Ctx& c, int l) {
 // pass over the level, and the black cut cells.  Within each of the four
 // groups no cell reads another's new value except through the colour order,
 // as in the colour passes.
-template <class T>
+// SW: the kernel carries the tile-streamed passes (an instantiation without
+// them keeps their out-of-line calls, and the registers those cost around
+// the call sites, out of every other solve).
+template <class T, bool SW>
 __device__ bool ph_smooth_grid(const Hier<T>& H, int l, int nu, const Ctx& c) {
   const Op<T>& o = H.op[l];
-  if (!H.sw[l].on || c.local || c.gsize < 2) return ph_smooth(o, nu, c, l);
+  if (!SW || !H.sw[l].on || c.local || c.gsize < 2) return ph_smooth(o, nu, c, l);
   const long long rr = 2 * o.nirr_red, rn = 2 * o.nirr;
   for (int s = 0; s < nu; ++s) {
     if (rr > 0) {
@@ -1083,16 +1103,16 @@ __device__ bool ph_bicgstab_grid(const Hier<T>& H, const Ctx& c) {
   return true;
 }
 
-template <class T>
+template <class T, bool SW>
 __device__ bool vcycle_dev(const Hier<T>& H, const Op<T>* lop, const Ctx& G) {
   for (int l = 0; l < H.lc; ++l) {
     const Op<T>& o = H.op[l];
-    if (!ph_smooth_grid(H, l, H.nu1, G)) return false;
+    if (!ph_smooth_grid<T, SW>(H, l, H.nu1, G)) return false;
     if (o.nirr) {
       ph_rows(o, 0, 2 * o.nirr, 1, G);
       if (!G.sync((l << 4) | 5)) return false;
     }
-    if (H.sw[l].on && H.sw[l].rs && G.gsize >= 2 && o.n[0] == 2 * H.op[l + 1].n[0] && o.n[1] == 2 * H.op[l + 1].n[1] &&
+    if (SW && H.sw[l].on && H.sw[l].rs && G.gsize >= 2 && o.n[0] == 2 * H.op[l + 1].n[0] && o.n[1] == 2 * H.op[l + 1].n[1] &&
         o.n[2] == 2 * H.op[l + 1].n[2]) {
       if (!ph_restrict3d(H, l, G)) return false;
     } else {
@@ -1115,7 +1135,7 @@ __device__ bool vcycle_dev(const Hier<T>& H, const Op<T>* lop, const Ctx& G) {
   for (int l = H.lc - 1; l >= 0; --l) {
     ph_prolong(H.op[l], H.op[l + 1], G);
     if (!G.sync((l << 4) | 7)) return false;
-    if (!ph_smooth_grid(H, l, H.nu2, G)) return false;
+    if (!ph_smooth_grid<T, SW>(H, l, H.nu2, G)) return false;
   }
   return true;
 }
@@ -1172,7 +1192,21 @@ __device__ __forceinline__ void stage_words(unsigned char* dst, const void* src,
   for (long long i = threadIdx.x; i < words; i += blockDim.x) d[i] = s[i];
 }
 
-template <class T>
+// The V-cycle as the FP64 solve calls it: out of line, which keeps ptxas
+// from spilling the FP64 V-cycle's registers into the outer loop (1276 bytes
+// of spills inlined, 92 out of line); the FP32 V-cycle stays inline (64
+// bytes inlined, 92 out of line).
+template <class T, bool SW>
+__device__ __noinline__ bool vcycle_dev_ool(const Hier<T>& H, const Op<T>* lop, const Ctx& G) {
+  return vcycle_dev<T, SW>(H, lop, G);
+}
+template <class T, bool SW>
+__device__ __forceinline__ bool vcycle_call(const Hier<T>& H, const Op<T>* lop, const Ctx& G) {
+  if constexpr (sizeof(T) == 8) return vcycle_dev_ool<T, SW>(H, lop, G);
+  else return vcycle_dev<T, SW>(H, lop, G);
+}
+
+template <class T, bool SW>
 __device__ __forceinline__ void solve_group(const Hier<T>* __restrict__ Hg, const Op<double>* __restrict__ Fg,
                                             const SolveCtl& ctl, const Barrier& B, int gcta, int gsize) {
   __shared__ Hier<T> H;
@@ -1268,7 +1302,7 @@ __device__ __forceinline__ void solve_group(const Hier<T>* __restrict__ Hg, cons
         Gk.tr = ctl.trace;
         if (gcta == 0 && threadIdx.x == 0) ctl.trace[1 + tn++] = ((unsigned long long)0xfff << 48) | (now_ns() & 0xffffffffffffULL);
       }
-      ok = vcycle_dev(H, lop, Gk);
+      ok = vcycle_call<T, SW>(H, lop, Gk);
     }
     if (ok && ctl.mixed) {
       ph_update64(F, H.op[0], G);
@@ -1291,10 +1325,10 @@ __device__ __forceinline__ void solve_group(const Hier<T>* __restrict__ Hg, cons
   }
 }
 
-template <class T>
+template <class T, bool SW>
 __global__ void __launch_bounds__(PT, 1) k_solve(const Hier<T>* __restrict__ Hg, const Op<double>* __restrict__ Fg,
                                                  SolveCtl ctl, Barrier B) {
-  solve_group(Hg, Fg, ctl, B, (int)blockIdx.x, (int)gridDim.x);
+  solve_group<T, SW>(Hg, Fg, ctl, B, (int)blockIdx.x, (int)gridDim.x);
 }
 
 // one instance of a batched solve: its hierarchy, fine operator, controls,
@@ -1310,11 +1344,11 @@ struct BatchItem {
 
 // Many independent solves in one cooperative launch: each CTA finds its
 // instance and runs the solve with the instance's own group barrier.
-template <class T>
+template <class T, bool SW>
 __global__ void __launch_bounds__(PT, 1) k_solve_batch(const BatchItem<T>* __restrict__ items,
                                                        const int* __restrict__ cta_item) {
   const BatchItem<T>& it = items[cta_item[blockIdx.x]];
-  solve_group(it.H, it.F, it.ctl, it.B, (int)blockIdx.x - it.start, it.size);
+  solve_group<T, SW>(it.H, it.F, it.ctl, it.B, (int)blockIdx.x - it.start, it.size);
 }
 
 // Setup of the tile-streamed passes: one CTA per (tile, plane).  Entry

@@ -853,6 +853,18 @@ static eb_status build_hier(eb_poisson* P, std::vector<Op<T>>& ops) {
   return st;
 }
 
+// The persistent kernels in two builds: with the tile-streamed passes (FP32
+// hierarchies that have streamed levels) and without them, so that every
+// other solve runs the lean build.
+static const void* solve_kernel(bool mixed, bool sw) {
+  if (!mixed) return (const void*)k_solve<double, false>;
+  return sw ? (const void*)k_solve<float, true> : (const void*)k_solve<float, false>;
+}
+static const void* batch_kernel(bool mixed, bool sw) {
+  if (!mixed) return (const void*)k_solve_batch<double, false>;
+  return sw ? (const void*)k_solve_batch<float, true> : (const void*)k_solve_batch<float, false>;
+}
+
 static eb_status setup_persistent(eb_poisson* P) {
   int dev = P->G->device, coop = 0, nsm = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
@@ -874,23 +886,19 @@ static eb_status setup_persistent(eb_poisson* P) {
   if (e != cudaSuccess) return cuda_fail(e, "persistent setup");
   if (!coop || P->o.launch_mode != 0) return EB_OK;  // per-phase kernels
   int per_sm = 0, smax = 0;
-  const void* fn = mixed ? (const void*)k_solve<float> : (const void*)k_solve<double>;
+  const bool sw = P->sweep_levels > 0;
+  const void* fn = solve_kernel(mixed, sw);
   // the attribute is per kernel, shared by every handle: allow the device maximum once
   cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   smax -= 16 * 1024;  // headroom for the kernel's static shared memory
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-  if (e == cudaSuccess) {
-    const void* fb = mixed ? (const void*)k_solve_batch<float> : (const void*)k_solve_batch<double>;
-    e = cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-  }
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel(mixed, sw), cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
   if (e == cudaSuccess && P->sweep_levels)
     e = cudaFuncSetAttribute((const void*)k_sweep_phase<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
   if (e == cudaSuccess && P->sweep_levels)
     e = cudaFuncSetAttribute((const void*)k_restrict3d_phase<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              smax);
-  if (e == cudaSuccess)
-    e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<float>, PT, P->smem_bytes)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<double>, PT, P->smem_bytes);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PT, P->smem_bytes);
   if (e != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return EB_OK;
@@ -938,7 +946,7 @@ static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cyc
     args[1] = (void*)&F;
     args[2] = (void*)&ctl;
     args[3] = (void*)&B;
-    e = cudaLaunchCooperativeKernel((const void*)k_solve<float>, dim3(P->grid), dim3(PT), args, dyn, s);
+    e = cudaLaunchCooperativeKernel(solve_kernel(true, P->sweep_levels > 0), dim3(P->grid), dim3(PT), args, dyn, s);
   } else {
     const Hier<double>* H = (const Hier<double>*)P->d_hier;
     const Op<double>* F = P->d_fine;
@@ -946,7 +954,7 @@ static eb_status solve_persistent(eb_poisson* P, double* r, int* iters, int* cyc
     args[1] = (void*)&F;
     args[2] = (void*)&ctl;
     args[3] = (void*)&B;
-    e = cudaLaunchCooperativeKernel((const void*)k_solve<double>, dim3(P->grid), dim3(PT), args, dyn, s);
+    e = cudaLaunchCooperativeKernel(solve_kernel(false, false), dim3(P->grid), dim3(PT), args, dyn, s);
   }
   counted();
   cudaEventRecord(P->kev[1], s);
@@ -1329,7 +1337,10 @@ static eb_status launch_batch_t(eb_poisson* const* P, int n, int max_iters, int 
   if (e == cudaSuccess) {
     void* args[2] = {(void*)&d_items, (void*)&d_cta};
     cudaEventRecord(P[0]->kev[0], s);
-    e = cudaLaunchCooperativeKernel((const void*)k_solve_batch<T>, dim3(start), dim3(PT), args, (size_t)smem, s);
+    bool sw = false;
+    for (int i = 0; i < n; ++i) sw = sw || P[i]->sweep_levels > 0;
+    e = cudaLaunchCooperativeKernel(batch_kernel(std::is_same<T, float>::value, sw), dim3(start), dim3(PT), args,
+                                    (size_t)smem, s);
     cudaEventRecord(P[0]->kev[1], s);
     counted();
   }
@@ -1421,8 +1432,9 @@ eb_status batch_step(eb_poisson* const* P, int n, const double* const* rhs, cons
   int nsm = 0, per_sm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P[0]->G->device);
   cudaError_t e = cudaSuccess;
-  e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch<float>, PT, smem)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch<double>, PT, smem);
+  bool sw = false;
+  for (int i = 0; i < n; ++i) sw = sw || P[i]->sweep_levels > 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(mixed, sw), PT, smem);
   if (e != cudaSuccess || per_sm < 1) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e, "batch occupancy");
   int total = nsm * std::min(per_sm, 1);
   if (fresh)

@@ -116,7 +116,7 @@ struct SwGrid {
     idg = o.idg[p];
   }
   // 1 / (dg + lh) for a cell whose stencil gave dg (dg = 6 away from the walls)
-  __device__ __forceinline__ T dinv(T dg) const { return dg == T(6) ? idg : T(1) / (dg + lh); }
+  __device__ __forceinline__ T dinv(T dg) const { return dg == T(6) ? idg : rcp_rn(dg + lh); }
 };
 
 // Implicit stencil sum and diagonal count of reg_stencil, same terms in the
