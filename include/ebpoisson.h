@@ -295,7 +295,9 @@ eb_status eb_field_eval(eb_poisson* P, const double* d_phi, const double* d_sigm
  * the red-black Gauss-Seidel sweep (regular cells) of the inner-precision finest level
  * (bytes: half of read x, read b, write x, read flags per cell); kernel 1: the
  * fused residual + restriction of that level (read x, b, flags per fine cell,
- * write coarse b and x). */
+ * write coarse b and x); kernel 6: the prolongation of the next level's
+ * correction onto it (read and write x, read the flags per fine cell, read
+ * the coarse x and flags). */
 eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, double* ms_per_launch, double* bytes_per_launch,
                              void* stream);
 /* kernel 2 of eb_poisson_profile times `reps` grid barriers of the persistent
@@ -303,7 +305,11 @@ eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, double* ms_per
  * the bounded-wait self-test: two CTAs wait at a grid barrier sized for
  * three, so the wait ends only by its clock bound (about 2 s); the call then
  * returns EB_ERR_TIMEOUT with ms_per_launch the kernel's duration, and the
- * context stays usable. */
+ * context stays usable.  Kernels 4 and 5 need a finest level relaxed by
+ * tile-streamed sweeps (EB_ERR_UNSUPPORTED otherwise): 4 is one such sweep,
+ * both colours in one pass (bytes: read x, b, flags, write x per cell), 5 the
+ * tile-streamed residual + restriction (read x, b, flags per fine cell, write
+ * coarse b and x); a wait of theirs that gives up returns EB_ERR_TIMEOUT. */
 
 /* Benchmark hook (no counterpart in the paper): the device's measured rate
  * of fused multiply-adds in FP64 and in FP32, in TFLOP/s (two flops per

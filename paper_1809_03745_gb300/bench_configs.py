@@ -20,8 +20,8 @@ summed per level and phase kind, and the grid-barrier cost.
 With --composite N it runs one C3 composite solve at N^3 + (N/2)^3 (after
 the set-up, no warm-up), and with --kernels N the large-grid kernels on their
 own on the N^3 pin-plane finest level (the tile-streamed sweep, one colour
-pass, the tile-streamed and the block residual + restriction, `--reps`
-launches each): the small, bounded programs the ncu captures run.
+pass, the tile-streamed and the block residual + restriction, the block
+prolongation, `--reps` launches each): the small, bounded programs the ncu captures run.
 
 Usage: python -m paper_1809_03745_gb300.bench_configs [--only C1 C2 C3 C4]
        python -m paper_1809_03745_gb300.bench_configs --trace c2 [--n N] [--precision mixed|fp64]
@@ -172,9 +172,13 @@ def kernels_once(n, reps):
     on its own (eb_poisson_profile kernels 4, 0, 5, 1)."""
     P = E.Poisson(E.Geometry(W.pin_plane_3d(n)), precision="mixed", tol=1e-10, max_cycles=1)
     names = {4: "streamed sweep", 0: "colour pass", 5: "streamed residual + restriction",
-             1: "block residual + restriction"}
-    for k in (4, 0, 5, 1):
-        ms, by = P.profile(k, reps=reps)
+             1: "block residual + restriction", 6: "block prolongation"}
+    for k in (4, 0, 5, 1, 6):
+        try:
+            ms, by = P.profile(k, reps=reps)
+        except E.EBError as exc:  # no streamed level below 2^25 cells
+            print(json.dumps({"kernel": names[k], "n": n, "skipped": str(exc)}), flush=True)
+            continue
         print(json.dumps({"kernel": names[k], "n": n, "ms": ms, "gbs": by / ms / 1e6}), flush=True)
 
 

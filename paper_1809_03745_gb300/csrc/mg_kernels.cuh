@@ -39,8 +39,10 @@ struct Op {
   // wall weight per side (xlo, xhi, ylo, yhi, zlo, zhi): 1 on a Dirichlet
   // wall, 0 on a Neumann wall, a1 / (a1 + 8 a2 / (3h)) on a Robin wall
   T wr[6];
+  T w3[6];   // wr / 3: the weight of the inward neighbour of a wall cell
   T lh[2];   // the Helmholtz shift per phase in the stencil's units: lam_p h^2 / eps_p
   T idg[2];  // 1 / (2D + lh[p]): the reciprocal diagonal of a cell away from the walls
+  int intdg;  // 1: every wall weight is 0 or 1 and no shift, so every diagonal is a small integer
   T* x[2];  // unknown per phase
   T* b[2];  // right-hand side per phase
   const uint8_t* flags;
@@ -62,29 +64,39 @@ struct Op {
 // second-order wall flux: w = 1 for Dirichlet; for Robin the wall value is
 // eliminated through the same formula.  A Neumann wall face (w = 0) adds
 // nothing.
+// The diagonal is counted as an integer (open faces, and 3 per Dirichlet
+// wall face when every weight is 0 or 1) and only fractional wall weights are
+// accumulated in T: on the FP64 path every extra operation per cell runs on
+// GB300's narrow FP64 pipe.
+template <class T>
+__device__ __forceinline__ void wall_term(const Op<T>& o, int side, T xin, T& sum, int& nf, T& wd) {
+  sum += xin * o.w3[side];
+  if (o.intdg) nf += 3;
+  else wd += T(3) * o.wr[side];
+}
+
 template <class T>
 __device__ __forceinline__ void reg_stencil(const Op<T>& o, const T* x, const int I[3], long long c, T& sum, T& dg) {
   sum = T(0);
-  dg = T(0);
+  int nf = 0;
+  T wd = T(0);
   long long st = 1;
-  const T third = T(1) / T(3);
   for (int a = 0; a < o.D; ++a) {
     if (I[a] > 0) {
       sum += x[c - st];
-      dg += T(1);
+      ++nf;
     } else if (o.wr[2 * a] != T(0)) {
-      sum += x[c + st] * (o.wr[2 * a] * third);
-      dg += T(3) * o.wr[2 * a];
+      wall_term(o, 2 * a, x[c + st], sum, nf, wd);
     }
     if (I[a] < o.n[a] - 1) {
       sum += x[c + st];
-      dg += T(1);
+      ++nf;
     } else if (o.wr[2 * a + 1] != T(0)) {
-      sum += x[c - st] * (o.wr[2 * a + 1] * third);
-      dg += T(3) * o.wr[2 * a + 1];
+      wall_term(o, 2 * a + 1, x[c - st], sum, nf, wd);
     }
     st *= o.n[a];
   }
+  dg = T(nf) + wd;
 }
 
 // Correctly rounded reciprocals (the same value as 1 / x, without a general
@@ -94,9 +106,32 @@ __device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
 
 // 1 / (dg + lh[p]), the reciprocal diagonal of a regular cell of phase p
 // whose stencil gave dg: the stored value for a cell away from the walls.
+// Reciprocals of the possible integer diagonals (faces + 3 per Dirichlet
+// wall face), as constants.
+__device__ __forceinline__ float inv_count(int d, float) { return 1.0f / (float)d; }
+__device__ __forceinline__ double inv_count(int d, double) {
+  switch (d) {
+    case 1: return 1.0;
+    case 2: return 0.5;
+    case 3: return 1.0 / 3.0;
+    case 4: return 0.25;
+    case 5: return 0.2;
+    case 6: return 1.0 / 6.0;
+    case 7: return 1.0 / 7.0;
+    case 8: return 0.125;
+    case 9: return 1.0 / 9.0;
+    case 10: return 0.1;
+    case 11: return 1.0 / 11.0;
+    case 12: return 1.0 / 12.0;
+    default: return 1.0 / (double)d;
+  }
+}
+
 template <class T>
 __device__ __forceinline__ T diag_inv(const Op<T>& o, int p, T dg) {
-  return dg == T(2 * o.D) ? o.idg[p] : rcp_rn(dg + o.lh[p]);
+  if (dg == T(2 * o.D)) return o.idg[p];
+  if (o.intdg) return inv_count((int)dg, T(0));
+  return rcp_rn(dg + o.lh[p]);
 }
 
 template <class T>

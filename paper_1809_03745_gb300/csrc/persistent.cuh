@@ -232,54 +232,48 @@ __device__ __forceinline__ void ld4(const T* p, T v[4]) {
 template <class T, int E>
 __device__ __forceinline__ T relax4(const Op<T>& o, int p, int i, int j, int k, const T xc[4], T xl, T xr,
                                     const T ym[4], const T yp[4], const T zm[4], const T zp[4], const T bv[4]) {
-  const T third = T(1) / T(3);
   T sum = T(0);
-  T dg = T(0);
+  int nf = 0;
+  T wd = T(0);
   if (i > 0) {
     sum += E > 0 ? xc[E > 0 ? E - 1 : 0] : xl;
-    dg += T(1);
+    ++nf;
   } else if (o.wr[0] != T(0)) {
-    sum += xc[E < 3 ? E + 1 : 3] * (o.wr[0] * third);
-    dg += T(3) * o.wr[0];
+    wall_term(o, 0, xc[E < 3 ? E + 1 : 3], sum, nf, wd);
   }
   if (i < o.n[0] - 1) {
     sum += E < 3 ? xc[E < 3 ? E + 1 : 3] : xr;
-    dg += T(1);
+    ++nf;
   } else if (o.wr[1] != T(0)) {
-    sum += xc[E > 0 ? E - 1 : 0] * (o.wr[1] * third);
-    dg += T(3) * o.wr[1];
+    wall_term(o, 1, xc[E > 0 ? E - 1 : 0], sum, nf, wd);
   }
   if (j > 0) {
     sum += ym[E];
-    dg += T(1);
+    ++nf;
   } else if (o.wr[2] != T(0)) {
-    sum += yp[E] * (o.wr[2] * third);
-    dg += T(3) * o.wr[2];
+    wall_term(o, 2, yp[E], sum, nf, wd);
   }
   if (j < o.n[1] - 1) {
     sum += yp[E];
-    dg += T(1);
+    ++nf;
   } else if (o.wr[3] != T(0)) {
-    sum += ym[E] * (o.wr[3] * third);
-    dg += T(3) * o.wr[3];
+    wall_term(o, 3, ym[E], sum, nf, wd);
   }
   if (o.D == 3) {
     if (k > 0) {
       sum += zm[E];
-      dg += T(1);
+      ++nf;
     } else if (o.wr[4] != T(0)) {
-      sum += zp[E] * (o.wr[4] * third);
-      dg += T(3) * o.wr[4];
+      wall_term(o, 4, zp[E], sum, nf, wd);
     }
     if (k < o.n[2] - 1) {
       sum += zp[E];
-      dg += T(1);
+      ++nf;
     } else if (o.wr[5] != T(0)) {
-      sum += zm[E] * (o.wr[5] * third);
-      dg += T(3) * o.wr[5];
+      wall_term(o, 5, zm[E], sum, nf, wd);
     }
   }
-  return (o.h2e[p] * bv[E] + sum) * diag_inv(o, p, dg);
+  return (o.h2e[p] * bv[E] + sum) * diag_inv(o, p, T(nf) + wd);
 }
 
 // Relaxed value of one regular cell by the scalar stencil (a group whose two
@@ -503,26 +497,30 @@ namespace ebp {
 template <class T, int D>
 __device__ __forceinline__ void ph_restrict_blk(const Op<T>& f, const Op<T>& co, const Ctx& c) {
   constexpr int NCH = 1 << D, NP = D == 3 ? 64 : 16;
-  const long long st[3] = {1, f.n[0], (long long)f.n[0] * f.n[1]};
-  const T scale = T(1) / T(NCH), third = T(1) / T(3);
+  // offsets within a coarse cell's children and their face halo fit in an
+  // int: 32-bit offsets from the first child keep the registers down
+  const int st[3] = {1, f.n[0], f.n[0] * f.n[1]};
+  const T scale = T(1) / T(NCH);
   for (long long C = c.i0; C < co.ncell; C += c.st) {
     int IC[3];
     ijk(co, C, IC);
     if (D == 2) IC[2] = 0;
     const int O[3] = {2 * IC[0], 2 * IC[1], 2 * IC[2]};
-    const long long c0 = O[0] + st[1] * O[1] + st[2] * O[2];
+    const long long c0 = O[0] + (long long)st[1] * O[1] + (long long)st[2] * O[2];
+    const uint8_t* const fl0 = f.flags + c0;
     unsigned fl[NCH];
     unsigned any = 0u;
 #pragma unroll
     for (int k = 0; k < NCH; ++k) {
-      fl[k] = f.flags[c0 + (k & 1) + st[1] * ((k >> 1) & 1) + (D == 3 ? st[2] * ((k >> 2) & 1) : 0)];
+      fl[k] = fl0[(k & 1) + st[1] * ((k >> 1) & 1) + (D == 3 ? st[2] * ((k >> 2) & 1) : 0)];
       any |= fl[k];
     }
     const unsigned cfl = co.flags[C];
     T acc[2] = {T(0), T(0)};
     for (int q = 0; q < 2; ++q) {
       if (!((any >> q) & 1u)) continue;
-      const T* x = f.x[q];
+      const T* x = f.x[q] + c0;
+      const T* bq = f.b[q] + c0;
       // patch value at local offset (u, v, w) in -1..2, loaded where it lies in the grid
       T P[NP];
       T bv[NCH];
@@ -534,12 +532,12 @@ __device__ __forceinline__ void ph_restrict_blk(const Op<T>& f, const Op<T>& co,
         if (out > 1) continue;  // corners and edges are never needed
         const bool in = O[0] + u >= 0 && O[0] + u < f.n[0] && O[1] + v >= 0 && O[1] + v < f.n[1] &&
                         (D == 2 || (O[2] + w >= 0 && O[2] + w < f.n[2]));
-        if (in) P[m] = x[c0 + u + st[1] * v + st[2] * w];
+        if (in) P[m] = x[u + st[1] * v + st[2] * w];
       }
 #pragma unroll
       for (int k = 0; k < NCH; ++k) {
-        const long long cc = c0 + (k & 1) + st[1] * ((k >> 1) & 1) + (D == 3 ? st[2] * ((k >> 2) & 1) : 0);
-        bv[k] = (((fl[k] >> q) & 1u) && !(fl[k] & F_IRR)) ? f.b[q][cc] : T(0);
+        const int ck = (k & 1) + st[1] * ((k >> 1) & 1) + (D == 3 ? st[2] * ((k >> 2) & 1) : 0);
+        bv[k] = (((fl[k] >> q) & 1u) && !(fl[k] & F_IRR)) ? bq[ck] : T(0);
       }
 #pragma unroll
       for (int k = 0; k < NCH; ++k) {
@@ -553,7 +551,8 @@ __device__ __forceinline__ void ph_restrict_blk(const Op<T>& f, const Op<T>& co,
           continue;
         }
 #define EBP_PIX(du, dv, dw) (((ku) + (du) + 1) + 4 * ((kv) + (dv) + 1) + 16 * ((kw) + (dw) + 1))
-        T sum = T(0), dg = T(0);
+        T sum = T(0), wd = T(0);
+        int nf = 0;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           const int e0 = a == 0, e1 = a == 1, e2 = a == 2;
@@ -561,23 +560,21 @@ __device__ __forceinline__ void ph_restrict_blk(const Op<T>& f, const Op<T>& co,
           const T hi = P[D == 3 ? EBP_PIX(e0, e1, e2) : EBP_PIX(e0, e1, 0) - 16];
           if (I[a] > 0) {
             sum += lo;
-            dg += T(1);
+            ++nf;
           } else if (f.wr[2 * a] != T(0)) {
-            sum += hi * (f.wr[2 * a] * third);
-            dg += T(3) * f.wr[2 * a];
+            wall_term(f, 2 * a, hi, sum, nf, wd);
           }
           if (I[a] < f.n[a] - 1) {
             sum += hi;
-            dg += T(1);
+            ++nf;
           } else if (f.wr[2 * a + 1] != T(0)) {
-            sum += lo * (f.wr[2 * a + 1] * third);
-            dg += T(3) * f.wr[2 * a + 1];
+            wall_term(f, 2 * a + 1, lo, sum, nf, wd);
           }
         }
         const T xc = P[D == 3 ? EBP_PIX(0, 0, 0) : EBP_PIX(0, 0, 0) - 16];
 #undef EBP_PIX
         (void)loc;
-        acc[q] += bv[k] - f.ceps[q] * ((dg + f.lh[q]) * xc - sum);
+        acc[q] += bv[k] - f.ceps[q] * ((T(nf) + wd + f.lh[q]) * xc - sum);
       }
     }
     for (int p = 0; p < 2; ++p) {
@@ -668,75 +665,88 @@ __device__ __forceinline__ T prolong_value(const Op<T>& f, const Op<T>& co, long
 // carry) and the children's flags and values are loaded in one round; each
 // child then gets the (bi/tri)linear value of prolong_value, same weights in
 // the same order, or the constant one.  Needs fine n = 2 coarse n per axis.
+// Neighbours and children are reached by 32-bit offsets from the cell (the
+// offsets of a 3^D neighbourhood and of the children fit in an int), which
+// keeps the persistent kernel's register use down (no spills with them, 64
+// bytes with 64-bit indices per neighbour).
+template <class T, int D>
+__device__ __forceinline__ void prolong_cell(const Op<T>& f, const Op<T>& co, long long C, const int IC[3]) {
+  constexpr int NB = D == 3 ? 27 : 9, NCH = 1 << D;
+  const int sc1 = co.n[0], sc2 = co.n[0] * co.n[1];
+  const int sf1 = f.n[0], sf2 = f.n[0] * f.n[1];
+  const long long F0 = (long long)(2 * IC[0]) + (long long)sf1 * (2 * IC[1]) + (D == 3 ? (long long)sf2 * (2 * IC[2]) : 0);
+  // children's flags and the coarse neighbourhood's, as one bit mask per phase
+  int cf[NCH];
+  unsigned fm[2] = {0u, 0u}, cm[2] = {0u, 0u};
+  const uint8_t* const ffl = f.flags + F0;
+#pragma unroll
+  for (int k = 0; k < NCH; ++k) {
+    cf[k] = (k & 1) + sf1 * ((k >> 1) & 1) + (D == 3 ? sf2 * ((k >> 2) & 1) : 0);
+    const unsigned v = ffl[cf[k]];
+    fm[0] |= (v & 1u) << k;
+    fm[1] |= ((v >> 1) & 1u) << k;
+  }
+  const uint8_t* const cfl = co.flags + C;
+#pragma unroll
+  for (int m = 0; m < NB; ++m) {
+    const int o0 = m % 3 - 1, o1 = (m / 3) % 3 - 1, o2 = D == 3 ? m / 9 - 1 : 0;
+    const bool in = IC[0] + o0 >= 0 && IC[0] + o0 < co.n[0] && IC[1] + o1 >= 0 && IC[1] + o1 < co.n[1] &&
+                    (D == 2 || (IC[2] + o2 >= 0 && IC[2] + o2 < co.n[2]));
+    const unsigned v = in ? cfl[o0 + o1 * sc1 + o2 * sc2] : 0u;
+    cm[0] |= (v & 1u) << m;
+    cm[1] |= ((v >> 1) & 1u) << m;
+  }
+  for (int q = 0; q < 2; ++q) {
+    if (!fm[q]) continue;
+    T cx[NB], xo[NCH];
+    const T* const xcq = co.x[q] + C;
+    T* const xfq = f.x[q] + F0;
+#pragma unroll
+    for (int m = 0; m < NB; ++m) {
+      const int o0 = m % 3 - 1, o1 = (m / 3) % 3 - 1, o2 = D == 3 ? m / 9 - 1 : 0;
+      cx[m] = ((cm[q] >> m) & 1u) ? xcq[o0 + o1 * sc1 + o2 * sc2] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) xo[k] = ((fm[q] >> k) & 1u) ? xfq[cf[k]] : T(0);
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+      if (!((fm[q] >> k) & 1u)) continue;
+      const int sd0 = (k & 1) ? 1 : -1, sd1 = ((k >> 1) & 1) ? 1 : -1, sd2 = ((k >> 2) & 1) ? 1 : -1;
+      bool lin = IC[0] + sd0 >= 0 && IC[0] + sd0 < co.n[0] && IC[1] + sd1 >= 0 && IC[1] + sd1 < co.n[1] &&
+                 (D == 2 || (IC[2] + sd2 >= 0 && IC[2] + sd2 < co.n[2]));
+      // neighbourhood slot of the corner whose offset bits j step sd along each axis
+      const int centre = D == 3 ? 13 : 4;
+#define EBP_SLOT(j) (centre + (((j) & 1) ? sd0 : 0) + ((((j) >> 1) & 1) ? 3 * sd1 : 0) + \
+                     ((D == 3 && (((j) >> 2) & 1)) ? 9 * sd2 : 0))
+#pragma unroll
+      for (int j = 1; j < NCH; ++j)
+        if (!((cm[q] >> EBP_SLOT(j)) & 1u)) lin = false;
+      T add;
+      if (!lin) {
+        add = cx[centre];
+      } else {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+          T w = T(1);
+          for (int a = 0; a < D; ++a) w *= ((j >> a) & 1) ? T(0.25) : T(0.75);
+          acc += w * cx[EBP_SLOT(j)];
+        }
+        add = acc;
+      }
+#undef EBP_SLOT
+      xfq[cf[k]] = xo[k] + add;
+    }
+  }
+}
+
 template <class T, int D>
 __device__ __forceinline__ void ph_prolong_blk(const Op<T>& f, const Op<T>& co, const Ctx& c) {
-  constexpr int NB = D == 3 ? 27 : 9, NCH = 1 << D;
-  const long long stc[3] = {1, co.n[0], (long long)co.n[0] * co.n[1]};
-  const long long stf[3] = {1, f.n[0], (long long)f.n[0] * f.n[1]};
   for (long long C = c.i0; C < co.ncell; C += c.st) {
     int IC[3];
     ijk(co, C, IC);
     if (D == 2) IC[2] = 0;
-    // children's flags and the coarse neighbourhood's, as one bit mask per phase
-    long long cf[NCH];
-    unsigned fm[2] = {0u, 0u}, cm[2] = {0u, 0u};
-#pragma unroll
-    for (int k = 0; k < NCH; ++k) {
-      cf[k] = (long long)(2 * IC[0] + (k & 1)) + stf[1] * (2 * IC[1] + ((k >> 1) & 1)) +
-              (D == 3 ? stf[2] * (2 * IC[2] + ((k >> 2) & 1)) : 0);
-      const unsigned v = f.flags[cf[k]];
-      fm[0] |= (v & 1u) << k;
-      fm[1] |= ((v >> 1) & 1u) << k;
-    }
-#pragma unroll
-    for (int m = 0; m < NB; ++m) {
-      const int o0 = m % 3 - 1, o1 = (m / 3) % 3 - 1, o2 = D == 3 ? m / 9 - 1 : 0;
-      const bool in = IC[0] + o0 >= 0 && IC[0] + o0 < co.n[0] && IC[1] + o1 >= 0 && IC[1] + o1 < co.n[1] &&
-                      (D == 2 || (IC[2] + o2 >= 0 && IC[2] + o2 < co.n[2]));
-      const unsigned v = in ? co.flags[C + o0 * stc[0] + o1 * stc[1] + o2 * stc[2]] : 0u;
-      cm[0] |= (v & 1u) << m;
-      cm[1] |= ((v >> 1) & 1u) << m;
-    }
-    for (int q = 0; q < 2; ++q) {
-      if (!fm[q]) continue;
-      T cx[NB], xo[NCH];
-#pragma unroll
-      for (int m = 0; m < NB; ++m) {
-        const int o0 = m % 3 - 1, o1 = (m / 3) % 3 - 1, o2 = D == 3 ? m / 9 - 1 : 0;
-        cx[m] = ((cm[q] >> m) & 1u) ? co.x[q][C + o0 * stc[0] + o1 * stc[1] + o2 * stc[2]] : T(0);
-      }
-#pragma unroll
-      for (int k = 0; k < NCH; ++k) xo[k] = ((fm[q] >> k) & 1u) ? f.x[q][cf[k]] : T(0);
-#pragma unroll
-      for (int k = 0; k < NCH; ++k) {
-        if (!((fm[q] >> k) & 1u)) continue;
-        const int sd0 = (k & 1) ? 1 : -1, sd1 = ((k >> 1) & 1) ? 1 : -1, sd2 = ((k >> 2) & 1) ? 1 : -1;
-        bool lin = IC[0] + sd0 >= 0 && IC[0] + sd0 < co.n[0] && IC[1] + sd1 >= 0 && IC[1] + sd1 < co.n[1] &&
-                   (D == 2 || (IC[2] + sd2 >= 0 && IC[2] + sd2 < co.n[2]));
-        // neighbourhood slot of the corner whose offset bits j step sd along each axis
-        const int centre = D == 3 ? 13 : 4;
-#define EBP_SLOT(j) (centre + (((j) & 1) ? sd0 : 0) + ((((j) >> 1) & 1) ? 3 * sd1 : 0) + \
-                     ((D == 3 && (((j) >> 2) & 1)) ? 9 * sd2 : 0))
-#pragma unroll
-        for (int j = 1; j < NCH; ++j)
-          if (!((cm[q] >> EBP_SLOT(j)) & 1u)) lin = false;
-        T add;
-        if (!lin) {
-          add = cx[centre];
-        } else {
-          T acc = T(0);
-#pragma unroll
-          for (int j = 0; j < NCH; ++j) {
-            T w = T(1);
-            for (int a = 0; a < D; ++a) w *= ((j >> a) & 1) ? T(0.25) : T(0.75);
-            acc += w * cx[EBP_SLOT(j)];
-          }
-          add = acc;
-        }
-#undef EBP_SLOT
-        f.x[q][cf[k]] = xo[k] + add;
-      }
-    }
+    prolong_cell<T, D>(f, co, C, IC);
   }
 }
 
@@ -1680,5 +1690,16 @@ __global__ void __launch_bounds__(PT) k_restrict_phase(Op<T> f, Op<T> co) {
   c.gsize = (int)gridDim.x;
   c.gcta = (int)blockIdx.x;
   ph_restrict(f, co, c);
+}
+
+// the prolongation of level 1's correction onto level 0 (x += P e), on its own
+template <class T>
+__global__ void __launch_bounds__(PT) k_prolong_phase(Op<T> f, Op<T> co) {
+  Ctx c{};
+  c.i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  c.st = (long long)gridDim.x * blockDim.x;
+  c.gsize = (int)gridDim.x;
+  c.gcta = (int)blockIdx.x;
+  ph_prolong(f, co, c);
 }
 }  // namespace ebp

@@ -335,6 +335,7 @@ extern "C" void eb_solver_opts_default(eb_solver_opts* o) {
 // formula once the wall value is eliminated; it depends on the level's h.
 template <class T>
 static void set_stencil_terms(Op<T>& o, const Grid& g) {
+  o.intdg = 1;
   for (int k = 0; k < 6; ++k) {
     double w = 0.0;
     if (k < 2 * g.D) {
@@ -342,11 +343,14 @@ static void set_stencil_terms(Op<T>& o, const Grid& g) {
       else if (g.bc[k] == 2) w = g.rob[k][0] / (g.rob[k][0] + g.rob[k][1] * 8.0 / (3.0 * g.h));
     }
     o.wr[k] = (T)w;
+    o.w3[k] = (T)w * (T(1) / T(3));
+    if (w != 0.0 && w != 1.0) o.intdg = 0;
   }
   for (int p = 0; p < 2; ++p) {
     const T lh = (T)(g.lam[p] * g.h * g.h / g.eps[p]);
     o.lh[p] = lh;
     o.idg[p] = T(1) / (T(2 * g.D) + lh);
+    if (lh != T(0)) o.intdg = 0;
   }
 }
 
@@ -1639,11 +1643,11 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
     *bytes = (double)P->G->L[0].g.ncell * (kernel == 4 ? 13.0 : 10.0);
     return EB_OK;
   }
-  if (!P || reps < 1 || (kernel != 0 && kernel != 1) || !ms || !bytes) {
+  if (!P || reps < 1 || (kernel != 0 && kernel != 1 && kernel != 6) || !ms || !bytes) {
     set_error("invalid argument");
     return EB_ERR_INVALID;
   }
-  if (kernel == 1 && P->nlev < 2) {
+  if ((kernel == 1 || kernel == 6) && P->nlev < 2) {
     set_error("no coarse level");
     return EB_ERR_INVALID;
   }
@@ -1663,9 +1667,12 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
     if (kernel == 0) {
       if (mixed) k_dense_phase<float><<<grid, PT, 0, s>>>(P->op32[0], i & 1);
       else k_dense_phase<double><<<grid, PT, 0, s>>>(P->op64[0], i & 1);
-    } else {
+    } else if (kernel == 1) {
       if (mixed) k_restrict_phase<float><<<grid, PT, 0, s>>>(P->op32[0], P->op32[1]);
       else k_restrict_phase<double><<<grid, PT, 0, s>>>(P->op64[0], P->op64[1]);
+    } else {
+      if (mixed) k_prolong_phase<float><<<grid, PT, 0, s>>>(P->op32[0], P->op32[1]);
+      else k_prolong_phase<double><<<grid, PT, 0, s>>>(P->op64[0], P->op64[1]);
     }
   };
   launch(0);
@@ -1680,7 +1687,8 @@ extern "C" eb_status eb_poisson_profile(eb_poisson* P, int kernel, int reps, dou
   if (e != cudaSuccess) return cuda_fail(e, "profile");
   *ms = (double)t / reps;
   if (kernel == 0) *bytes = (double)n * (3.0 * tb + 1.0) / 2.0;
-  else *bytes = (double)n * (2.0 * tb + 1.0) + (double)n / (double)(1 << D) * 2.0 * tb;
+  else if (kernel == 1) *bytes = (double)n * (2.0 * tb + 1.0) + (double)n / (double)(1 << D) * 2.0 * tb;
+  else *bytes = (double)n * (2.0 * tb + 1.0) + (double)n / (double)(1 << D) * (tb + 1.0);
   return EB_OK;
 }
 
