@@ -286,6 +286,48 @@ eb_status eb_poisson_solve_batched(eb_poisson* const* P, int n, const double* co
 eb_status eb_field_eval(eb_poisson* P, const double* d_phi, const double* d_sigma, double* d_E, double* d_En,
                         void* stream);
 
+/* The constants of one TGA step of length dt (Sec. 3.4, Eq. tga; Twizell, Gumel
+ * and Arigu): mu[0..3] = mu1, mu2, mu3, mu4 with a = 2 - sqrt(2) - (machine
+ * precision), mu1,2 = (a -+ sqrt(a^2 - 4a + 2)) dt / 2, mu3 = (1 - a) dt,
+ * mu4 = (1/2 - a) dt.  EB_ERR_INVALID unless dt > 0 and finite. */
+eb_status eb_tga_coefficients(double dt, double mu[4]);
+
+/* Opaque handle of a TGA diffusion stepper (Sec. 3.4, Eq. tga). */
+typedef struct eb_tga eb_tga;
+
+/* A stepper for the implicit diffusion d phi/dt = L phi + rho with
+ * L phi = div(eps grad phi) on the cut-cell grid, where each cell's balance is
+ * kappa d phi/dt = (L phi integrated over the cell) + kappa rho.  One step of
+ * length dt solves
+ *   (M - mu1 L) psi = (M + mu3 L) phi + dt (M + mu4 L) rho,
+ *   (M - mu2 L) phi_next = M psi,       M = diag(kappa).
+ * We read the printed equation this way: it omits dt on the source and writes
+ * the model equation with +L while the scheme's operators carry -L.
+ * G0, G1, G2 are geometries built from one description whose helmholtz_lam is
+ * 0, 1/mu1 and 1/mu2 of this dt (eb_tga_coefficients; both phases when there
+ * are two; eps is the diffusion coefficient); P0, P1, P2 are persistent solver
+ * handles on them (only P0's operator is applied).  EB_ERR_INVALID when the grids differ or a shift does not match dt.  Boundary
+ * conditions are the description's types with homogeneous data (its values
+ * are not used).  The stepper borrows the six handles (they must outlive it)
+ * and owns 10 x n_cells doubles of device memory; kappa is computed on
+ * `stream` here.  *out is null on failure. */
+eb_status eb_tga_create(const eb_geom* G0, const eb_geom* G1, const eb_geom* G2, eb_poisson* P0, eb_poisson* P1,
+                        eb_poisson* P2, double dt, void* stream, eb_tga** out);
+
+/* One step of the stepper T.  d_phi, d_rho, d_out: FP64 [2][n_cells] device
+ * arrays (d_out may be d_phi); entries without an unknown must be finite and
+ * come out 0.  Each stage is solved to max|r| <= tol max|b| from zero
+ * (0 < tol < 1); info[0] and info[1] (may be null) report the two stage
+ * solves.  The step is enqueued on `stream` and returns after the stages; one
+ * stepper runs one step at a time.  Returns the first stage status that is not
+ * EB_OK (EB_ERR_NOT_CONVERGED when an iteration limit is reached). */
+eb_status eb_tga_step(eb_tga* T, const double* d_phi, const double* d_rho, double* d_out, double tol,
+                      eb_solve_info* info, void* stream);
+
+/* Frees the stepper's device memory (not the borrowed handles); null is a
+ * no-op. */
+void eb_tga_destroy(eb_tga* T);
+
 /* Benchmark hook (no counterpart in the paper): launches one kernel of the
  * finest multigrid level `reps` times on `stream` between CUDA events and
  * reports the mean duration per launch and the algorithmic bytes one launch

@@ -114,6 +114,7 @@ eb_status launch_field(const eb_geom* G, const double* phi, const double* sigma,
                        cudaStream_t s);
 eb_status launch_rhs64(const eb_geom* G, const double* s_rhs, const double* sigma, double* b, double* bnorm,
                        cudaStream_t s);
+eb_status launch_kappa(const eb_geom* G, double* kappa, cudaStream_t s);
 
 }  // namespace ebp
 

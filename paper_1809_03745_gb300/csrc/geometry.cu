@@ -932,6 +932,14 @@ eb_status build_cf(const eb_geom* Gf, const eb_geom* Gc, const CFBox& B, CFFace*
   return check(s, "coarse-fine faces");
 }
 
+// kappa [2][ncell] of the finest level (volume fraction per phase, 0 where
+// the phase has no unknown), enqueued on s
+eb_status launch_kappa(const eb_geom* G, double* kappa, cudaStream_t s) {
+  const DevLevel& L = G->L[0];
+  k_export_kappa<<<nblk(L.g.ncell), TB, 0, s>>>(view(L), kappa);
+  return check(s, "kappa");
+}
+
 eb_status export_geometry(const eb_geom* G, eb_geom_arrays* out, cudaStream_t s) {
   const DevLevel& L = G->L[0];
   LevelGeom v = view(L);

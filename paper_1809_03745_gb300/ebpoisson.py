@@ -92,7 +92,8 @@ EXPORTS = ["eb_status_str", "eb_last_error", "eb_geom_build", "eb_geom_query", "
            "eb_poisson_residual_noalloc", "eb_poisson_solve_batched", "eb_server_opts_default", "eb_server_create",
            "eb_server_submit", "eb_server_poll", "eb_server_wait", "eb_server_query", "eb_server_destroy",
            "eb_amr_setup", "eb_amr_query", "eb_amr_residual", "eb_amr_solve", "eb_amr_kernel_stats",
-           "eb_amr_destroy", "eb_device_fma_rates"]
+           "eb_amr_destroy", "eb_device_fma_rates", "eb_tga_coefficients", "eb_tga_create",
+           "eb_tga_step", "eb_tga_destroy"]
 
 
 def lib_path() -> str:
@@ -155,6 +156,13 @@ def load(build_if_missing: bool = False):
         lib.eb_amr_kernel_stats.argtypes = [P, C.POINTER(C.c_double)]
         lib.eb_device_fma_rates.restype = C.c_int
         lib.eb_device_fma_rates.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        lib.eb_tga_coefficients.restype = C.c_int
+        lib.eb_tga_coefficients.argtypes = [C.c_double, C.POINTER(C.c_double)]
+        lib.eb_tga_create.restype = C.c_int
+        lib.eb_tga_create.argtypes = [P] * 6 + [C.c_double, P, C.POINTER(P)]
+        lib.eb_tga_step.restype = C.c_int
+        lib.eb_tga_step.argtypes = [P, P, P, P, C.c_double, C.POINTER(SolveInfo), P]
+        lib.eb_tga_destroy.argtypes = [P]
         lib.eb_server_opts_default.argtypes = [C.POINTER(ServerOpts)]
         lib.eb_server_create.restype = C.c_int
         lib.eb_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(P)]
@@ -336,6 +344,26 @@ def eb_poisson_solve_batched(handles, rhs, sigma, phi, stream=None) -> list:
 def eb_field_eval(handle, phi, sigma, E, En, stream=None):
     _check(load().eb_field_eval(handle, _ptr(phi), _ptr(sigma), _ptr(E), _ptr(En), _stream(stream)),
            "eb_field_eval")
+
+
+def eb_tga_coefficients(dt):
+    mu = (C.c_double * 4)()
+    _check(load().eb_tga_coefficients(float(dt), mu), "eb_tga_coefficients")
+    return [mu[k] for k in range(4)]
+
+
+def eb_tga_create(g0, g1, g2, p0, p1, p2, dt, stream=None):
+    h = C.c_void_p()
+    _check(load().eb_tga_create(g0, g1, g2, p0, p1, p2, float(dt), _stream(stream), C.byref(h)), "eb_tga_create")
+    return h
+
+
+def eb_tga_step(handle, phi, rho, out, tol, stream=None):
+    infos = (SolveInfo * 2)()
+    st = load().eb_tga_step(handle, _ptr(phi), _ptr(rho), _ptr(out), float(tol), infos, _stream(stream))
+    if st not in (EB_OK, EB_ERR_NOT_CONVERGED):
+        _check(st, "eb_tga_step")
+    return [_info_dict(infos[k]) for k in range(2)]
 
 
 # ------------------------------------------------------------- convenience
@@ -615,3 +643,46 @@ class Composite:
             self.close()
         except Exception:
             pass
+
+
+class TGA:
+    """Implicit diffusion by TGA steps (Sec. 3.4) on one geometry description
+    (owns an eb_tga and the three geometries and solvers it borrows, with
+    Helmholtz shifts 0, 1/mu1, 1/mu2 for the step length dt; eps of the
+    description is the diffusion coefficient)."""
+
+    def __init__(self, desc: dict, dt: float, *, precision="mixed", tol=1e-10, device="cuda", stream=None):
+        self.dt, self.tol = float(dt), float(tol)
+        mu = eb_tga_coefficients(self.dt)
+        self.mu = mu
+        self.handles = []
+        for lam in (0.0, 1.0 / mu[0], 1.0 / mu[1]):
+            d = dict(desc)
+            d["lam"] = (lam, lam)
+            g = Geometry(d, device=device)
+            self.handles.append(Poisson(g, precision=precision, tol=tol, max_cycles=200))
+        self.geom = self.handles[0].geom
+        with torch.cuda.device(self.geom.device):
+            self._h = eb_tga_create(*(P.geom._h for P in self.handles), *(P._h for P in self.handles), self.dt,
+                                    stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().eb_tga_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, phi, rho, out=None, stream=None):
+        """phi^{n+1} from phi^n and the source rho ([2][n_cells] FP64 on the device)."""
+        dev, n = self.geom.device, self.geom.ncell
+        phi = _dev(phi, torch.float64, dev).reshape(2, n).contiguous()
+        rho = _dev(rho, torch.float64, dev).reshape(2, n).contiguous()
+        if out is None:
+            out = torch.empty_like(phi)
+        infos = eb_tga_step(self._h, phi, rho, out, self.tol, stream)
+        return out, infos

@@ -343,3 +343,28 @@ def photo_inputs(dim, n, L=0.02, peak=1.0):
         out.append((d, S, np.zeros(eta.size)))
         w.append(PHOTO_NU_EFF * PHOTO_P_O2 * PHOTO_GROUPS[gi][1])
     return out, w
+
+
+def diffusion_inputs(dim, n, peak=1.0):
+    """A species diffusing in the gas of the rod-plane (2D) or pin-plane (3D)
+    geometry, the diffusion part of the drift-diffusion step of Sec. 3.4 in a
+    unit box with eps = D = 1: the electrode and the dielectric as one
+    absorbing solid (homogeneous Dirichlet on its surface), no flux through the
+    walls.  Returns (desc, phi0, rho): a Gaussian seed of width 0.03 below the
+    tip and a Gaussian source of width 0.05 around it, [2][n_cells] each (the
+    solid's phase 1 is empty)."""
+    d = rod_plane_2d(n, dielectric=True) if dim == 2 else pin_plane_3d(n)
+    d["nodes"] = list(d["nodes"]) + [(CSG_UNION, 0, 1)]
+    d["root_E"], d["root_D"] = len(d["nodes"]) - 1, -1
+    d["electrodes"] = [(d["root_E"], 0.0)]
+    d["phi_E"] = 0.0
+    d["eps"] = (1.0, 1.0)
+    d["bc"] = [NEUMANN] * 6
+    d["phi_wall"] = [0.0] * 6
+    x, y, z = cell_centres(d)
+    r2 = (x - 0.5) ** 2 + ((y - 0.42) ** 2 + z ** 2 if dim == 2 else (y - 0.5) ** 2 + (z - 0.42) ** 2)
+    phi = np.zeros((2, x.size))
+    rho = np.zeros((2, x.size))
+    phi[0] = peak * np.exp(-r2 / (2 * 0.03 ** 2))
+    rho[0] = 10.0 * peak * np.exp(-r2 / (2 * 0.05 ** 2))
+    return d, phi, rho
