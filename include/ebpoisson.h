@@ -416,6 +416,88 @@ eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double* d_sig_c, 
 eb_status eb_amr_kernel_stats(const eb_amr* A, double out[8]);
 void eb_amr_destroy(eb_amr* A);
 
+/* ---------------------------------------------------------------- nested levels
+ * A composite grid of n_levels levels (2 .. EB_AMR_MAX_LEVELS; Sec. 3.3.2
+ * solves on a hierarchy of refined levels, Sec. 6 refines where the tracer
+ * criteria ask).  Level 0 is the grid of `base`; level l >= 1 is one ratio-2
+ * box over cells [box_lo[l-1][k], box_hi[l-1][k]) of level l-1's grid,
+ * counted from that grid's lower corner (sides a positive multiple of 4
+ * parent cells).  Every pair of consecutive levels is coupled as in the
+ * two-level grid above; a cell under the next finer box carries no equation
+ * and takes the kappa-weighted mean of its children (themselves such means
+ * under a still finer box).  Proper nesting: a box keeps at least one parent
+ * cell away from each coarse-fine side of its parent (EB_ERR_INVALID
+ * otherwise); sides on the domain boundary keep the domain's conditions.
+ * box_lo / box_hi: host arrays of 3 (n_levels - 1) ints.  The two-level calls
+ * above are this with n_levels = 2 (eb_amr_residual / eb_amr_solve refuse
+ * more levels; eb_amr_query reports levels 0 and 1). */
+#define EB_AMR_MAX_LEVELS 4
+eb_status eb_amr_setup_levels(const eb_geom_desc* base, int n_levels, const int* box_lo, const int* box_hi,
+                              const eb_solver_opts* opts, void* stream, eb_amr** out);
+/* Level `level`'s grid: number of levels, cells, cells per axis, physical
+ * lower corner, spacing, and fine CF faces towards its parent (0 on level 0).
+ * Any output may be NULL. */
+eb_status eb_amr_level_query(const eb_amr* A, int level, int* n_levels, long long* n_cells, int n[3],
+                             double lo[3], double* h, long long* cf_faces);
+/* The geometry of level `level` (owned by A; CF sides as Neumann walls), for
+ * eb_geom_query / eb_geom_export / eb_tag_cells. */
+eb_status eb_amr_level_geom(const eb_amr* A, int level, const eb_geom** out);
+/* Composite residual b - A phi (FP64) over all levels: d_rhs, d_sig, d_phi,
+ * d_r are host arrays of n_levels device pointers, each level [2][n_cells]
+ * (d_sig or its entries may be NULL).  d_r is 0 under the next finer box and
+ * where a cell has no unknown; phi values under a finer box are ignored. */
+eb_status eb_amr_residual_levels(eb_amr* A, const double* const* d_rhs, const double* const* d_sig,
+                                 const double* const* d_phi, double* const* d_r, void* stream);
+/* Composite solve over all levels to max|r| <= tol max|b|: restarted FGMRES
+ * (restart 12, FP64) preconditioned by one multiplicative FAC sweep from
+ * level 0 up (a level-0 correction over the domain with the finer remainders
+ * restricted under the boxes, constant per parent on level 1, then on every
+ * finer level a correction of what remains there with zero Dirichlet data on
+ * its CF sides), each correction one V-cycle of the persistent multigrid
+ * solve.  d_phi holds the guess on entry; on return every level's values
+ * under the next finer box hold the finer means.  info as eb_amr_solve. */
+eb_status eb_amr_solve_levels(eb_amr* A, const double* const* d_rhs, const double* const* d_sig,
+                              double* const* d_phi, eb_solve_info* info, void* stream);
+/* E = -grad phi on level `level`'s grid alone (as eb_field_eval; the level's CF
+ * sides act as Neumann walls, so cells next to them take one-sided values). */
+eb_status eb_amr_field_eval(eb_amr* A, int level, const double* d_phi, const double* d_sigma, double* d_E,
+                            double* d_En, void* stream);
+
+/* ---------------------------------------------------------------- regrid tags
+ * Refinement tags of Sec. 6 on one grid (a plain geometry or a level of a
+ * composite grid): the tracer T = |E| / max |E|, |E| per cell the largest
+ * field magnitude over the phases with an unknown, the maximum over the
+ * grid's cells; a cell is tagged for refinement (tag value 1) when
+ * |grad T| dx / T > eps[0] or T > eps[1], for coarsening (value 2) when
+ * |grad T| dx / T < eps[2] and T < eps[3] (the paper uses 0.1, 0.8, 0.1, 0.2).
+ * grad T by differences over the axis neighbours that carry T: centred
+ * ((T+ - T-)/2 in index units, dx cancels), one-sided where one neighbour
+ * does, 0 where none does; the ratio is 0 where T and the gradient are 0 and
+ * infinite where only T is 0.  Covered cells get no tag.  All arithmetic is
+ * FP64 without contraction, so the tags are a function of d_E alone.
+ * d_E: [D][2][n_cells] as eb_field_eval writes it.  keep_lo / keep_hi (both
+ * or neither NULL): the current finer box on this grid; its cells that carry
+ * T and are not tagged for coarsening are marked as well (a refined region is
+ * kept until the coarsening test releases it).  d_tags (may be NULL):
+ * [n_cells] tag bytes.  On return bbox_lo / bbox_hi (host, 3 ints; hi
+ * exclusive) bound the marked cells (refine-tagged or kept), *n_marked counts
+ * them (0: bbox undefined) and *e_max is max |E|.  EB_ERR_INVALID for a NULL
+ * argument or an eps that is not finite. */
+eb_status eb_tag_cells(const eb_geom* G, const double* d_E, const double eps[4], const int* keep_lo,
+                       const int* keep_hi, unsigned char* d_tags, int bbox_lo[3], int bbox_hi[3],
+                       long long* n_marked, double* e_max, void* stream);
+/* The next finer box from the marked cells' bounding box (host arithmetic, no
+ * device work): grown by `buf` cells per side, rounded outward to multiples
+ * of `block`, clipped to the grid n[dim] and `block` cells short of every side
+ * that is a coarse-fine side (cf_lo / cf_hi per axis, nonzero for CF), then
+ * widened to `block` cells away from the side it was clipped at if clipping
+ * left it thinner.  *has_box = 0 when n_marked is 0 or the grid has no room;
+ * else box_lo / box_hi hold the box (the next level's box_lo / box_hi).
+ * EB_ERR_INVALID for buf < 0, block < 1 or dim outside 2..3. */
+eb_status eb_regrid_box(int dim, const int n[3], const int cf_lo[3], const int cf_hi[3], const int bbox_lo[3],
+                        const int bbox_hi[3], long long n_marked, int buf, int block, int box_lo[3],
+                        int box_hi[3], int* has_box);
+
 /* ---------------------------------------------------------------- serving
  * Continuous-batching solve server (no counterpart in the paper, whose
  * solves run one per time step inside a plasma code).  Requests (a geometry

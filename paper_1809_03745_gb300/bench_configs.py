@@ -17,6 +17,11 @@ With --trace c1|c2|c3 it instead prints where one V-cycle's time goes: the
 persistent kernel's phase stamps of the first V-cycle (eb_poisson_trace),
 summed per level and phase kind, and the grid-barrier cost.
 
+With --regrid N it refines the N^3 pin-plane (C3 geometry and line charge)
+by the Sec. 6 tracer criteria up to three levels (regrid.build_hierarchy),
+then times a solve of the final hierarchy and the tagging kernels on its
+finest level; with --regrid2d N the same on the N^2 C2 rod-plane.
+
 With --composite N it runs one C3 composite solve at N^3 + (N/2)^3 (after
 the set-up, no warm-up), and with --kernels N the large-grid kernels on their
 own on the N^3 pin-plane finest level (the tile-streamed sweep, one colour
@@ -27,6 +32,7 @@ Usage: python -m paper_1809_03745_gb300.bench_configs [--only C1 C2 C3 C4]
        python -m paper_1809_03745_gb300.bench_configs --trace c2 [--n N] [--precision mixed|fp64]
        python -m paper_1809_03745_gb300.bench_configs --peaks   (measured FP64 / FP32 FMA rates)
        python -m paper_1809_03745_gb300.bench_configs --composite 256
+       python -m paper_1809_03745_gb300.bench_configs --regrid 128
        python -m paper_1809_03745_gb300.bench_configs --kernels 384 [--reps 20]
 """
 from __future__ import annotations
@@ -182,6 +188,46 @@ def kernels_once(n, reps):
         print(json.dumps({"kernel": names[k], "n": n, "ms": ms, "gbs": by / ms / 1e6}), flush=True)
 
 
+def regrid_once(n, dim):
+    """Sec. 6 regrid of the pin-plane (3D) or rod-plane (2D) to three levels, then timings."""
+    from . import regrid as R
+    if dim == 3:
+        desc = W.pin_plane_3d(n)
+        src = lambda x, y, z: W.line_charge(x, y, z, 1e3)  # noqa: E731
+    else:
+        desc = W.rod_plane_2d(n, dielectric=True)
+        src = lambda x, y, z: 100 * np.exp(-((x - 0.5) ** 2 + (y - 0.45) ** 2) / (2 * 0.03 ** 2))  # noqa: E731
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    out = R.build_hierarchy(desc, src, max_levels=3, precision="mixed", tol=1e-10)
+    torch.cuda.synchronize()
+    t_regrid = time.perf_counter() - t
+    H = out["hierarchy"]
+    rec = {"workload": f"regrid {'pin-plane' if dim == 3 else 'rod-plane'} {n}^{dim}, three levels by Sec. 6 tags",
+           "boxes": out["boxes"], "steps": [{k: v for k, v in st.items() if k != "e_max"} for st in out["steps"]],
+           "regrid_s": t_regrid}
+    if H is not None:
+        cells = [H.levels[l]["n_cells"] for l in range(H.L)]
+        S = [torch.from_numpy(R.level_sources(H.level_desc(l), src)).cuda() for l in range(H.L)]
+        dt, (phis, info) = _timed(lambda: H.solve(S), reps=2)
+        own = sum(cells) - sum(int(np.prod([hi - lo for lo, hi in zip(*b)])) for b in out["boxes"])
+        rec.update(level_cells=cells, composite_cells=own, solve_ms=dt * 1e3, cells_per_s=own / dt,
+                   composite_iters=info["outer_iters"], vcycles=info["vcycles"], rel_res=info["rel_res"])
+        Ef = H.field(H.L - 1, phis[-1])[0]
+        g = H.level_geom(H.L - 1)
+        reps = 20
+        E.tag_cells(g, Ef, want_tags=True)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            E.tag_cells(g, Ef, want_tags=True)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t) / reps * 1e3
+        nf = cells[-1]
+        rec.update(tag_ms=ms, tag_cells=nf, tag_gbs=(dim * 2 * 8 + 1 + 1) * nf / ms / 1e6)
+    print(json.dumps(rec), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", nargs="+", default=["C1", "C2", "C3", "C4"])
@@ -192,10 +238,15 @@ def main():
     ap.add_argument("--composite", type=int, default=None)
     ap.add_argument("--kernels", type=int, default=None)
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--regrid", type=int, default=None)
+    ap.add_argument("--regrid2d", type=int, default=None)
     args = ap.parse_args()
     E.load()
     if args.composite:
         composite_once(args.composite)
+        return
+    if args.regrid or args.regrid2d:
+        regrid_once(args.regrid or args.regrid2d, 3 if args.regrid else 2)
         return
     if args.kernels:
         kernels_once(args.kernels, args.reps)

@@ -1,9 +1,10 @@
 """Builds the CUDA library libebpoisson.so in-tree for sm_103a (GB300).
 
-Five translation units compiled in parallel: geometry.cu (setup work, no FMA
+Six translation units compiled in parallel: geometry.cu (setup work, no FMA
 contraction so the cut-cell geometry is bit-reproducible), solver.cu
 (multigrid kernels, driver, C ABI), server.cu (the serving loop, host code),
-amr.cu (the composite refined-box solve) and tga.cu (TGA diffusion steps).  The CUDA runtime is linked statically.
+amr.cu (the composite solve over nested refined boxes), tga.cu (TGA
+diffusion steps) and tagging.cu (refinement tags, no FMA contraction).  The CUDA runtime is linked statically.
 """
 from __future__ import annotations
 
@@ -17,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libebpoisson.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = {"geometry.cu": ["--fmad=false"], "solver.cu": [], "server.cu": [], "amr.cu": [], "tga.cu": []}
+UNITS = {"geometry.cu": ["--fmad=false"], "solver.cu": [], "server.cu": [], "amr.cu": [], "tga.cu": [], "tagging.cu": ["--fmad=false"]}
 
 
 def _nvcc():

@@ -1,9 +1,10 @@
-// amr.cu -- composite two-level solve: one ratio-2 refined box over a coarse
-// grid (Sec. 3.3.2 runs its multigrid over refined levels; the coarse-fine
-// coupling follows the refluxing of Sec. 3.3).
+// amr.cu -- composite multi-level solve: nested ratio-2 refined boxes, one
+// per level (Sec. 3.3.2 runs its multigrid over refined levels; the
+// coarse-fine coupling of each pair of levels follows the refluxing of
+// Sec. 3.3).
 //
 // Composite operator (the same reading as the oracle's):
-//   * the fine box is a grid of its own whose coarse-fine (CF) sides are
+//   * every box is a grid of its own whose coarse-fine (CF) sides are
 //     homogeneous Neumann walls; the CF flux eps0 (ghost - phi_F)/h_f times the
 //     fine aperture is added to each fine cell next to a CF side, the ghost by
 //     quadratic tangential then quadratic normal Lagrange steps (fallbacks to
@@ -11,15 +12,18 @@
 //   * a coarse cell outside the box next to a CF side loses the coarse
 //     operator's own flux through that face and gains minus the mean of the
 //     fine fluxes through it (refluxing: exact conservation);
-//   * coarse cells under the box carry no equation; where a coarse stencil
-//     reaches one, its value is the kappa-weighted mean of its children.
+//   * cells under the next finer box carry no equation; where a stencil
+//     reaches one, its value is the kappa-weighted mean of its children, which
+//     are such means themselves under a still finer box;
+//   * each box keeps one parent cell away from its parent's CF sides (proper
+//     nesting), so every coarse cell across a CF face carries an equation.
 // Solve: restarted FGMRES in FP64 on the composite system, right-
-// preconditioned by one FAC step: a coarse correction over the whole domain
-// (the fine part of the vector averaged onto the coarse cells under the box),
-// added constant per parent on the fine grid, then a fine correction of what
-// remains on the box with zero Dirichlet data on its CF sides.  Both
-// corrections run one V-cycle of the persistent multigrid kernel; dot products are
-// summed in a fixed order (deterministic).
+// preconditioned by one multiplicative FAC sweep from level 0 up: a level-0
+// correction over the whole domain (the finer parts of the vector restricted
+// under the boxes), added constant per parent on level 1, then on every finer
+// level a correction of what remains there with zero Dirichlet data on its CF
+// sides.  Every correction runs one V-cycle of the persistent multigrid
+// kernel; dot products are summed in a fixed order (deterministic).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -305,27 +309,45 @@ __global__ void k_cv_sub(const uint8_t* flags, long long n, const double* b, con
 
 }  // namespace
 
+constexpr int AMR_MAXL = EB_AMR_MAX_LEVELS;
+
+// A composite vector: one [2][n_l] array per level (entries under the next
+// finer box and without an unknown ignored)
 struct CVec {
-  double* c = nullptr;
-  double* f = nullptr;
+  double* v[AMR_MAXL] = {};
+};
+
+// One level: its grid as an operator (CF sides homogeneous Neumann) and, from
+// level 1 on, as a correction grid (CF sides zero Dirichlet)
+struct AmrLevel {
+  eb_geom_desc d{}, d0{};
+  eb_geom *G = nullptr, *G0 = nullptr;
+  eb_poisson *P = nullptr, *P0 = nullptr;  // level 0: P0 == P
+  long long n = 0;
+  double h = 0.0;
+  const uint8_t* flags = nullptr;  // finest-level flags of G (owned by G)
+  double *pc = nullptr;            // phi with the cells under the next box replaced by the finer means
+  double *r = nullptr, *b0 = nullptr, *e = nullptr, *kap = nullptr;
+};
+
+// The coupling of levels l-1 (coarse) and l (fine), stored at index l
+struct AmrPair {
+  BoxIdx B{};
+  CFBox cfb{};
+  long long nface = 0, ncface = 0;
+  CFFace* faces = nullptr;
+  CFCoarse* cfaces = nullptr;
+  double* fl = nullptr;
 };
 
 struct eb_amr {
-  int D = 2;
-  BoxIdx B{};
-  CFBox cfb{};
-  eb_geom_desc dc{}, df{}, df0{};
+  int D = 2, L = 2;
+  AmrLevel lv[AMR_MAXL];
+  AmrPair pr[AMR_MAXL];
   std::vector<eb_prim> prims;
   std::vector<eb_csg> nodes;
-  eb_geom *Gc = nullptr, *Gf = nullptr, *Gf0 = nullptr;
-  eb_poisson *Pc = nullptr, *Pf = nullptr, *Pf0 = nullptr;
   eb_solver_opts o{};
-  long long ncc = 0, nff = 0, nface = 0, ncface = 0;
-  double hc = 0.0, hf = 0.0, eps0 = 1.0;
-  const uint8_t *cflags = nullptr, *fflags = nullptr;  // finest-level flags (owned by the geometries)
-  CFFace* faces = nullptr;
-  CFCoarse* cfaces = nullptr;
-  double *fl = nullptr, *kf = nullptr, *pcf = nullptr, *rc = nullptr, *rf = nullptr, *ec = nullptr, *ef = nullptr;
+  double eps0 = 1.0;
   int* d_status = nullptr;
   unsigned long long* d_norm = nullptr;
   // FGMRES work space (allocated at the first solve)
@@ -334,9 +356,8 @@ struct eb_amr {
   double* d_part = nullptr;
   std::vector<void*> allocs;
   long long bytes = 0;
-  double *bc0 = nullptr, *bf0 = nullptr;  // b of the coarse and fine operators for the current data
   // persistent solve launches of the last composite solve, coarse [0] and
-  // fine [1] correction solvers: launches, kernel ms, V-cycles, FP64 outer iterations
+  // finer levels' [1] correction solvers: launches, kernel ms, V-cycles, FP64 outer iterations
   double kstat[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
 };
 
@@ -355,143 +376,181 @@ static eb_status amr_fail(eb_amr* A, eb_status st) {
 extern "C" void eb_amr_destroy(eb_amr* A) {
   if (!A) return;
   cudaDeviceSynchronize();
-  eb_poisson_destroy(A->Pc);
-  eb_poisson_destroy(A->Pf);
-  eb_poisson_destroy(A->Pf0);
-  eb_geom_destroy(A->Gc);
-  eb_geom_destroy(A->Gf);
-  eb_geom_destroy(A->Gf0);
+  for (int l = 0; l < AMR_MAXL; ++l) {
+    AmrLevel& v = A->lv[l];
+    if (v.P0 != v.P) eb_poisson_destroy(v.P0);
+    eb_poisson_destroy(v.P);
+    eb_geom_destroy(v.G0);
+    eb_geom_destroy(v.G);
+  }
   for (void* p : A->allocs) cudaFree(p);
   delete A;
 }
 
-extern "C" eb_status eb_amr_setup(const eb_geom_desc* desc, const int box_lo[3], const int box_hi[3],
-                                  const eb_solver_opts* opts, void* stream, eb_amr** out) {
+// is side s2 of axis k of the box of pair B a CF side (inside its parent grid)?
+static bool cf_side(const BoxIdx& B, int k, int s2) { return s2 == 0 ? B.lo[k] > 0 : B.hi[k] < B.nc[k]; }
+
+extern "C" eb_status eb_amr_setup_levels(const eb_geom_desc* desc, int n_levels, const int* box_lo,
+                                         const int* box_hi, const eb_solver_opts* opts, void* stream,
+                                         eb_amr** out) {
   if (!desc || !box_lo || !box_hi || !out) {
     set_error("null argument");
     return EB_ERR_INVALID;
   }
   *out = nullptr;
+  if (n_levels < 2 || n_levels > AMR_MAXL) {
+    set_error("a composite grid has 2 to " + std::to_string(AMR_MAXL) + " levels");
+    return EB_ERR_INVALID;
+  }
   if (desc->n_prims < 0 || desc->n_prims > EB_MAX_PRIMS || desc->n_nodes < 0 || desc->n_nodes > EB_MAX_NODES ||
       (desc->n_prims && !desc->prims) || (desc->n_nodes && !desc->nodes)) {
     set_error("invalid primitive or CSG node list");
     return EB_ERR_INVALID;
   }
-  cudaStream_t s = (cudaStream_t)stream;
-  eb_amr* A = new eb_amr();
-  A->D = desc->dim;
-  const int D = A->D;
-  if (D < 2 || D > 3) {
-    delete A;
+  if (desc->dim < 2 || desc->dim > 3) {
     set_error("dimension must be 2 or 3");
     return EB_ERR_INVALID;
   }
+  cudaStream_t s = (cudaStream_t)stream;
+  eb_amr* A = new eb_amr();
+  A->D = desc->dim;
+  A->L = n_levels;
+  const int D = A->D, L = A->L;
   if (opts) A->o = *opts;
   else eb_solver_opts_default(&A->o);
   A->o.launch_mode = 0;
   A->prims.assign(desc->prims, desc->prims + desc->n_prims);
   A->nodes.assign(desc->nodes, desc->nodes + desc->n_nodes);
-  A->dc = *desc;
-  A->dc.prims = A->prims.data();
-  A->dc.nodes = A->nodes.data();
-  BoxIdx& B = A->B;
-  B.D = D;
-  for (int k = 0; k < 3; ++k) {
-    B.nc[k] = k < D ? desc->n[k] : 1;
-    B.lo[k] = k < D ? box_lo[k] : 0;
-    B.hi[k] = k < D ? box_hi[k] : 1;
-    B.nf[k] = k < D ? 2 * (B.hi[k] - B.lo[k]) : 1;
-    if (k < D && (B.lo[k] < 0 || B.hi[k] > B.nc[k] || B.hi[k] - B.lo[k] < 4 || (B.hi[k] - B.lo[k]) % 4)) {
-      delete A;
-      set_error("refined box must lie in the domain with sides a positive multiple of 4 coarse cells");
-      return EB_ERR_INVALID;
+  A->lv[0].d = *desc;
+  A->lv[0].d.prims = A->prims.data();
+  A->lv[0].d.nodes = A->nodes.data();
+  // level descriptions: each box over cells [lo, hi) of its parent's grid
+  for (int l = 1; l < L; ++l) {
+    const eb_geom_desc& pd = A->lv[l - 1].d;
+    BoxIdx& B = A->pr[l].B;
+    const int* lo = box_lo + 3 * (l - 1);
+    const int* hi = box_hi + 3 * (l - 1);
+    B.D = D;
+    for (int k = 0; k < 3; ++k) {
+      B.nc[k] = k < D ? pd.n[k] : 1;
+      B.lo[k] = k < D ? lo[k] : 0;
+      B.hi[k] = k < D ? hi[k] : 1;
+      B.nf[k] = k < D ? 2 * (B.hi[k] - B.lo[k]) : 1;
+      if (k < D && (B.lo[k] < 0 || B.hi[k] > B.nc[k] || B.hi[k] - B.lo[k] < 4 || (B.hi[k] - B.lo[k]) % 4)) {
+        delete A;
+        set_error("the box of level " + std::to_string(l) +
+                  " must lie in its parent grid with sides a positive multiple of 4 parent cells");
+        return EB_ERR_INVALID;
+      }
     }
-  }
-  // fine grid descriptions: CF sides Neumann (operator) or zero Dirichlet (corrections)
-  A->df = A->dc;
-  for (int k = 0; k < D; ++k) {
-    A->df.n[k] = B.nf[k];
-    A->df.lo[k] = desc->lo[k] + B.lo[k] * desc->h;
-  }
-  A->df.h = desc->h / 2.0;
-  A->df0 = A->df;
-  for (int k = 0; k < D; ++k)
-    for (int s2 = 0; s2 < 2; ++s2) {
-      bool cf = s2 == 0 ? B.lo[k] > 0 : B.hi[k] < B.nc[k];
-      if (!cf) continue;
-      A->df.bc_type[2 * k + s2] = EB_BC_NEUMANN;
-      A->df.bc_value[2 * k + s2] = 0.0;
-      A->df0.bc_type[2 * k + s2] = EB_BC_DIRICHLET;
-      A->df0.bc_value[2 * k + s2] = 0.0;
-    }
-  A->df0.n_electrodes = desc->n_electrodes;
-  for (int e = 0; e < desc->n_electrodes; ++e) A->df0.electrode_phi[e] = 0.0;
-  eb_status st = eb_geom_build(&A->dc, stream, &A->Gc);
-  if (st == EB_OK) st = eb_geom_build(&A->df, stream, &A->Gf);
-  if (st == EB_OK) st = eb_geom_build(&A->df0, stream, &A->Gf0);
-  if (st != EB_OK) return amr_fail(A, st);
-  A->ncc = A->Gc->L[0].g.ncell;
-  A->nff = A->Gf->L[0].g.ncell;
-  if (A->ncc >= (1LL << 32) || A->nff >= (1LL << 32)) {  // the composite kernels index cells in 32 bits
-    set_error("composite grids are limited to 2^32 cells per level");
-    return amr_fail(A, EB_ERR_INVALID);
-  }
-  A->hc = desc->h;
-  A->hf = desc->h / 2.0;
-  A->eps0 = desc->eps_gas;
-  A->cflags = A->Gc->L[0].flags;
-  A->fflags = A->Gf->L[0].flags;
-  // CF sides and face counts
-  CFBox& cb = A->cfb;
-  std::memset(&cb, 0, sizeof(cb));
-  for (int k = 0; k < 3; ++k) {
-    cb.lo[k] = B.lo[k];
-    cb.hi[k] = B.hi[k];
-  }
-  long long off = 0, coff = 0;
-  for (int a = 0; a < D; ++a)
-    for (int s2 = 0; s2 < 2; ++s2) {
-      bool cf = s2 == 0 ? B.lo[a] > 0 : B.hi[a] < B.nc[a];
-      if (!cf) continue;
-      long long nfa = 1, nca = 1;
-      for (int k = 0; k < D; ++k)
-        if (k != a) {
-          nfa *= B.nf[k];
-          nca *= B.hi[k] - B.lo[k];
+    // proper nesting: one parent cell between the box and each CF side of the parent
+    if (l >= 2)
+      for (int k = 0; k < D; ++k) {
+        const BoxIdx& PB = A->pr[l - 1].B;
+        if ((cf_side(PB, k, 0) && B.lo[k] < 1) || (cf_side(PB, k, 1) && B.hi[k] > B.nc[k] - 1)) {
+          delete A;
+          set_error("the box of level " + std::to_string(l) +
+                    " must keep one parent cell away from every coarse-fine side of its parent");
+          return EB_ERR_INVALID;
         }
-      cb.side_a[cb.nside] = a;
-      cb.side_s[cb.nside] = s2;
-      cb.off[cb.nside] = off;
-      cb.coff[cb.nside] = coff;
-      ++cb.nside;
-      off += nfa;
-      coff += nca;
+      }
+    eb_geom_desc& d = A->lv[l].d;
+    d = pd;
+    for (int k = 0; k < D; ++k) {
+      d.n[k] = B.nf[k];
+      d.lo[k] = pd.lo[k] + B.lo[k] * pd.h;
     }
-  cb.off[cb.nside] = off;
-  cb.coff[cb.nside] = coff;
-  A->nface = off;
-  A->ncface = coff;
+    d.h = pd.h / 2.0;
+    // sides on the domain boundary keep the parent's (domain) conditions
+    eb_geom_desc& d0 = A->lv[l].d0;
+    d0 = d;
+    for (int k = 0; k < D; ++k)
+      for (int s2 = 0; s2 < 2; ++s2) {
+        if (!cf_side(B, k, s2)) continue;
+        d.bc_type[2 * k + s2] = EB_BC_NEUMANN;
+        d.bc_value[2 * k + s2] = 0.0;
+        d0.bc_type[2 * k + s2] = EB_BC_DIRICHLET;
+        d0.bc_value[2 * k + s2] = 0.0;
+      }
+    d0.n_electrodes = pd.n_electrodes;
+    for (int e = 0; e < pd.n_electrodes; ++e) d0.electrode_phi[e] = 0.0;
+  }
+  eb_status st = EB_OK;
+  for (int l = 0; l < L && st == EB_OK; ++l) {
+    st = eb_geom_build(&A->lv[l].d, stream, &A->lv[l].G);
+    if (st == EB_OK && l > 0) st = eb_geom_build(&A->lv[l].d0, stream, &A->lv[l].G0);
+  }
+  if (st != EB_OK) return amr_fail(A, st);
+  for (int l = 0; l < L; ++l) {
+    AmrLevel& v = A->lv[l];
+    v.n = v.G->L[0].g.ncell;
+    v.h = v.d.h;
+    v.flags = v.G->L[0].flags;
+    if (v.n >= (1LL << 32)) {  // the composite kernels index cells in 32 bits
+      set_error("composite grids are limited to 2^32 cells per level");
+      return amr_fail(A, EB_ERR_INVALID);
+    }
+  }
+  A->eps0 = desc->eps_gas;
   auto alloc = [&](size_t bytes) { return dev_alloc(A->allocs, std::max<size_t>(bytes, 16), &A->bytes, &st); };
-  A->faces = (CFFace*)alloc(sizeof(CFFace) * off);
-  A->cfaces = (CFCoarse*)alloc(sizeof(CFCoarse) * coff);
-  A->fl = (double*)alloc(sizeof(double) * off);
-  A->kf = (double*)alloc(sizeof(double) * 2 * A->nff);
-  A->pcf = (double*)alloc(sizeof(double) * 2 * A->ncc);
-  A->rc = (double*)alloc(sizeof(double) * 2 * A->ncc);
-  A->bc0 = (double*)alloc(sizeof(double) * 2 * A->ncc);
-  A->bf0 = (double*)alloc(sizeof(double) * 2 * A->nff);
-  A->ec = (double*)alloc(sizeof(double) * 2 * A->ncc);
-  A->rf = (double*)alloc(sizeof(double) * 2 * A->nff);
-  A->ef = (double*)alloc(sizeof(double) * 2 * A->nff);
+  // CF sides and face counts of every pair
+  for (int l = 1; l < L; ++l) {
+    AmrPair& P = A->pr[l];
+    const BoxIdx& B = P.B;
+    CFBox& cb = P.cfb;
+    std::memset(&cb, 0, sizeof(cb));
+    for (int k = 0; k < 3; ++k) {
+      cb.lo[k] = B.lo[k];
+      cb.hi[k] = B.hi[k];
+    }
+    long long off = 0, coff = 0;
+    for (int a = 0; a < D; ++a)
+      for (int s2 = 0; s2 < 2; ++s2) {
+        if (!cf_side(B, a, s2)) continue;
+        long long nfa = 1, nca = 1;
+        for (int k = 0; k < D; ++k)
+          if (k != a) {
+            nfa *= B.nf[k];
+            nca *= B.hi[k] - B.lo[k];
+          }
+        cb.side_a[cb.nside] = a;
+        cb.side_s[cb.nside] = s2;
+        cb.off[cb.nside] = off;
+        cb.coff[cb.nside] = coff;
+        ++cb.nside;
+        off += nfa;
+        coff += nca;
+      }
+    cb.off[cb.nside] = off;
+    cb.coff[cb.nside] = coff;
+    P.nface = off;
+    P.ncface = coff;
+    P.faces = (CFFace*)alloc(sizeof(CFFace) * off);
+    P.cfaces = (CFCoarse*)alloc(sizeof(CFCoarse) * coff);
+    P.fl = (double*)alloc(sizeof(double) * off);
+  }
+  for (int l = 0; l < L; ++l) {
+    AmrLevel& v = A->lv[l];
+    const size_t b2 = sizeof(double) * 2 * v.n;
+    if (l < L - 1) v.pc = (double*)alloc(b2);
+    if (l > 0) v.kap = (double*)alloc(b2);
+    v.r = (double*)alloc(b2);
+    v.b0 = (double*)alloc(b2);
+    v.e = (double*)alloc(b2);
+  }
   A->d_status = (int*)alloc(sizeof(int));
   A->d_norm = (unsigned long long*)alloc(sizeof(unsigned long long) * 2);
   if (st != EB_OK) return amr_fail(A, st);
-  st = build_cf(A->Gf, A->Gc, cb, A->faces, A->cfaces, A->d_status, s);
+  for (int l = 1; l < L && st == EB_OK; ++l) {
+    AmrPair& P = A->pr[l];
+    st = build_cf(A->lv[l].G, A->lv[l - 1].G, P.cfb, P.faces, P.cfaces, A->d_status, s);
+    if (st != EB_OK) break;
+    eb_geom_arrays ga;
+    std::memset(&ga, 0, sizeof(ga));
+    ga.kappa = A->lv[l].kap;
+    st = eb_geom_export(A->lv[l].G, &ga, stream);
+  }
   if (st != EB_OK) return amr_fail(A, st);
-  eb_geom_arrays ga;
-  std::memset(&ga, 0, sizeof(ga));
-  ga.kappa = A->kf;
-  st = eb_geom_export(A->Gf, &ga, stream);
   // a correction inside the preconditioner is one V-cycle of 3+3 sweeps: one
   // inner V-cycle per defect-correction step and a loose tolerance (on the
   // 256^3 + 128^3 pin-plane grid: 21 FGMRES iterations and 285 ms, against 19
@@ -499,13 +558,21 @@ extern "C" eb_status eb_amr_setup(const eb_geom_desc* desc, const int box_lo[3],
   eb_solver_opts oc = A->o;
   oc.inner_cycles = 1;
   oc.nu1 = oc.nu2 = 3;
-  if (st == EB_OK) st = eb_poisson_setup(A->Gc, &oc, stream, &A->Pc);
-  if (st == EB_OK) st = eb_poisson_setup(A->Gf, &A->o, stream, &A->Pf);
-  if (st == EB_OK) st = eb_poisson_setup(A->Gf0, &oc, stream, &A->Pf0);
+  st = eb_poisson_setup(A->lv[0].G, &oc, stream, &A->lv[0].P);
+  A->lv[0].P0 = A->lv[0].P;
+  for (int l = 1; l < L && st == EB_OK; ++l) {
+    st = eb_poisson_setup(A->lv[l].G, &A->o, stream, &A->lv[l].P);
+    if (st == EB_OK) st = eb_poisson_setup(A->lv[l].G0, &oc, stream, &A->lv[l].P0);
+  }
   if (st != EB_OK) return amr_fail(A, st);
   if (cudaStreamSynchronize(s) != cudaSuccess) return amr_fail(A, cuda_fail(cudaGetLastError(), "amr setup"));
   *out = A;
   return EB_OK;
+}
+
+extern "C" eb_status eb_amr_setup(const eb_geom_desc* desc, const int box_lo[3], const int box_hi[3],
+                                  const eb_solver_opts* opts, void* stream, eb_amr** out) {
+  return eb_amr_setup_levels(desc, 2, box_lo, box_hi, opts, stream, out);
 }
 
 extern "C" eb_status eb_amr_query(const eb_amr* A, long long* n_coarse, long long* n_fine, int fine_n[3],
@@ -514,54 +581,93 @@ extern "C" eb_status eb_amr_query(const eb_amr* A, long long* n_coarse, long lon
     set_error("null argument");
     return EB_ERR_INVALID;
   }
-  if (n_coarse) *n_coarse = A->ncc;
-  if (n_fine) *n_fine = A->nff;
+  if (n_coarse) *n_coarse = A->lv[0].n;
+  if (n_fine) *n_fine = A->lv[1].n;
   if (fine_n)
-    for (int k = 0; k < 3; ++k) fine_n[k] = A->B.nf[k];
-  if (cf_faces) *cf_faces = A->nface;
+    for (int k = 0; k < 3; ++k) fine_n[k] = A->pr[1].B.nf[k];
+  if (cf_faces) *cf_faces = A->pr[1].nface;
   return EB_OK;
 }
 
-// composite residual into A->rc / A->rf (phi_c values under the box are replaced by fine means)
-// b of both operators for the given data, into A->bc0 / A->bf0
-static eb_status amr_rhs(eb_amr* A, const double* rhs_c, const double* sig_c, const double* rhs_f,
-                         const double* sig_f, cudaStream_t s) {
-  eb_status st = poisson_rhs(A->Pc, rhs_c, sig_c, A->bc0, s);
-  if (st == EB_OK) st = poisson_rhs(A->Pf, rhs_f, sig_f, A->bf0, s);
+extern "C" eb_status eb_amr_level_query(const eb_amr* A, int level, int* n_levels, long long* n_cells, int n[3],
+                                        double lo[3], double* h, long long* cf_faces) {
+  if (!A || level < 0 || level >= A->L) {
+    set_error(A ? "level out of range" : "null argument");
+    return EB_ERR_INVALID;
+  }
+  const AmrLevel& v = A->lv[level];
+  if (n_levels) *n_levels = A->L;
+  if (n_cells) *n_cells = v.n;
+  for (int k = 0; k < 3; ++k) {
+    if (n) n[k] = k < A->D ? v.d.n[k] : 1;
+    if (lo) lo[k] = k < A->D ? v.d.lo[k] : 0.0;
+  }
+  if (h) *h = v.h;
+  if (cf_faces) *cf_faces = level > 0 ? A->pr[level].nface : 0;
+  return EB_OK;
+}
+
+extern "C" eb_status eb_amr_level_geom(const eb_amr* A, int level, const eb_geom** out) {
+  if (!A || !out || level < 0 || level >= A->L) {
+    set_error(A && out ? "level out of range" : "null argument");
+    return EB_ERR_INVALID;
+  }
+  *out = A->lv[level].G;
+  return EB_OK;
+}
+
+// b of every level's operator for the given data, into lv[l].b0
+static eb_status amr_rhs(eb_amr* A, const double* const* rhs, const double* const* sig, cudaStream_t s) {
+  eb_status st = EB_OK;
+  for (int l = 0; l < A->L && st == EB_OK; ++l)
+    st = poisson_rhs(A->lv[l].P, rhs[l], sig ? sig[l] : nullptr, A->lv[l].b0, s);
   return st;
 }
 
-static eb_status amr_resid(eb_amr* A, const double* phi_c, const double* phi_f, cudaStream_t s) {
-  cudaMemcpyAsync(A->pcf, phi_c, 2 * A->ncc * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  k_avg_down<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->cflags, A->fflags, A->kf, phi_f, A->pcf, A->ncc, A->nff);
-  note_launch();
-  eb_status st = poisson_residual_view(A->Pc, A->bc0, A->pcf, A->rc, s);
-  if (st == EB_OK) st = poisson_residual_view(A->Pf, A->bf0, phi_f, A->rf, s);
-  if (st != EB_OK) return st;
-  if (A->nface) {
-    k_cf_flux<<<nb(A->nface), TBA, 0, s>>>(A->faces, A->nface, A->pcf, phi_f, A->eps0, A->hf, A->fl);
+// composite residual into lv[l].r: every level's values under the next finer
+// box are first replaced by the finer level's means, finest first
+static eb_status amr_resid(eb_amr* A, const double* const* phi, cudaStream_t s) {
+  const int L = A->L;
+  const double* val[AMR_MAXL];
+  val[L - 1] = phi[L - 1];
+  for (int l = L - 2; l >= 0; --l) {
+    AmrLevel &c = A->lv[l], &f = A->lv[l + 1];
+    cudaMemcpyAsync(c.pc, phi[l], 2 * c.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    k_avg_down<<<nb(c.n), TBA, 0, s>>>(A->pr[l + 1].B, c.flags, f.flags, f.kap, val[l + 1], c.pc, c.n, f.n);
     note_launch();
-    for (int sd = 0; sd < A->cfb.nside; ++sd) {
-      long long t0 = A->cfb.off[sd], t1 = A->cfb.off[sd + 1];
-      k_cf_fine_apply<<<nb(t1 - t0), TBA, 0, s>>>(A->faces, t0, t1, A->fl, A->hf, A->rf);
+    val[l] = c.pc;
+  }
+  eb_status st = EB_OK;
+  for (int l = 0; l < L && st == EB_OK; ++l) st = poisson_residual_view(A->lv[l].P, A->lv[l].b0, val[l], A->lv[l].r, s);
+  if (st != EB_OK) return st;
+  for (int l = 1; l < L; ++l) {
+    const AmrPair& P = A->pr[l];
+    AmrLevel &c = A->lv[l - 1], &f = A->lv[l];
+    if (!P.nface) continue;
+    k_cf_flux<<<nb(P.nface), TBA, 0, s>>>(P.faces, P.nface, val[l - 1], val[l], A->eps0, f.h, P.fl);
+    note_launch();
+    for (int sd = 0; sd < P.cfb.nside; ++sd) {
+      long long t0 = P.cfb.off[sd], t1 = P.cfb.off[sd + 1];
+      k_cf_fine_apply<<<nb(t1 - t0), TBA, 0, s>>>(P.faces, t0, t1, P.fl, f.h, f.r);
       note_launch();
     }
-    k_cf_coarse_apply<<<nb(A->ncface), TBA, 0, s>>>(A->cfaces, A->ncface, A->fl, A->pcf, A->ncc, A->hc, A->D,
-                                                     A->rc);
+    k_cf_coarse_apply<<<nb(P.ncface), TBA, 0, s>>>(P.cfaces, P.ncface, P.fl, val[l - 1], c.n, c.h, A->D, c.r);
     note_launch();
   }
-  k_zero_under<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->rc, A->ncc);
-  note_launch();
+  for (int l = 1; l < L; ++l) {
+    k_zero_under<<<nb(A->lv[l - 1].n), TBA, 0, s>>>(A->pr[l].B, A->lv[l - 1].r, A->lv[l - 1].n);
+    note_launch();
+  }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? EB_OK : cuda_fail(e, "composite residual");
 }
 
 static eb_status amr_norm(eb_amr* A, cudaStream_t s, double* out) {
   cudaMemsetAsync(A->d_norm, 0, sizeof(unsigned long long), s);
-  k_absmax2<<<nb(A->ncc), TBA, 0, s>>>(A->cflags, A->ncc, A->rc, A->d_norm);
-  note_launch();
-  k_absmax2<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, A->rf, A->d_norm);
-  note_launch();
+  for (int l = 0; l < A->L; ++l) {
+    k_absmax2<<<nb(A->lv[l].n), TBA, 0, s>>>(A->lv[l].flags, A->lv[l].n, A->lv[l].r, A->d_norm);
+    note_launch();
+  }
   unsigned long long v = 0;
   cudaError_t e = cudaMemcpyAsync(&v, A->d_norm, sizeof(v), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -570,135 +676,191 @@ static eb_status amr_norm(eb_amr* A, cudaStream_t s, double* out) {
   return EB_OK;
 }
 
-extern "C" eb_status eb_amr_residual(eb_amr* A, const double* d_rhs_c, const double* d_sig_c, const double* d_rhs_f,
-                                     const double* d_sig_f, const double* d_phi_c, const double* d_phi_f,
-                                     double* d_r_c, double* d_r_f, void* stream) {
-  if (!A || !d_rhs_c || !d_rhs_f || !d_phi_c || !d_phi_f || !d_r_c || !d_r_f) {
+static bool all_set(const double* const* p, int n) {
+  if (!p) return false;
+  for (int l = 0; l < n; ++l)
+    if (!p[l]) return false;
+  return true;
+}
+
+extern "C" eb_status eb_amr_residual_levels(eb_amr* A, const double* const* d_rhs, const double* const* d_sig,
+                                            const double* const* d_phi, double* const* d_r, void* stream) {
+  if (!A || !all_set(d_rhs, A->L) || !all_set(d_phi, A->L) || !d_r || !all_set(d_r, A->L)) {
     set_error("null argument");
     return EB_ERR_INVALID;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  eb_status st = amr_rhs(A, d_rhs_c, d_sig_c, d_rhs_f, d_sig_f, s);
-  if (st == EB_OK) st = amr_resid(A, d_phi_c, d_phi_f, s);
+  eb_status st = amr_rhs(A, d_rhs, d_sig, s);
+  if (st == EB_OK) st = amr_resid(A, d_phi, s);
   if (st != EB_OK) return st;
-  cudaMemcpyAsync(d_r_c, A->rc, 2 * A->ncc * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  cudaMemcpyAsync(d_r_f, A->rf, 2 * A->nff * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  for (int l = 0; l < A->L; ++l)
+    cudaMemcpyAsync(d_r[l], A->lv[l].r, 2 * A->lv[l].n * sizeof(double), cudaMemcpyDeviceToDevice, s);
   cudaError_t e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? EB_OK : cuda_fail(e, "composite residual");
 }
 
+extern "C" eb_status eb_amr_residual(eb_amr* A, const double* d_rhs_c, const double* d_sig_c, const double* d_rhs_f,
+                                     const double* d_sig_f, const double* d_phi_c, const double* d_phi_f,
+                                     double* d_r_c, double* d_r_f, void* stream) {
+  if (A && A->L != 2) {
+    set_error("eb_amr_residual serves two-level grids; use eb_amr_residual_levels");
+    return EB_ERR_INVALID;
+  }
+  const double* rhs[2] = {d_rhs_c, d_rhs_f};
+  const double* sig[2] = {d_sig_c, d_sig_f};
+  const double* phi[2] = {d_phi_c, d_phi_f};
+  double* r[2] = {d_r_c, d_r_f};
+  return eb_amr_residual_levels(A, rhs, sig, phi, r, stream);
+}
+
+// level l's cells under the next finer box are skipped by the dot products
+static const BoxIdx& dot_box(const eb_amr* A, int l) { return A->pr[l + 1 < A->L ? l + 1 : l].B; }
+
 static double cv_dot(eb_amr* A, const CVec& a, const CVec& b, cudaStream_t s) {
-  k_cv_dot<<<DOT_BLOCKS, TBA, 0, s>>>(A->B, A->cflags, A->ncc, 1, a.c, b.c, A->d_part);
-  note_launch();
-  k_cv_dot<<<DOT_BLOCKS, TBA, 0, s>>>(A->B, A->fflags, A->nff, 0, a.f, b.f, A->d_part + DOT_BLOCKS);
-  note_launch();
-  double h[2 * DOT_BLOCKS];
-  cudaMemcpyAsync(h, A->d_part, sizeof(h), cudaMemcpyDeviceToHost, s);
+  const int L = A->L;
+  for (int l = 0; l < L; ++l) {
+    const AmrLevel& v = A->lv[l];
+    k_cv_dot<<<DOT_BLOCKS, TBA, 0, s>>>(dot_box(A, l), v.flags, v.n, l < L - 1, a.v[l], b.v[l],
+                                        A->d_part + l * DOT_BLOCKS);
+    note_launch();
+  }
+  std::vector<double> h(L * DOT_BLOCKS);
+  cudaMemcpyAsync(h.data(), A->d_part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   double t = 0.0;
-  for (int i = 0; i < 2 * DOT_BLOCKS; ++i) t += h[i];
+  for (int i = 0; i < L * DOT_BLOCKS; ++i) t += h[i];
   return t;
 }
 static void cv_axpby(eb_amr* A, double a, const CVec& x, double b, const CVec& y, cudaStream_t s) {
-  k_cv_axpby<<<nb(A->ncc), TBA, 0, s>>>(A->cflags, A->ncc, a, x.c, b, y.c);
-  note_launch();
-  k_cv_axpby<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, a, x.f, b, y.f);
-  note_launch();
+  for (int l = 0; l < A->L; ++l) {
+    k_cv_axpby<<<nb(A->lv[l].n), TBA, 0, s>>>(A->lv[l].flags, A->lv[l].n, a, x.v[l], b, y.v[l]);
+    note_launch();
+  }
+}
+static void cv_copy(eb_amr* A, const CVec& x, const CVec& y, cudaStream_t s) {
+  for (int l = 0; l < A->L; ++l)
+    cudaMemcpyAsync(y.v[l], x.v[l], 2 * A->lv[l].n * sizeof(double), cudaMemcpyDeviceToDevice, s);
 }
 
-// h[i] = (V[i], w) for i < m, both grids, one launch per grid and one sync;
+// h[i] = (V[i], w) for i < m, all levels, one launch per level and one sync;
 // with `self` also h[m] = (w, w), from the same pass over w
 static void cv_mdot(eb_amr* A, int m, const CVec& w, double* h, cudaStream_t s, bool self = false) {
-  CVPtrs pc{}, pf{};
-  for (int i = 0; i < m; ++i) {
-    pc.v[i] = A->V[i].c;
-    pf.v[i] = A->V[i].f;
+  const int L = A->L;
+  CVPtrs p[AMR_MAXL] = {};
+  for (int l = 0; l < L; ++l) {
+    for (int i = 0; i < m; ++i) p[l].v[i] = A->V[i].v[l];
+    if (self) p[l].v[m] = w.v[l];
   }
-  if (self) {
-    pc.v[m] = w.c;
-    pf.v[m] = w.f;
-    ++m;
+  if (self) ++m;
+  for (int l = 0; l < L; ++l) {
+    const AmrLevel& v = A->lv[l];
+    k_cv_mdot<<<DOT_BLOCKS, TBA, 0, s>>>(dot_box(A, l), v.flags, v.n, l < L - 1, m, p[l], w.v[l],
+                                         A->d_part + l * CV_MAXV * DOT_BLOCKS);
+    note_launch();
   }
-  k_cv_mdot<<<DOT_BLOCKS, TBA, 0, s>>>(A->B, A->cflags, A->ncc, 1, m, pc, w.c, A->d_part);
-  note_launch();
-  k_cv_mdot<<<DOT_BLOCKS, TBA, 0, s>>>(A->B, A->fflags, A->nff, 0, m, pf, w.f, A->d_part + CV_MAXV * DOT_BLOCKS);
-  note_launch();
-  std::vector<double> hp(2 * CV_MAXV * DOT_BLOCKS);
+  std::vector<double> hp(L * CV_MAXV * DOT_BLOCKS);
   cudaMemcpyAsync(hp.data(), A->d_part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   for (int i = 0; i < m; ++i) {
     double t = 0.0;
-    for (int b = 0; b < DOT_BLOCKS; ++b) t += hp[i * DOT_BLOCKS + b];
-    for (int b = 0; b < DOT_BLOCKS; ++b) t += hp[CV_MAXV * DOT_BLOCKS + i * DOT_BLOCKS + b];
+    for (int l = 0; l < L; ++l)
+      for (int b = 0; b < DOT_BLOCKS; ++b) t += hp[l * CV_MAXV * DOT_BLOCKS + i * DOT_BLOCKS + b];
     h[i] = t;
   }
 }
 // w -= sum_{i < m} h[i] V[i]
 static void cv_maxpy(eb_amr* A, int m, const double* h, const CVec& w, cudaStream_t s) {
-  CVPtrs pc{}, pf{};
-  for (int i = 0; i < m; ++i) {
-    pc.v[i] = A->V[i].c;
-    pf.v[i] = A->V[i].f;
-    pc.a[i] = pf.a[i] = h[i];
+  for (int l = 0; l < A->L; ++l) {
+    CVPtrs p{};
+    for (int i = 0; i < m; ++i) {
+      p.v[i] = A->V[i].v[l];
+      p.a[i] = h[i];
+    }
+    k_cv_maxpy<<<nb(A->lv[l].n), TBA, 0, s>>>(A->lv[l].flags, A->lv[l].n, m, p, w.v[l]);
+    note_launch();
   }
-  k_cv_maxpy<<<nb(A->ncc), TBA, 0, s>>>(A->cflags, A->ncc, m, pc, w.c);
-  note_launch();
-  k_cv_maxpy<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, m, pf, w.f);
-  note_launch();
 }
 
-// accuracy asked of the two multigrid corrections inside one FAC step: loose
+// accuracy asked of the multigrid corrections inside one FAC step: loose
 // enough that each stops after its first V-cycle
 constexpr double FAC_TOL = 3e-1;
 
-// z = M^-1 v: one FAC step from zero (coarse correction over the domain,
-// constant per parent on the box, then a fine correction of what remains);
-// uses A->rc / rf / ec / ef / tmp as scratch.
+// w[l] for l = L-2 .. lmin: cells under the next finer box take the mean of
+// that level's children (finest first, so every level sees the whole remainder)
+static void restrict_down(eb_amr* A, const CVec& w, int lmin, cudaStream_t s) {
+  for (int l = A->L - 2; l >= lmin; --l) {
+    const AmrLevel &c = A->lv[l], &f = A->lv[l + 1];
+    k_zero_under<<<nb(c.n), TBA, 0, s>>>(A->pr[l + 1].B, w.v[l], c.n);
+    note_launch();
+    k_restrict_under<<<nb(c.n), TBA, 0, s>>>(A->pr[l + 1].B, f.flags, w.v[l + 1], w.v[l], c.n, f.n);
+    note_launch();
+  }
+}
+
+// z = M^-1 v: one multiplicative FAC sweep from zero, coarse to fine: a
+// correction of level 0 over the domain (the finer parts of v restricted
+// under the boxes), added constant per parent on level 1; then on every finer
+// level a correction of what remains there (zero Dirichlet CF sides), the
+// remainder of the still finer levels restricted under its box, added to the
+// level and constant per parent on the next.  Uses lv[].r / e and tmp.
 static eb_status fac_apply(eb_amr* A, const CVec& v, const CVec& z, int* cycles, cudaStream_t s) {
   const double tol = FAC_TOL;
-  cudaMemcpyAsync(A->rc, v.c, 2 * A->ncc * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  k_zero_under<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->rc, A->ncc);
-  note_launch();
-  k_restrict_under<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->fflags, v.f, A->rc, A->ncc, A->nff);
-  note_launch();
+  const int L = A->L;
+  cv_copy(A, v, A->tmp, s);
+  restrict_down(A, A->tmp, 0, s);
   int cyc = 0, outer = 0;
   double kms = 0.0;
-  eb_status st = poisson_solve_b(A->Pc, A->rc, A->ec, tol, &cyc, s, &outer, &kms);
+  eb_status st = poisson_solve_b(A->lv[0].P, A->tmp.v[0], A->lv[0].e, tol, &cyc, s, &outer, &kms);
   *cycles += cyc;
   amr_count(A, 0, cyc, outer, kms);
   if (st != EB_OK) return st;
-  cudaMemsetAsync(z.c, 0, 2 * A->ncc * sizeof(double), s);
-  cudaMemsetAsync(z.f, 0, 2 * A->nff * sizeof(double), s);
-  k_add_coarse<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->ec, z.c, A->ncc);
-  note_launch();
-  k_prolong_const<<<nb(A->nff), TBA, 0, s>>>(A->B, A->fflags, A->ec, z.f, A->ncc, A->nff);
-  note_launch();
-  // what remains on the box: v_f - (A z)_f = v_f - b_f + r_f(z)
-  st = amr_resid(A, z.c, z.f, s);
-  if (st != EB_OK) return st;
-  k_cv_sub<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, A->bvec.f, A->rf, A->tmp.f);  // (A z)_f
-  note_launch();
-  k_cv_axpby<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, 1.0, v.f, -1.0, A->tmp.f);  // v_f - (A z)_f
-  note_launch();
-  st = poisson_solve_b(A->Pf0, A->tmp.f, A->ef, tol, &cyc, s, &outer, &kms);
-  *cycles += cyc;
-  amr_count(A, 1, cyc, outer, kms);
-  if (st != EB_OK) return st;
-  k_axpy_masked<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, A->ef, z.f);
-  note_launch();
+  for (int l = 0; l < L; ++l) cudaMemsetAsync(z.v[l], 0, 2 * A->lv[l].n * sizeof(double), s);
+  for (int l = 0; l < L; ++l) {
+    if (l > 0) {
+      // what remains on levels l and finer: v - A z, restricted into level l
+      st = amr_resid(A, z.v, s);
+      if (st != EB_OK) return st;
+      for (int k = l; k < L; ++k) {
+        const AmrLevel& q = A->lv[k];
+        k_cv_sub<<<nb(q.n), TBA, 0, s>>>(q.flags, q.n, A->bvec.v[k], q.r, A->tmp.v[k]);  // (A z)_k
+        note_launch();
+        k_cv_axpby<<<nb(q.n), TBA, 0, s>>>(q.flags, q.n, 1.0, v.v[k], -1.0, A->tmp.v[k]);  // v_k - (A z)_k
+        note_launch();
+      }
+      restrict_down(A, A->tmp, l, s);
+      st = poisson_solve_b(A->lv[l].P0, A->tmp.v[l], A->lv[l].e, tol, &cyc, s, &outer, &kms);
+      *cycles += cyc;
+      amr_count(A, 1, cyc, outer, kms);
+      if (st != EB_OK) return st;
+    }
+    const AmrLevel& c = A->lv[l];
+    if (l < L - 1) {
+      const AmrLevel& f = A->lv[l + 1];
+      k_add_coarse<<<nb(c.n), TBA, 0, s>>>(A->pr[l + 1].B, c.e, z.v[l], c.n);
+      note_launch();
+      k_prolong_const<<<nb(f.n), TBA, 0, s>>>(A->pr[l + 1].B, f.flags, c.e, z.v[l + 1], c.n, f.n);
+      note_launch();
+    } else {
+      k_axpy_masked<<<nb(c.n), TBA, 0, s>>>(c.flags, c.n, c.e, z.v[l]);
+      note_launch();
+    }
+  }
   return EB_OK;
 }
 
 // w = A z (homogeneous operator) = b - r(z)
 static eb_status op_apply(eb_amr* A, const CVec& z, const CVec& w, cudaStream_t s) {
-  eb_status st = amr_resid(A, z.c, z.f, s);
+  eb_status st = amr_resid(A, z.v, s);
   if (st != EB_OK) return st;
-  k_cv_sub<<<nb(A->ncc), TBA, 0, s>>>(A->cflags, A->ncc, A->bvec.c, A->rc, w.c);
-  note_launch();
-  k_zero_under<<<nb(A->ncc), TBA, 0, s>>>(A->B, w.c, A->ncc);
-  note_launch();
-  k_cv_sub<<<nb(A->nff), TBA, 0, s>>>(A->fflags, A->nff, A->bvec.f, A->rf, w.f);
-  note_launch();
+  for (int l = 0; l < A->L; ++l) {
+    const AmrLevel& q = A->lv[l];
+    k_cv_sub<<<nb(q.n), TBA, 0, s>>>(q.flags, q.n, A->bvec.v[l], q.r, w.v[l]);
+    note_launch();
+    if (l < A->L - 1) {
+      k_zero_under<<<nb(q.n), TBA, 0, s>>>(A->pr[l + 1].B, w.v[l], q.n);
+      note_launch();
+    }
+  }
   return EB_OK;
 }
 
@@ -709,15 +871,15 @@ static eb_status amr_workspace(eb_amr* A) {
   eb_status st = EB_OK;
   auto vec = [&]() {
     CVec v;
-    v.c = (double*)dev_alloc(A->allocs, 2 * A->ncc * sizeof(double), &A->bytes, &st);
-    v.f = (double*)dev_alloc(A->allocs, 2 * A->nff * sizeof(double), &A->bytes, &st);
+    for (int l = 0; l < A->L; ++l)
+      v.v[l] = (double*)dev_alloc(A->allocs, 2 * A->lv[l].n * sizeof(double), &A->bytes, &st);
     return v;
   };
   for (int i = 0; i <= GM; ++i) A->V.push_back(vec());
   for (int i = 0; i < GM; ++i) A->Z.push_back(vec());
   A->bvec = vec();
   A->tmp = vec();
-  A->d_part = (double*)dev_alloc(A->allocs, 2 * CV_MAXV * DOT_BLOCKS * sizeof(double), &A->bytes, &st);
+  A->d_part = (double*)dev_alloc(A->allocs, A->L * CV_MAXV * DOT_BLOCKS * sizeof(double), &A->bytes, &st);
   if (st != EB_OK) {
     A->V.clear();
     A->Z.clear();
@@ -725,13 +887,13 @@ static eb_status amr_workspace(eb_amr* A) {
   return st;
 }
 
-extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double* d_sig_c, const double* d_rhs_f,
-                                  const double* d_sig_f, double* d_phi_c, double* d_phi_f, eb_solve_info* info,
-                                  void* stream) {
-  if (!A || !d_rhs_c || !d_rhs_f || !d_phi_c || !d_phi_f) {
+extern "C" eb_status eb_amr_solve_levels(eb_amr* A, const double* const* d_rhs, const double* const* d_sig,
+                                         double* const* d_phi, eb_solve_info* info, void* stream) {
+  if (!A || !all_set(d_rhs, A->L) || !d_phi || !all_set(d_phi, A->L)) {
     set_error("null argument");
     return EB_ERR_INVALID;
   }
+  const int L = A->L;
   cudaStream_t s = (cudaStream_t)stream;
   eb_solve_info inf;
   std::memset(&inf, 0, sizeof(inf));
@@ -740,23 +902,29 @@ extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double
   eb_status st = amr_workspace(A);
   if (st != EB_OK) return st;
   // b: the composite residual at phi = 0
-  cudaMemsetAsync(A->ec, 0, 2 * A->ncc * sizeof(double), s);
-  cudaMemsetAsync(A->ef, 0, 2 * A->nff * sizeof(double), s);
-  st = amr_rhs(A, d_rhs_c, d_sig_c, d_rhs_f, d_sig_f, s);
-  if (st == EB_OK) st = amr_resid(A, A->ec, A->ef, s);
+  CVec zero;
+  for (int l = 0; l < L; ++l) {
+    zero.v[l] = A->lv[l].e;
+    cudaMemsetAsync(A->lv[l].e, 0, 2 * A->lv[l].n * sizeof(double), s);
+  }
+  st = amr_rhs(A, d_rhs, d_sig, s);
+  if (st == EB_OK) st = amr_resid(A, zero.v, s);
   double bn = 0.0, r = 0.0;
   if (st == EB_OK) st = amr_norm(A, s, &bn);
   if (st != EB_OK) return st;
-  cudaMemcpyAsync(A->bvec.c, A->rc, 2 * A->ncc * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  cudaMemcpyAsync(A->bvec.f, A->rf, 2 * A->nff * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  const CVec x{d_phi_c, d_phi_f};
+  CVec res, x;
+  for (int l = 0; l < L; ++l) {
+    res.v[l] = A->lv[l].r;
+    x.v[l] = d_phi[l];
+  }
+  cv_copy(A, res, A->bvec, s);
   int it = 0, cycles = 0;
   const int max_it = std::max(1, A->o.max_cycles);
-  // restarted FGMRES, right-preconditioned by one FAC step (Sec. 3.3.2's
+  // restarted FGMRES, right-preconditioned by one FAC sweep (Sec. 3.3.2's
   // multigrid as the inner solver of every correction)
   st = EB_ERR_NOT_CONVERGED;
   while (it < max_it) {
-    eb_status s2 = amr_resid(A, x.c, x.f, s);
+    eb_status s2 = amr_resid(A, x.v, s);
     if (s2 == EB_OK) s2 = amr_norm(A, s, &r);
     if (s2 != EB_OK) {
       st = s2;
@@ -768,10 +936,11 @@ extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double
     }
     if (!(r == r) || r > 1e6 * bn) break;
     // v0 = r / |r|_2
-    cudaMemcpyAsync(A->V[0].c, A->rc, 2 * A->ncc * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(A->V[0].f, A->rf, 2 * A->nff * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    k_zero_under<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->V[0].c, A->ncc);
-    note_launch();
+    cv_copy(A, res, A->V[0], s);
+    for (int l = 0; l < L - 1; ++l) {
+      k_zero_under<<<nb(A->lv[l].n), TBA, 0, s>>>(A->pr[l + 1].B, A->V[0].v[l], A->lv[l].n);
+      note_launch();
+    }
     double beta = std::sqrt(cv_dot(A, A->V[0], A->V[0], s));
     if (!(beta > 0.0)) {
       st = EB_OK;
@@ -841,10 +1010,14 @@ extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double
     }
     for (int i = 0; i < k; ++i) cv_axpby(A, y[i], A->Z[i], 1.0, x, s);
   }
-  // report phi_c under the box as the fine means
+  // report every level's phi under the next finer box as the finer means (finest first)
   if (st == EB_OK || st == EB_ERR_NOT_CONVERGED) {
-    k_avg_down<<<nb(A->ncc), TBA, 0, s>>>(A->B, A->cflags, A->fflags, A->kf, d_phi_f, d_phi_c, A->ncc, A->nff);
-    note_launch();
+    for (int l = L - 2; l >= 0; --l) {
+      const AmrLevel &c = A->lv[l], &f = A->lv[l + 1];
+      k_avg_down<<<nb(c.n), TBA, 0, s>>>(A->pr[l + 1].B, c.flags, f.flags, f.kap, d_phi[l + 1], d_phi[l], c.n,
+                                         f.n);
+      note_launch();
+    }
     if (st == EB_ERR_NOT_CONVERGED) set_error("composite iteration cap reached");
   }
   cudaError_t e = cudaStreamSynchronize(s);
@@ -858,6 +1031,28 @@ extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double
   inf.kernel_launches = launch_total() - launches0;
   if (info) *info = inf;
   return st;
+}
+
+extern "C" eb_status eb_amr_solve(eb_amr* A, const double* d_rhs_c, const double* d_sig_c, const double* d_rhs_f,
+                                  const double* d_sig_f, double* d_phi_c, double* d_phi_f, eb_solve_info* info,
+                                  void* stream) {
+  if (A && A->L != 2) {
+    set_error("eb_amr_solve serves two-level grids; use eb_amr_solve_levels");
+    return EB_ERR_INVALID;
+  }
+  const double* rhs[2] = {d_rhs_c, d_rhs_f};
+  const double* sig[2] = {d_sig_c, d_sig_f};
+  double* phi[2] = {d_phi_c, d_phi_f};
+  return eb_amr_solve_levels(A, rhs, sig, phi, info, stream);
+}
+
+extern "C" eb_status eb_amr_field_eval(eb_amr* A, int level, const double* d_phi, const double* d_sigma,
+                                       double* d_E, double* d_En, void* stream) {
+  if (!A || level < 0 || level >= A->L) {
+    set_error(A ? "level out of range" : "null argument");
+    return EB_ERR_INVALID;
+  }
+  return eb_field_eval(A->lv[level].P, d_phi, d_sigma, d_E, d_En, stream);
 }
 
 extern "C" eb_status eb_amr_kernel_stats(const eb_amr* A, double out[8]) {

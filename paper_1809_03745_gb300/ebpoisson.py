@@ -92,7 +92,9 @@ EXPORTS = ["eb_status_str", "eb_last_error", "eb_geom_build", "eb_geom_query", "
            "eb_poisson_residual_noalloc", "eb_poisson_solve_batched", "eb_server_opts_default", "eb_server_create",
            "eb_server_submit", "eb_server_poll", "eb_server_wait", "eb_server_query", "eb_server_destroy",
            "eb_amr_setup", "eb_amr_query", "eb_amr_residual", "eb_amr_solve", "eb_amr_kernel_stats",
-           "eb_amr_destroy", "eb_device_fma_rates", "eb_tga_coefficients", "eb_tga_create",
+           "eb_amr_destroy", "eb_amr_setup_levels", "eb_amr_level_query", "eb_amr_level_geom",
+           "eb_amr_residual_levels", "eb_amr_solve_levels", "eb_amr_field_eval", "eb_tag_cells", "eb_regrid_box",
+           "eb_device_fma_rates", "eb_tga_coefficients", "eb_tga_create",
            "eb_tga_step", "eb_tga_destroy"]
 
 
@@ -154,6 +156,29 @@ def load(build_if_missing: bool = False):
         lib.eb_amr_destroy.argtypes = [P]
         lib.eb_amr_kernel_stats.restype = C.c_int
         lib.eb_amr_kernel_stats.argtypes = [P, C.POINTER(C.c_double)]
+        lib.eb_amr_setup_levels.restype = C.c_int
+        lib.eb_amr_setup_levels.argtypes = [C.POINTER(GeomDesc), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                            C.POINTER(SolverOpts), P, C.POINTER(P)]
+        lib.eb_amr_level_query.restype = C.c_int
+        lib.eb_amr_level_query.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                                           C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                           C.POINTER(C.c_longlong)]
+        lib.eb_amr_level_geom.restype = C.c_int
+        lib.eb_amr_level_geom.argtypes = [P, C.c_int, C.POINTER(P)]
+        lib.eb_amr_residual_levels.restype = C.c_int
+        lib.eb_amr_residual_levels.argtypes = [P, P, P, P, P, P]
+        lib.eb_amr_solve_levels.restype = C.c_int
+        lib.eb_amr_solve_levels.argtypes = [P, P, P, P, C.POINTER(SolveInfo), P]
+        lib.eb_amr_field_eval.restype = C.c_int
+        lib.eb_amr_field_eval.argtypes = [P, C.c_int, P, P, P, P, P]
+        lib.eb_tag_cells.restype = C.c_int
+        lib.eb_tag_cells.argtypes = [P, P, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int), P,
+                                     C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                                     C.POINTER(C.c_double), P]
+        lib.eb_regrid_box.restype = C.c_int
+        lib.eb_regrid_box.argtypes = [C.c_int] + [C.POINTER(C.c_int)] * 5 + [C.c_longlong, C.c_int, C.c_int,
+                                                                            C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                                                            C.POINTER(C.c_int)]
         lib.eb_device_fma_rates.restype = C.c_int
         lib.eb_device_fma_rates.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         lib.eb_tga_coefficients.restype = C.c_int
@@ -643,6 +668,144 @@ class Composite:
             self.close()
         except Exception:
             pass
+
+
+class Hierarchy:
+    """Composite grid of nested ratio-2 boxes, one per level (owns an eb_amr).
+
+    boxes: [(lo, hi), ...] for levels 1.., each over cells of its parent level's grid counted from
+    that grid's lower corner."""
+
+    def __init__(self, desc: dict, boxes, *, precision="mixed", tol=1e-10, max_cycles=100, nu1=-1, nu2=-1,
+                 inner_cycles=2, device=None, stream=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.desc = desc
+        self.dim = int(desc["dim"])
+        d, keep = make_desc(desc)
+        o = eb_solver_opts_default()
+        o.tol, o.max_cycles, o.nu1, o.nu2 = tol, max_cycles, nu1, nu2
+        o.precision = EB_PREC_MIXED if precision == "mixed" else EB_PREC_FP64
+        o.inner_cycles = inner_cycles
+        self.boxes = [([int(v) for v in (list(lo) + [0] * 3)[:3]], [int(v) for v in (list(hi) + [1] * 3)[:3]])
+                      for lo, hi in boxes]
+        nb_ = len(self.boxes)
+        lo = (C.c_int * (3 * max(nb_, 1)))(*[v for b in self.boxes for v in b[0]])
+        hi = (C.c_int * (3 * max(nb_, 1)))(*[v for b in self.boxes for v in b[1]])
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(load().eb_amr_setup_levels(C.byref(d), nb_ + 1, lo, hi, C.byref(o), _stream(stream),
+                                              C.byref(h)), "eb_amr_setup_levels")
+        self._h = h
+        self.levels = []
+        for l in range(nb_ + 1):
+            nl, nc, faces = C.c_int(), C.c_longlong(), C.c_longlong()
+            n3, lo3, hh = (C.c_int * 3)(), (C.c_double * 3)(), C.c_double()
+            _check(load().eb_amr_level_query(h, l, C.byref(nl), C.byref(nc), n3, lo3, C.byref(hh), C.byref(faces)),
+                   "eb_amr_level_query")
+            self.levels.append(dict(n_cells=nc.value, n=tuple(n3), lo=tuple(lo3), h=hh.value, cf_faces=faces.value))
+        self.L = nb_ + 1
+
+    def level_desc(self, l):
+        """The level's grid as a description (for cell centres)."""
+        out = dict(self.desc)
+        out.update(n=self.levels[l]["n"], lo=self.levels[l]["lo"], h=self.levels[l]["h"])
+        return out
+
+    def level_geom(self, l):
+        g = C.c_void_p()
+        _check(load().eb_amr_level_geom(self._h, l, C.byref(g)), "eb_amr_level_geom")
+        return g
+
+    def _f(self, x, l):
+        n = self.levels[l]["n_cells"]
+        if x is None:
+            return None
+        x = _dev(x, torch.float64, self.device)
+        return x.reshape(2, n).contiguous()
+
+    @staticmethod
+    def _arr(ts):
+        return (C.c_void_p * len(ts))(*[(t.data_ptr() if t is not None else 0) for t in ts])
+
+    def residual(self, rhs, sig, phi, stream=None):
+        L = self.L
+        ins = [[self._f(v[l] if v is not None else None, l) for l in range(L)] for v in (rhs, sig, phi)]
+        r = [torch.empty(2, self.levels[l]["n_cells"], dtype=torch.float64, device=self.device) for l in range(L)]
+        _check(load().eb_amr_residual_levels(self._h, C.cast(self._arr(ins[0]), C.c_void_p),
+                                             C.cast(self._arr(ins[1]), C.c_void_p),
+                                             C.cast(self._arr(ins[2]), C.c_void_p), C.cast(self._arr(r), C.c_void_p),
+                                             _stream(stream)), "eb_amr_residual_levels")
+        return r
+
+    def solve(self, rhs, sig=None, phi=None, stream=None):
+        L = self.L
+        rs = [self._f(rhs[l], l) for l in range(L)]
+        ss = [self._f(sig[l] if sig is not None else None, l) for l in range(L)]
+        ps = [torch.zeros(2, self.levels[l]["n_cells"], dtype=torch.float64, device=self.device) if phi is None
+              else self._f(phi[l], l).clone() for l in range(L)]
+        info = SolveInfo()
+        st = load().eb_amr_solve_levels(self._h, C.cast(self._arr(rs), C.c_void_p), C.cast(self._arr(ss), C.c_void_p),
+                                        C.cast(self._arr(ps), C.c_void_p), C.byref(info), _stream(stream))
+        if st not in (EB_OK, EB_ERR_NOT_CONVERGED):
+            _check(st, "eb_amr_solve_levels")
+        return ps, _info_dict(info)
+
+    def field(self, l, phi, sigma=None, stream=None):
+        """E [D][2][n] on level l's grid (and the EB normal field)."""
+        n = self.levels[l]["n_cells"]
+        lev_geom = self.level_geom(l)
+        gi = GeomInfo()
+        _check(load().eb_geom_query(lev_geom, C.byref(gi)), "eb_geom_query")
+        E = torch.empty(self.dim, 2, n, dtype=torch.float64, device=self.device)
+        En = torch.empty(max(int(gi.n_eb), 1), 2, dtype=torch.float64, device=self.device)
+        ph = self._f(phi, l)
+        sg = self._f(sigma, l) if sigma is not None else None
+        _check(load().eb_amr_field_eval(self._h, l, _ptr(ph), _ptr(sg), _ptr(E), _ptr(En), _stream(stream)),
+               "eb_amr_field_eval")
+        return E, En
+
+    def kernel_stats(self):
+        out = (C.c_double * 8)()
+        _check(load().eb_amr_kernel_stats(self._h, out), "eb_amr_kernel_stats")
+        keys = ("launches", "kernel_ms", "vcycles", "outer")
+        return {w: {k: out[4 * i + j] for j, k in enumerate(keys)} for i, w in enumerate(("coarse", "fine"))}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().eb_amr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tag_cells(geom_handle, E, eps=(0.1, 0.8, 0.1, 0.2), keep=None, want_tags=True, stream=None):
+    """Refinement tags of one grid (a Geometry's handle or Hierarchy.level_geom(l)).
+    Returns (tags uint8 tensor or None, bbox_lo, bbox_hi, n_marked, e_max)."""
+    h = geom_handle._h if isinstance(geom_handle, Geometry) else geom_handle
+    ep = (C.c_double * 4)(*[float(v) for v in eps])
+    klo = khi = None
+    if keep is not None:
+        klo = (C.c_int * 3)(*[int(v) for v in (list(keep[0]) + [0] * 3)[:3]])
+        khi = (C.c_int * 3)(*[int(v) for v in (list(keep[1]) + [1] * 3)[:3]])
+    tags = torch.empty(E.shape[-1], dtype=torch.uint8, device=E.device) if want_tags else None
+    blo, bhi = (C.c_int * 3)(), (C.c_int * 3)()
+    nm, em = C.c_longlong(), C.c_double()
+    _check(load().eb_tag_cells(h, _ptr(E.contiguous()), ep, klo, khi, _ptr(tags), blo, bhi, C.byref(nm), C.byref(em),
+                               _stream(stream)), "eb_tag_cells")
+    return tags, list(blo), list(bhi), nm.value, em.value
+
+
+def regrid_box(dim, n, cf_lo, cf_hi, bbox_lo, bbox_hi, n_marked, buf=2, block=4):
+    """The next finer box from a tag bounding box, or None (host arithmetic in the library)."""
+    i3 = lambda v, f: (C.c_int * 3)(*[int(x) for x in (list(v) + [f] * 3)[:3]])  # noqa: E731
+    lo, hi, has = (C.c_int * 3)(), (C.c_int * 3)(), C.c_int()
+    _check(load().eb_regrid_box(int(dim), i3(n, 1), i3(cf_lo, 0), i3(cf_hi, 0), i3(bbox_lo, 0), i3(bbox_hi, 0),
+                                int(n_marked), int(buf), int(block), lo, hi, C.byref(has)), "eb_regrid_box")
+    return (list(lo)[:dim], list(hi)[:dim]) if has.value else None
 
 
 class TGA:
