@@ -33,6 +33,8 @@ Usage: python -m paper_1809_03745_gb300.bench_configs [--only C1 C2 C3 C4]
        python -m paper_1809_03745_gb300.bench_configs --peaks   (measured FP64 / FP32 FMA rates)
        python -m paper_1809_03745_gb300.bench_configs --composite 256
        python -m paper_1809_03745_gb300.bench_configs --regrid 128
+       python -m paper_1809_03745_gb300.bench_configs --tags 192 [--reps 20]
+       python -m paper_1809_03745_gb300.bench_configs --bottom-ab 256   (bottom sweeps 64, 32, 24, 16)
        python -m paper_1809_03745_gb300.bench_configs --kernels 384 [--reps 20]
 """
 from __future__ import annotations
@@ -173,6 +175,19 @@ def composite_once(n):
                       "kernel_launches": info["kernel_launches"], "kernel_stats": G.kernel_stats()}), flush=True)
 
 
+def composite_bottom_ab(n, sweeps):
+    """The C3 composite solve at n^3 + (n/2)^3 with each bottom sweep count (set-up, one warm-up, best of 2)."""
+    d, lo, hi, Sc, sc, Sf, sf = W.c3_amr_inputs(n)
+    args = [torch.from_numpy(a).cuda() for a in (Sc, Sf, sc, sf)]
+    for bs in sweeps:
+        G = E.Composite(d, lo, hi, precision="mixed", tol=1e-10, max_cycles=200, bottom_sweeps=bs)
+        dt, (_, _, info) = _timed(lambda: G.solve(*args), reps=2)
+        print(json.dumps({"workload": f"C3 composite {n}^3 + {n // 2}^3 box", "bottom_sweeps": bs, "ms": dt * 1e3,
+                          "outer_iters": info["outer_iters"], "vcycles": info["vcycles"], "rel_res": info["rel_res"],
+                          "status": info["status"], "kernel_stats": G.kernel_stats()}), flush=True)
+        G.close()
+
+
 def kernels_once(n, reps):
     """The large-grid kernels of the n^3 pin-plane finest level, each launched
     on its own (eb_poisson_profile kernels 4, 0, 5, 1)."""
@@ -228,6 +243,29 @@ def regrid_once(n, dim):
     print(json.dumps(rec), flush=True)
 
 
+def tags_once(n, reps):
+    """The tagging kernels on the N^3 pin-plane's single-level field, `reps` launches."""
+    desc = W.pin_plane_3d(n)
+    x, y, z = W.cell_centres(desc)
+    S = np.zeros((2, x.size))
+    S[0] = W.line_charge(x, y, z, 1e3)
+    g = E.Geometry(desc)
+    P = E.Poisson(g, precision="mixed", tol=1e-10, max_cycles=400)
+    phi, _ = P.solve(torch.from_numpy(S))
+    Ef = P.field(phi)[0]
+    E.tag_cells(g, Ef)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        _, blo, bhi, nm, emax = E.tag_cells(g, Ef)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t) / reps * 1e3
+    by = (3 * 2 * 8 + 1 + 1) * g.ncell
+    print(json.dumps({"workload": f"tags of the {n}^3 pin-plane field", "cells": g.ncell, "ms_per_call": ms,
+                      "bytes_model": "per cell: E read once (3 x 2 x 8 B), flags 1 B, tag 1 B",
+                      "gbs": by / ms / 1e6, "n_marked": nm, "bbox": [blo, bhi]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", nargs="+", default=["C1", "C2", "C3", "C4"])
@@ -240,10 +278,18 @@ def main():
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--regrid", type=int, default=None)
     ap.add_argument("--regrid2d", type=int, default=None)
+    ap.add_argument("--tags", type=int, default=None)
+    ap.add_argument("--bottom-ab", type=int, default=None)
     args = ap.parse_args()
     E.load()
     if args.composite:
         composite_once(args.composite)
+        return
+    if args.bottom_ab:
+        composite_bottom_ab(args.bottom_ab, (64, 32, 24, 16))
+        return
+    if args.tags:
+        tags_once(args.tags, args.reps)
         return
     if args.regrid or args.regrid2d:
         regrid_once(args.regrid or args.regrid2d, 3 if args.regrid else 2)

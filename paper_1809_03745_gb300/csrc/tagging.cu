@@ -3,15 +3,19 @@
 //
 // The tracer is T = |E| / max |E|; a cell is tagged for refinement when
 // |grad T| dx / T > eps1 or T > eps2 and for coarsening when
-// |grad T| dx / T < eps3 and T < eps4.  Two passes over the grid: the first
-// takes max |E| (order-free atomicMax on the bit pattern of a non-negative
-// double), the second forms T at the cell and its axis neighbours, the
-// gradient by centred or one-sided differences in index units (dx cancels),
-// the tag byte, and the bounding box and count of the marked cells (warp
-// reductions, then one atomic per warp).  Every product and sum is written
-// with round-to-nearest intrinsics (this unit is also compiled without FMA
-// contraction) and sqrt and division are correctly rounded, so the tags are
-// a function of E alone and match a plain FP64 evaluation in the same order.
+// |grad T| dx / T < eps3 and T < eps4.  Three passes over the grid: the first
+// writes |E| per cell into a scratch array and takes its maximum (order-free
+// atomicMax on the bit pattern of a non-negative double), the second divides
+// by the maximum in place, the third reads T at the cell and its axis
+// neighbours, forms the gradient by centred or one-sided differences in
+// index units (dx cancels), the tag byte, and the bounding box and count of
+// the marked cells (warp reductions, then one atomic per warp).  FP64 is slow
+// on this part, so every square root and division is taken once per cell
+// (reading the neighbours' T instead of recomputing them costs 8 bytes each,
+// mostly from L1).  Every product and sum is written with round-to-nearest
+// intrinsics (this unit is also compiled without FMA contraction) and sqrt
+// and division are correctly rounded, so the tags are a function of E alone
+// and match a plain FP64 evaluation in the same order.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -47,6 +51,7 @@ __device__ __forceinline__ double cell_mag(const TagView& v, long long c) {
   const unsigned f = v.flags[c];
   double mag = 0.0;
   for (int p = 0; p < 2; ++p) {
+    if (!((f >> p) & 1u)) continue;  // a phase without an unknown is never selected: skip its reads
     const double e0 = v.E[(long long)p * v.ncell + c];
     double m2 = __dmul_rn(e0, e0);
     for (int a = 1; a < v.D; ++a) {
@@ -54,23 +59,33 @@ __device__ __forceinline__ double cell_mag(const TagView& v, long long c) {
       m2 = __dadd_rn(m2, __dmul_rn(e, e));
     }
     const double m = sqrt(m2);
-    if (((f >> p) & 1u) && m > mag) mag = m;
+    if (m > mag) mag = m;
   }
   return mag;
 }
 
-__global__ void k_emax(TagView v, TagOut* out) {
+__global__ void k_emag(TagView v, double* T, TagOut* out) {
   double m = 0.0;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < v.ncell;
-       c += (long long)gridDim.x * blockDim.x)
-    m = fmax(m, cell_mag(v, c));
+       c += (long long)gridDim.x * blockDim.x) {
+    const double mc = cell_mag(v, c);
+    T[c] = mc;
+    m = fmax(m, mc);
+  }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(&out->emax, (unsigned long long)__double_as_longlong(m));
 }
 
-__global__ void k_tag(TagView v, double eps1, double eps2, double eps3, double eps4, int keep, int klo0, int klo1,
-                      int klo2, int khi0, int khi1, int khi2, uint8_t* tags, TagOut* out) {
+__global__ void k_tnorm(long long n, double* T, const TagOut* out) {
   const double emax = __longlong_as_double((long long)out->emax);
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+    T[c] = emax > 0.0 ? T[c] / emax : 0.0;
+}
+
+template <int D>
+__global__ void k_tag(TagView v, const double* __restrict__ Tt, double eps1, double eps2, double eps3, double eps4,
+                      int keep, int klo0, int klo1, int klo2, int khi0, int khi1, int khi2, uint8_t* tags,
+                      TagOut* out) {
   const int klo[3] = {klo0, klo1, klo2}, khi[3] = {khi0, khi1, khi2};
   int mlo[3] = {INT_MAX, INT_MAX, INT_MAX}, mhi[3] = {-1, -1, -1};
   unsigned cnt = 0;
@@ -81,13 +96,14 @@ __global__ void k_tag(TagView v, double eps1, double eps2, double eps3, double e
     const int I[3] = {(int)(c - (long long)r * v.n[0]), (int)(r % (unsigned)v.n[1]), (int)(r / (unsigned)v.n[1])};
     uint8_t t = 0;
     if (v.flags[c] & 3u) {
-      const double T = emax > 0.0 ? cell_mag(v, c) / emax : 0.0;
+      const double T = Tt[c];
       double s2 = 0.0;
-      for (int a = 0; a < v.D; ++a) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
         const bool hp = I[a] + 1 < v.n[a] && (v.flags[c + stride[a]] & 3u);
         const bool hm = I[a] > 0 && (v.flags[c - stride[a]] & 3u);
-        const double Tp = hp ? (emax > 0.0 ? cell_mag(v, c + stride[a]) / emax : 0.0) : 0.0;
-        const double Tm = hm ? (emax > 0.0 ? cell_mag(v, c - stride[a]) / emax : 0.0) : 0.0;
+        const double Tp = hp ? Tt[c + stride[a]] : 0.0;
+        const double Tm = hm ? Tt[c - stride[a]] : 0.0;
         const double d = hp && hm ? __dmul_rn(__dsub_rn(Tp, Tm), 0.5) : hp ? __dsub_rn(Tp, T)
                                                                       : hm ? __dsub_rn(T, Tm) : 0.0;
         s2 = __dadd_rn(s2, __dmul_rn(d, d));
@@ -100,10 +116,12 @@ __global__ void k_tag(TagView v, double eps1, double eps2, double eps3, double e
       bool marked = refine;
       if (!marked && keep && !coarsen) {
         marked = true;
-        for (int a = 0; a < v.D; ++a) marked = marked && I[a] >= klo[a] && I[a] < khi[a];
+#pragma unroll
+        for (int a = 0; a < D; ++a) marked = marked && I[a] >= klo[a] && I[a] < khi[a];
       }
       if (marked) {
         ++cnt;
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
           mlo[a] = min(mlo[a], I[a]);
           mhi[a] = max(mhi[a], I[a]);
@@ -112,6 +130,7 @@ __global__ void k_tag(TagView v, double eps1, double eps2, double eps3, double e
     }
     if (tags) tags[c] = t;
   }
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     mlo[a] = __reduce_min_sync(0xffffffffu, mlo[a]);
     mhi[a] = __reduce_max_sync(0xffffffffu, mhi[a]);
@@ -119,6 +138,7 @@ __global__ void k_tag(TagView v, double eps1, double eps2, double eps3, double e
   cnt = __reduce_add_sync(0xffffffffu, cnt);
   if ((threadIdx.x & 31) == 0 && cnt) {
     atomicAdd(&out->count, (unsigned long long)cnt);
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
       atomicMin(&out->lo[a], mlo[a]);
       atomicMax(&out->hi[a], mhi[a]);
@@ -154,13 +174,18 @@ extern "C" eb_status eb_tag_cells(const eb_geom* G, const double* d_E, const dou
     init.lo[a] = INT_MAX;
     init.hi[a] = -1;
   }
-  TagOut* d_out = nullptr;
-  cudaError_t e = cudaMalloc(&d_out, sizeof(TagOut));
+  // one allocation: the result words, then T [ncell] (16-byte aligned)
+  const size_t head = (sizeof(TagOut) + 255) / 256 * 256;
+  char* d_buf = nullptr;
+  cudaError_t e = cudaMalloc(&d_buf, head + sizeof(double) * (size_t)v.ncell);
   if (e != cudaSuccess) return cuda_fail(e, "tag scratch");
+  TagOut* d_out = (TagOut*)d_buf;
+  double* d_T = (double*)(d_buf + head);
   e = cudaMemcpyAsync(d_out, &init, sizeof(init), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
-    k_emax<<<nbt(v.ncell), TBT, 0, s>>>(v, d_out);
-    note_launch();
+    k_emag<<<nbt(v.ncell), TBT, 0, s>>>(v, d_T, d_out);
+    k_tnorm<<<nbt(v.ncell), TBT, 0, s>>>(v.ncell, d_T, d_out);
+    note_launch(2);
     const int keep = keep_lo ? 1 : 0;
     int klo[3] = {0, 0, 0}, khi[3] = {0, 0, 0};
     if (keep)
@@ -168,15 +193,19 @@ extern "C" eb_status eb_tag_cells(const eb_geom* G, const double* d_E, const dou
         klo[a] = keep_lo[a];
         khi[a] = keep_hi[a];
       }
-    k_tag<<<nbt(v.ncell), TBT, 0, s>>>(v, eps[0], eps[1], eps[2], eps[3], keep, klo[0], klo[1], klo[2], khi[0],
-                                       khi[1], khi[2], d_tags, d_out);
+    if (v.D == 2)
+      k_tag<2><<<nbt(v.ncell), TBT, 0, s>>>(v, d_T, eps[0], eps[1], eps[2], eps[3], keep, klo[0], klo[1], klo[2],
+                                            khi[0], khi[1], khi[2], d_tags, d_out);
+    else
+      k_tag<3><<<nbt(v.ncell), TBT, 0, s>>>(v, d_T, eps[0], eps[1], eps[2], eps[3], keep, klo[0], klo[1], klo[2],
+                                            khi[0], khi[1], khi[2], d_tags, d_out);
     note_launch();
     e = cudaGetLastError();
   }
   TagOut res;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&res, d_out, sizeof(res), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(d_out);
+  cudaFree(d_buf);
   if (e != cudaSuccess) return cuda_fail(e, "refinement tags");
   *n_marked = (long long)res.count;
   for (int a = 0; a < 3; ++a) {

@@ -601,13 +601,13 @@ class Composite:
     """Composite grid: one ratio-2 refined box over coarse cells [box_lo, box_hi) (owns an eb_amr)."""
 
     def __init__(self, desc: dict, box_lo, box_hi, *, precision="mixed", tol=1e-10, max_cycles=100, nu1=-1, nu2=-1,
-                 inner_cycles=2, device=None, stream=None):
+                 inner_cycles=2, bottom_sweeps=64, device=None, stream=None):
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         d, keep = make_desc(desc)
         o = eb_solver_opts_default()
         o.tol, o.max_cycles, o.nu1, o.nu2 = tol, max_cycles, nu1, nu2
         o.precision = EB_PREC_MIXED if precision == "mixed" else EB_PREC_FP64
-        o.inner_cycles = inner_cycles
+        o.inner_cycles, o.bottom_sweeps = inner_cycles, bottom_sweeps
         lo = (C.c_int * 3)(*[int(v) for v in (list(box_lo) + [0] * 3)[:3]])
         hi = (C.c_int * 3)(*[int(v) for v in (list(box_hi) + [1] * 3)[:3]])
         h = C.c_void_p()

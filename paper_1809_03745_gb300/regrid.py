@@ -4,7 +4,10 @@ Level by level: solve on the current hierarchy (level 0 alone at first),
 evaluate E = -grad phi on the finest level, tag its cells (eb_tag_cells: the
 tracer T = |E| / max |E|, refine where |grad T| dx / T > eps1 or T > eps2),
 turn the marked cells' bounding box into the next box (eb_regrid_box: buffer,
-blocking factor, proper nesting) and rebuild the composite grid with it.
+blocking factor, proper nesting) and rebuild the composite grid with it.  The
+composite grid lets only the gas phase touch a coarse-fine side; when a box
+would cut through a dielectric, its coarse-fine sides move outward by the
+blocking factor until the set-up accepts it (or the box reaches the grid).
 Every step runs in the library; this module only sequences the calls.
 """
 from __future__ import annotations
@@ -33,6 +36,36 @@ def cf_sides(boxes, parent_n, D):
     lo, hi = boxes[-1]
     return ([int(lo[a] > 0) if a < D else 0 for a in range(3)],
             [int(hi[a] < parent_n[a]) if a < D else 0 for a in range(3)])
+
+
+def _grow(box, n, cflo, cfhi, D, block):
+    """The box with every side that is not at its limit moved out by `block` cells (None if none can)."""
+    lo, hi = list(box[0]), list(box[1])
+    moved = False
+    for a in range(D):
+        lmin = block if cflo[a] else 0
+        hmax = n[a] - block if cfhi[a] else n[a]
+        if lo[a] > lmin:
+            lo[a] = max(lmin, lo[a] - block)
+            moved = True
+        if hi[a] < hmax:
+            hi[a] = min(hmax, hi[a] + block)
+            moved = True
+    return (lo, hi) if moved else None
+
+
+def _hierarchy(desc, boxes, n, cflo, cfhi, D, block, **kw):
+    """Set up the composite grid, growing the newest box while a dielectric cuts its CF sides."""
+    while True:
+        try:
+            return E.Hierarchy(desc, boxes, **kw), boxes
+        except E.EBError as exc:
+            if exc.status != E.EB_ERR_UNSUPPORTED:
+                raise
+            grown = _grow(boxes[-1], n, cflo, cfhi, D, block)
+            if grown is None:
+                raise
+            boxes = boxes[:-1] + [grown]
 
 
 def build_hierarchy(desc, source, *, max_levels=3, eps=PAPER_EPS, buf=2, block=4, keep=None, precision="mixed",
@@ -64,15 +97,16 @@ def build_hierarchy(desc, source, *, max_levels=3, eps=PAPER_EPS, buf=2, block=4
         steps.append(dict(level=len(boxes), n_marked=nm, bbox=(blo[:D], bhi[:D]), e_max=emax, box=box))
         if box is None or len(boxes) + 1 >= max_levels:
             break
-        boxes.append(box)
         if H is not None:
             H.close()
-        H = E.Hierarchy(desc, boxes, precision=precision, tol=tol, device=dev)
+        H, boxes = _hierarchy(desc, boxes + [box], n_here, cflo, cfhi, D, block, precision=precision, tol=tol,
+                              device=dev)
+        steps[-1]["box"] = boxes[-1]
         S = [level_sources(H.level_desc(l), source) for l in range(H.L)]
         phis, info = H.solve([torch.from_numpy(s) for s in S])
         Ef = H.field(H.L - 1, phis[-1])[0]
         # the earlier finer box is kept only while the grid it sits on is unchanged
         k = len(boxes)
-        keep_box = keep[k] if keep and len(keep) > k and [list(b) for b in keep[k - 1]] == [list(b) for b in box] \
-            else None
+        same_grid = keep and len(keep) > k and [list(b) for b in keep[k - 1]] == [list(b) for b in boxes[-1]]
+        keep_box = keep[k] if same_grid else None
     return dict(hierarchy=H, boxes=boxes, phis=phis, info=info, steps=steps)

@@ -61,3 +61,11 @@ def test_setup_levels_refuses_bad_boxes_before_device_work():
     assert setup([([8, 8, 0], [22, 24, 1])]) == E.EB_ERR_INVALID
     # too many levels
     assert setup([([8, 8, 0], [24, 24, 1])] * 4) == E.EB_ERR_INVALID
+
+
+def test_regrid_driver_grows_boxes_to_their_limits():
+    from paper_1809_03745_gb300 import regrid as R
+    # CF sides in x (limits 4 and n - 4), domain sides in y (limits 0 and n)
+    box = ([8, 2], [20, 30])
+    assert R._grow(box, [32, 32], [1, 0], [1, 0], 2, 4) == ([4, 0], [24, 32])
+    assert R._grow(([4, 0], [28, 32]), [32, 32], [1, 0], [1, 0], 2, 4) is None
