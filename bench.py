@@ -244,7 +244,8 @@ def kernels_at_scale(dev, E, W, n=384):
 
 def extra_configs(dev, E, W, with_oracle):
     """The 2D 1024^2 multi-material solve (with its phi error against the
-    oracle's direct solution) and the 64-instance batched launch."""
+    oracle's direct solution), the 64-instance batched launch, and the 128^3
+    pin-plane refined to three levels by the regrid tags."""
     import torch
     out = {}
     d, S, sig = W.c2_inputs(C2_SIDE)
@@ -289,6 +290,34 @@ def extra_configs(dev, E, W, with_oracle):
                             "statuses": sorted(set(i["status"] for i in infos))}
     del Pb
     torch.cuda.empty_cache()
+    try:  # nested levels placed by the Sec. 6 tracer criteria on the 128^3 pin-plane (reported, never required)
+        from paper_1809_03745_gb300 import regrid as R
+        src = lambda x, y, z: W.line_charge(x, y, z, 1e3)  # noqa: E731
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rg = R.build_hierarchy(W.pin_plane_3d(128), src, max_levels=3, precision="mixed", tol=1e-10, device=dev)
+        torch.cuda.synchronize()
+        t_regrid = time.perf_counter() - t0
+        H = rg["hierarchy"]
+        Sl = [torch.from_numpy(R.level_sources(H.level_desc(l), src)).to(dev) for l in range(H.L)]
+        H.solve(Sl)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, hi = H.solve(Sl)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        cells = [H.levels[l]["n_cells"] for l in range(H.L)]
+        own = sum(cells) - sum(int(np.prod([b - a for a, b in zip(*bx)])) for bx in rg["boxes"])
+        out["regrid_pinplane_128_3levels"] = {
+            "workload": "3D pin-plane 128^3 base refined twice by the Sec. 6 tracer criteria (0.1/0.8/0.1/0.2), "
+                        "mixed, tol 1e-10", "boxes": rg["boxes"], "level_cells": cells, "composite_cells": own,
+            "regrid_s": t_regrid, "solve_ms": dt * 1e3, "cells_per_s": own / dt, "fgmres_iters": hi["outer_iters"],
+            "vcycles": hi["vcycles"], "rel_res": hi["rel_res"], "status": hi["status"]}
+        H.close()
+        del rg, H, Sl
+        torch.cuda.empty_cache()
+    except Exception as exc:
+        out["regrid_pinplane_128_3levels"] = f"failed: {exc}"
     return out
 
 
@@ -459,7 +488,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scale", action="store_true", help="skip the large-grid kernel measurement")
-    ap.add_argument("--no-extra", action="store_true", help="skip the 1024^2 and batched configurations")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 1024^2, batched and regrid configurations")
     ap.add_argument("--scale-n", type=int, default=384, help="cells per side of the large-grid measurement")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -401,7 +401,8 @@ eb_status eb_amr_residual(eb_amr* A, const double* d_rhs_c, const double* d_sig_
  * by one FAC step: a coarse correction over the domain (fine part averaged
  * under the box), constant per parent on the fine grid, then a fine
  * correction on the box with zero Dirichlet data on its CF sides, each one V-cycle
- * of the persistent multigrid solve.  d_phi_c / d_phi_f hold the guess on
+ * of the persistent multigrid solve (3+3 sweeps, a relaxed bottom at most 32
+ * sweeps).  d_phi_c / d_phi_f hold the guess on
  * entry; on return d_phi_c under the box holds the fine means.  info:
  * outer_iters = FGMRES iterations, vcycles = V-cycles of the corrections.
  * The work space (27 composite vectors) is allocated at the first call. */

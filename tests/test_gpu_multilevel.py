@@ -1,8 +1,9 @@
 """Nested refined levels and regrid tags on the GPU against the oracle.
 
 - the composite residual over three levels equals the oracle's multi-level
-  operator (2D rod crossing both boxes' CF sides; 3D pin through both boxes);
-- the three-level solve equals the oracle's direct solution (FP64 and mixed);
+  operator (2D rod crossing both boxes' CF sides; 3D pin through both boxes),
+  and over four levels (2D, the rod crossing all three boxes);
+- those solves equal the oracle's direct solution (FP64 and mixed);
 - two levels through the nested-level calls equal the two-level calls bitwise;
 - the tags of eb_tag_cells equal the oracle's bit for bit on the same E
   (2D and 3D, with and without a kept box), and so do the marked count, the
@@ -37,6 +38,8 @@ def _src3(x, y, z):
 def _case(name):
     if name == "rod2d":
         return W.rod_plane_2d(32), [([8, 8], [24, 24]), ([8, 8], [24, 24])], _src2
+    if name == "rod2d_4lev":
+        return W.rod_plane_2d(32), [([8, 8], [24, 24])] * 3, _src2
     return W.pin_plane_3d(16, radius=0.1, disk=False), [([4, 4, 4], [12, 12, 12]), ([4, 4, 4], [12, 12, 12])], _src3
 
 
@@ -50,7 +53,7 @@ def _sources(grids, src):
     return out
 
 
-CASES = ["rod2d", "pin3d"]
+CASES = ["rod2d", "pin3d", "rod2d_4lev"]
 
 
 @pytest.fixture(scope="module")
@@ -66,11 +69,11 @@ def oracles():
 
 
 @pytest.mark.parametrize("name", CASES)
-def test_three_level_residual_parity(name, oracles):
+def test_nested_level_residual_parity(name, oracles):
     d, boxes, _ = _case(name)
     M, S, A, b, _ = oracles[name]
     H = E.Hierarchy(d, boxes, precision="fp64")
-    assert H.L == 3 and [H.levels[l]["n_cells"] for l in range(3)] == [g.ncell for g in M.g]
+    assert H.L == len(boxes) + 1 and [H.levels[l]["n_cells"] for l in range(H.L)] == [g.ncell for g in M.g]
     x = np.random.default_rng(5).normal(size=M.n)
     phis = M.split(x)
     r = [t.cpu().numpy() for t in H.residual(S, None, phis)]
@@ -87,7 +90,7 @@ def test_three_level_residual_parity(name, oracles):
 
 @pytest.mark.parametrize("name", CASES)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_three_level_solve_parity(name, precision, oracles):
+def test_nested_level_solve_parity(name, precision, oracles):
     d, boxes, _ = _case(name)
     M, S, A, b, xo = oracles[name]
     H = E.Hierarchy(d, boxes, precision=precision, tol=1e-12, max_cycles=200)
