@@ -136,3 +136,12 @@ def test_planted_inner_pair_spacing_breaks_exactness(monkeypatch):
     M.h[2] = M.h[1]
     rel, *_ = _truncation(M, _quad2, 2 * (C2[3] + C2[4]))
     assert rel > 1e-6
+
+
+def test_four_levels_quadratic_exactness_and_conservation_2d():
+    M = MultiLevel(_sphere_2d(), [([12, 12], [28, 28]), ([4, 8], [28, 24]), ([8, 8], [40, 24])])
+    assert M.L == 4 and all(len(P.faces) > 0 for P in M.pairs)
+    rel, A, b, x = _truncation(M, _quad2, 2 * (C2[3] + C2[4]))
+    assert rel <= 1e-12
+    d = W.rod_plane_2d(32)
+    assert _conservation_gap(MultiLevel(d, [([8, 8], [24, 24])] * 3)) <= 1e-12
