@@ -44,6 +44,10 @@ struct BoxIdx {
   int D;
   int nc[3], nf[3], lo[3], hi[3];
 };
+// coarse cells under the box: the launch size of the passes that touch only them
+long long box_cells(const BoxIdx& B) {
+  return (long long)(B.hi[0] - B.lo[0]) * (B.hi[1] - B.lo[1]) * (B.hi[2] - B.lo[2]);
+}
 
 // cell indices of linear index c (grids of fewer than 2^32 cells: 32-bit
 // divisions, several times cheaper than 64-bit ones in these memory-bound
@@ -64,15 +68,25 @@ __device__ __forceinline__ bool under_box(const BoxIdx& B, const int I[3]) {
     if (I[k] < B.lo[k] || I[k] >= B.hi[k]) return false;
   return true;
 }
+// the t-th coarse cell under the box (x fastest); false past the last one.
+// Passes that only touch the cells under the box launch over these alone.
+__device__ __forceinline__ bool box_cell(const BoxIdx& B, long long t, int I[3]) {
+  const unsigned e0 = (unsigned)(B.hi[0] - B.lo[0]), e1 = (unsigned)(B.hi[1] - B.lo[1]);
+  const unsigned e2 = (unsigned)(B.hi[2] - B.lo[2]);
+  if (t >= (long long)e0 * e1 * e2) return false;
+  const unsigned tu = (unsigned)t, r = tu / e0;
+  I[0] = B.lo[0] + (int)(tu - r * e0);
+  I[1] = B.lo[1] + (int)(r % e1);
+  I[2] = B.lo[2] + (int)(r / e1);
+  return true;
+}
 
 // coarse values under the box: kappa-weighted mean of the children with the phase
 __global__ void k_avg_down(BoxIdx B, const uint8_t* cflags, const uint8_t* fflags, const double* kf, const double* pf,
                            double* pc, long long ncc, long long nff) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncc) return;
   int I[3];
-  ijk3(B.nc, c, I);
-  if (!under_box(B, I)) return;
+  if (!box_cell(B, (long long)blockIdx.x * blockDim.x + threadIdx.x, I)) return;
+  const long long c = lin3(B.nc, I);
   for (int p = 0; p < 2; ++p) {
     if (!((cflags[c] >> p) & 1)) {
       pc[p * ncc + c] = 0.0;
@@ -138,22 +152,19 @@ __global__ void k_cf_coarse_apply(const CFCoarse* cf, long long n, const double*
 }
 
 __global__ void k_zero_under(BoxIdx B, double* rc, long long ncc) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncc) return;
   int I[3];
-  ijk3(B.nc, c, I);
-  if (under_box(B, I)) rc[c] = rc[ncc + c] = 0.0;
+  if (!box_cell(B, (long long)blockIdx.x * blockDim.x + threadIdx.x, I)) return;
+  const long long c = lin3(B.nc, I);
+  rc[c] = rc[ncc + c] = 0.0;
 }
 
 // coarse correction right-hand side under the box: mean fine residual of the
 // children carrying the phase
 __global__ void k_restrict_under(BoxIdx B, const uint8_t* fflags, const double* rf, double* rc, long long ncc,
                                  long long nff) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncc) return;
   int I[3];
-  ijk3(B.nc, c, I);
-  if (!under_box(B, I)) return;
+  if (!box_cell(B, (long long)blockIdx.x * blockDim.x + threadIdx.x, I)) return;
+  const long long c = lin3(B.nc, I);
   for (int p = 0; p < 2; ++p) {
     double s = 0.0;
     int m = 0;
@@ -276,20 +287,41 @@ __global__ void k_cv_mdot(BoxIdx B, const uint8_t* flags, long long n, int coars
     part[threadIdx.x * gridDim.x + blockIdx.x] = t;
   }
 }
-// w -= sum_i a_i v_i on the entries with an unknown (others 0)
-__global__ void k_cv_maxpy(const uint8_t* flags, long long n, int m, CVPtrs V, double* w) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
-  const unsigned f = flags[c];
-  for (int p = 0; p < 2; ++p) {
-    if (!((f >> p) & 1u)) {
-      w[p * n + c] = 0.0;
-      continue;
+// w -= sum_i a_i v_i on the entries with an unknown (others 0), and from the
+// same pass the per-block partial sums of the new w . w over the entries a
+// dot product counts (the caller adds the blocks in order: deterministic)
+__global__ void k_cv_maxpy_norm(BoxIdx B, const uint8_t* flags, long long n, int coarse, int m, CVPtrs V, double* w,
+                                double* part) {
+  __shared__ double sh[TBA];
+  double acc = 0.0;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    bool counted = true;
+    if (coarse) {
+      int I[3];
+      ijk3(B.nc, c, I);
+      counted = !under_box(B, I);
     }
-    double t = w[p * n + c];
-    for (int i = 0; i < m; ++i) t -= V.a[i] * V.v[i][p * n + c];
-    w[p * n + c] = t;
+    const unsigned f = flags[c];
+    for (int p = 0; p < 2; ++p) {
+      if (!((f >> p) & 1u)) {
+        w[p * n + c] = 0.0;
+        continue;
+      }
+      double t = w[p * n + c];
+#pragma unroll
+      for (int i = 0; i < CV_MAXV; ++i)
+        if (i < m) t -= V.a[i] * V.v[i][p * n + c];
+      w[p * n + c] = t;
+      if (counted) acc += t * t;
+    }
   }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+    if ((int)threadIdx.x < s2) sh[threadIdx.x] += sh[threadIdx.x + s2];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
 // y = a x + b y on the entries with an unknown
@@ -636,7 +668,8 @@ static eb_status amr_resid(eb_amr* A, const double* const* phi, cudaStream_t s) 
   for (int l = L - 2; l >= 0; --l) {
     AmrLevel &c = A->lv[l], &f = A->lv[l + 1];
     cudaMemcpyAsync(c.pc, phi[l], 2 * c.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    k_avg_down<<<nb(c.n), TBA, 0, s>>>(A->pr[l + 1].B, c.flags, f.flags, f.kap, val[l + 1], c.pc, c.n, f.n);
+    k_avg_down<<<nb(box_cells(A->pr[l + 1].B)), TBA, 0, s>>>(A->pr[l + 1].B, c.flags, f.flags, f.kap, val[l + 1],
+                                                            c.pc, c.n, f.n);
     note_launch();
     val[l] = c.pc;
   }
@@ -658,7 +691,7 @@ static eb_status amr_resid(eb_amr* A, const double* const* phi, cudaStream_t s) 
     note_launch();
   }
   for (int l = 1; l < L; ++l) {
-    k_zero_under<<<nb(A->lv[l - 1].n), TBA, 0, s>>>(A->pr[l].B, A->lv[l - 1].r, A->lv[l - 1].n);
+    k_zero_under<<<nb(box_cells(A->pr[l].B)), TBA, 0, s>>>(A->pr[l].B, A->lv[l - 1].r, A->lv[l - 1].n);
     note_launch();
   }
   cudaError_t e = cudaGetLastError();
@@ -771,17 +804,26 @@ static void cv_mdot(eb_amr* A, int m, const CVec& w, double* h, cudaStream_t s, 
     h[i] = t;
   }
 }
-// w -= sum_{i < m} h[i] V[i]
-static void cv_maxpy(eb_amr* A, int m, const double* h, const CVec& w, cudaStream_t s) {
-  for (int l = 0; l < A->L; ++l) {
+// w -= sum_{i < m} h[i] V[i], returning the new (w, w) from the same pass
+static double cv_maxpy_norm(eb_amr* A, int m, const double* h, const CVec& w, cudaStream_t s) {
+  const int L = A->L;
+  for (int l = 0; l < L; ++l) {
     CVPtrs p{};
     for (int i = 0; i < m; ++i) {
       p.v[i] = A->V[i].v[l];
       p.a[i] = h[i];
     }
-    k_cv_maxpy<<<nb(A->lv[l].n), TBA, 0, s>>>(A->lv[l].flags, A->lv[l].n, m, p, w.v[l]);
+    const AmrLevel& v = A->lv[l];
+    k_cv_maxpy_norm<<<DOT_BLOCKS, TBA, 0, s>>>(dot_box(A, l), v.flags, v.n, l < L - 1, m, p, w.v[l],
+                                               A->d_part + l * DOT_BLOCKS);
     note_launch();
   }
+  std::vector<double> hp(L * DOT_BLOCKS);
+  cudaMemcpyAsync(hp.data(), A->d_part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  double t = 0.0;
+  for (int i = 0; i < L * DOT_BLOCKS; ++i) t += hp[i];
+  return t;
 }
 
 // accuracy asked of the multigrid corrections inside one FAC step: loose
@@ -793,9 +835,10 @@ constexpr double FAC_TOL = 3e-1;
 static void restrict_down(eb_amr* A, const CVec& w, int lmin, cudaStream_t s) {
   for (int l = A->L - 2; l >= lmin; --l) {
     const AmrLevel &c = A->lv[l], &f = A->lv[l + 1];
-    k_zero_under<<<nb(c.n), TBA, 0, s>>>(A->pr[l + 1].B, w.v[l], c.n);
+    k_zero_under<<<nb(box_cells(A->pr[l + 1].B)), TBA, 0, s>>>(A->pr[l + 1].B, w.v[l], c.n);
     note_launch();
-    k_restrict_under<<<nb(c.n), TBA, 0, s>>>(A->pr[l + 1].B, f.flags, w.v[l + 1], w.v[l], c.n, f.n);
+    k_restrict_under<<<nb(box_cells(A->pr[l + 1].B)), TBA, 0, s>>>(A->pr[l + 1].B, f.flags, w.v[l + 1], w.v[l], c.n,
+                                                                   f.n);
     note_launch();
   }
 }
@@ -860,7 +903,7 @@ static eb_status op_apply(eb_amr* A, const CVec& z, const CVec& w, cudaStream_t 
     k_cv_sub<<<nb(q.n), TBA, 0, s>>>(q.flags, q.n, A->bvec.v[l], q.r, w.v[l]);
     note_launch();
     if (l < A->L - 1) {
-      k_zero_under<<<nb(q.n), TBA, 0, s>>>(A->pr[l + 1].B, w.v[l], q.n);
+      k_zero_under<<<nb(box_cells(A->pr[l + 1].B)), TBA, 0, s>>>(A->pr[l + 1].B, w.v[l], q.n);
       note_launch();
     }
   }
@@ -941,7 +984,7 @@ extern "C" eb_status eb_amr_solve_levels(eb_amr* A, const double* const* d_rhs, 
     // v0 = r / |r|_2
     cv_copy(A, res, A->V[0], s);
     for (int l = 0; l < L - 1; ++l) {
-      k_zero_under<<<nb(A->lv[l].n), TBA, 0, s>>>(A->pr[l + 1].B, A->V[0].v[l], A->lv[l].n);
+      k_zero_under<<<nb(box_cells(A->pr[l + 1].B)), TBA, 0, s>>>(A->pr[l + 1].B, A->V[0].v[l], A->lv[l].n);
       note_launch();
     }
     double beta = std::sqrt(cv_dot(A, A->V[0], A->V[0], s));
@@ -970,14 +1013,12 @@ extern "C" eb_status eb_amr_solve_levels(eb_amr* A, const double* const* d_rhs, 
       double hp[CV_MAXV];
       cv_mdot(A, k + 1, A->V[k + 1], hp, s, true);  // (V_i, w) and (w, w)
       const double w0 = std::sqrt(std::max(hp[k + 1], 0.0));
-      cv_maxpy(A, k + 1, hp, A->V[k + 1], s);
+      double w1 = std::sqrt(std::max(cv_maxpy_norm(A, k + 1, hp, A->V[k + 1], s), 0.0));
       for (int i = 0; i <= k; ++i) H[i][k] += hp[i];
-      double w1 = std::sqrt(cv_dot(A, A->V[k + 1], A->V[k + 1], s));
       if (w1 < w0 / std::sqrt(2.0)) {
         cv_mdot(A, k + 1, A->V[k + 1], hp, s);
-        cv_maxpy(A, k + 1, hp, A->V[k + 1], s);
+        w1 = std::sqrt(std::max(cv_maxpy_norm(A, k + 1, hp, A->V[k + 1], s), 0.0));
         for (int i = 0; i <= k; ++i) H[i][k] += hp[i];
-        w1 = std::sqrt(cv_dot(A, A->V[k + 1], A->V[k + 1], s));
       }
       H[k + 1][k] = w1;
       if (H[k + 1][k] > 0.0) cv_axpby(A, 0.0, A->V[k + 1], 1.0 / H[k + 1][k], A->V[k + 1], s);
@@ -1017,8 +1058,8 @@ extern "C" eb_status eb_amr_solve_levels(eb_amr* A, const double* const* d_rhs, 
   if (st == EB_OK || st == EB_ERR_NOT_CONVERGED) {
     for (int l = L - 2; l >= 0; --l) {
       const AmrLevel &c = A->lv[l], &f = A->lv[l + 1];
-      k_avg_down<<<nb(c.n), TBA, 0, s>>>(A->pr[l + 1].B, c.flags, f.flags, f.kap, d_phi[l + 1], d_phi[l], c.n,
-                                         f.n);
+      k_avg_down<<<nb(box_cells(A->pr[l + 1].B)), TBA, 0, s>>>(A->pr[l + 1].B, c.flags, f.flags, f.kap,
+                                                              d_phi[l + 1], d_phi[l], c.n, f.n);
       note_launch();
     }
     if (st == EB_ERR_NOT_CONVERGED) set_error("composite iteration cap reached");
