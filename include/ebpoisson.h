@@ -484,7 +484,8 @@ eb_status eb_amr_field_eval(eb_amr* A, int level, const double* d_phi, const dou
  * exclusive) bound the marked cells (refine-tagged or kept), *n_marked counts
  * them (0: bbox undefined) and *e_max is max |E|.  The call allocates a
  * scratch of n_cells doubles (T) for its duration and synchronises the
- * stream.  EB_ERR_INVALID for a NULL argument or an eps that is not finite. */
+ * stream.  EB_ERR_INVALID for a NULL argument, an eps that is not finite, or
+ * a current device other than the geometry's (checked before any launch). */
 eb_status eb_tag_cells(const eb_geom* G, const double* d_E, const double eps[4], const int* keep_lo,
                        const int* keep_hi, unsigned char* d_tags, int bbox_lo[3], int bbox_hi[3],
                        long long* n_marked, double* e_max, void* stream);

@@ -160,6 +160,16 @@ extern "C" eb_status eb_tag_cells(const eb_geom* G, const double* d_E, const dou
       set_error("tagging thresholds must be finite");
       return EB_ERR_INVALID;
     }
+  // the geometry's arrays live on the device it was built on: the kernels
+  // must run there
+  int dev = -1;
+  cudaError_t ed = cudaGetDevice(&dev);
+  if (ed != cudaSuccess) return cuda_fail(ed, "device query");
+  if (dev != G->device) {
+    set_error("the current device (" + std::to_string(dev) + ") is not the geometry's device (" +
+              std::to_string(G->device) + ")");
+    return EB_ERR_INVALID;
+  }
   const DevLevel& F = G->L[0];
   TagView v;
   v.D = F.g.D;

@@ -69,3 +69,18 @@ def test_regrid_driver_grows_boxes_to_their_limits():
     box = ([8, 2], [20, 30])
     assert R._grow(box, [32, 32], [1, 0], [1, 0], 2, 4) == ([4, 0], [24, 32])
     assert R._grow(([4, 0], [28, 32]), [32, 32], [1, 0], [1, 0], 2, 4) is None
+
+
+def test_tag_and_box_calls_refuse_bad_arguments_without_device_work():
+    lib = E.load(build_if_missing=True)
+    eps = (ctypes.c_double * 4)(0.1, 0.8, 0.1, 0.2)
+    lo, hi = (ctypes.c_int * 3)(), (ctypes.c_int * 3)()
+    nm, em = ctypes.c_longlong(), ctypes.c_double()
+    assert lib.eb_tag_cells(None, None, eps, None, None, None, lo, hi, ctypes.byref(nm), ctypes.byref(em),
+                            None) == E.EB_ERR_INVALID
+    i3 = lambda *v: (ctypes.c_int * 3)(*v)  # noqa: E731
+    has = ctypes.c_int()
+    assert lib.eb_regrid_box(2, i3(32, 32, 1), i3(0, 0, 0), i3(0, 0, 0), i3(1, 1, 0), i3(2, 2, 1), 1, 2, 0,
+                             lo, hi, ctypes.byref(has)) == E.EB_ERR_INVALID  # block < 1
+    assert lib.eb_regrid_box(4, i3(32, 32, 1), i3(0, 0, 0), i3(0, 0, 0), i3(1, 1, 0), i3(2, 2, 1), 1, 2, 4,
+                             lo, hi, ctypes.byref(has)) == E.EB_ERR_INVALID  # dim
