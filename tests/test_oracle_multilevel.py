@@ -8,9 +8,12 @@
 - exact conservation over three levels with the rod crossing the CF sides of
   both boxes (2D) and a pin crossing both boxes' top sides (3D);
 - proper nesting is enforced;
+- values under the boxes are the composed kappa-weighted means (exact for a
+  linear phi on regular cells);
 - planted mistakes: the inner pair keeping the coarse operator's own CF flux
   breaks conservation; the inner pair scaled by the outer pair's spacing
-  breaks exactness.
+  breaks exactness; means not composed through the inner box break the
+  composition pin.
 """
 import numpy as np
 import pytest
@@ -145,3 +148,53 @@ def test_four_levels_quadratic_exactness_and_conservation_2d():
     assert rel <= 1e-12
     d = W.rod_plane_2d(32)
     assert _conservation_gap(MultiLevel(d, [([8, 8], [24, 24])] * 3)) <= 1e-12
+
+
+def test_values_under_boxes_are_composed_means():
+    """A linear phi given on every level's own cells: split() reports, under
+    each box, the kappa-weighted mean of the children, composed level by
+    level, which for a linear phi on regular cells is phi at the cell centre
+    exactly.  Level 0 cells under box 2 get their values only through level
+    1's means, so a map that skipped the composition would report 0 there."""
+    M = MultiLevel(_sphere_2d(), [([12, 12], [28, 28]), ([4, 8], [28, 24])])
+
+    def lin(x, y, z):
+        return 0.3 + 1.7 * x - 0.9 * y
+    phis = []
+    for g in M.g:
+        X, Y, Z = g.cell_centres()
+        phis.append(np.stack([lin(X, Y, Z)] * 2))
+    out = M.split(M.join(phis))
+    g0 = M.g[0]
+    X, Y, Z = g0.cell_centres()
+    m = (g0.dof[0] >= 0) & M.under(0) & (g0.kappa[0] == 1.0)
+    # level-0 cells whose children are under box 2: box 2 covers level-1 cells [4, 28) x [8, 24),
+    # i.e. level-0 cells [14, 26) x [16, 24)
+    deep = m & (X > (12 + 2) / 32) & (X < (12 + 14) / 32) & (Y > (12 + 4) / 32) & (Y < (12 + 12) / 32)
+    assert deep.sum() > 0
+    assert np.abs(out[0][0][m] - lin(X, Y, Z)[m]).max() <= 1e-13
+
+
+def test_planted_uncomposed_means_fail_the_composition_pin():
+    """Plant a mistake in the oracle: level 0's values under box 1 taken from
+    level 1's own unknowns alone (no composition through box 2).  The
+    composition pin must then fail."""
+    import scipy.sparse as sp
+    M = MultiLevel(_sphere_2d(), [([12, 12], [28, 28]), ([4, 8], [28, 24])])
+    g1, own1 = M.g[1], M.own[1]
+    E1 = sp.csr_matrix((np.ones(len(own1)), (own1, M.off[1] + np.arange(len(own1)))), shape=(g1.ndof, M.n))
+    own0 = M.own[0]
+    E0 = sp.csr_matrix((np.ones(len(own0)), (own0, M.off[0] + np.arange(len(own0)))), shape=(M.g[0].ndof, M.n))
+    M.T[0] = (E0 + M.M[0] @ E1).tocsr()
+
+    def lin(x, y, z):
+        return 0.3 + 1.7 * x - 0.9 * y
+    phis = []
+    for g in M.g:
+        X, Y, Z = g.cell_centres()
+        phis.append(np.stack([lin(X, Y, Z)] * 2))
+    out = M.split(M.join(phis))
+    g0 = M.g[0]
+    X, Y, Z = g0.cell_centres()
+    m = (g0.dof[0] >= 0) & M.under(0) & (g0.kappa[0] == 1.0)
+    assert np.abs(out[0][0][m] - lin(X, Y, Z)[m]).max() > 1e-3
