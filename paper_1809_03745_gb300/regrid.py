@@ -38,6 +38,12 @@ def cf_sides(boxes, parent_n, D):
             [int(hi[a] < parent_n[a]) if a < D else 0 for a in range(3)])
 
 
+def same_boxes(a, b):
+    """Do two box lists place the same levels (box l of a equals box l of b for every l)?"""
+    key = lambda bs: [([int(v) for v in lo], [int(v) for v in hi]) for lo, hi in bs]  # noqa: E731
+    return len(a) == len(b) and key(a) == key(b)
+
+
 def _grow(box, n, cflo, cfhi, D, block):
     """The box with every side that is not at its limit moved out by `block` cells (None if none can)."""
     lo, hi = list(box[0]), list(box[1])
@@ -107,6 +113,5 @@ def build_hierarchy(desc, source, *, max_levels=3, eps=PAPER_EPS, buf=2, block=4
         Ef = H.field(H.L - 1, phis[-1])[0]
         # the earlier finer box is kept only while the grid it sits on is unchanged
         k = len(boxes)
-        same_grid = keep and len(keep) > k and [list(b) for b in keep[k - 1]] == [list(b) for b in boxes[-1]]
-        keep_box = keep[k] if same_grid else None
+        keep_box = keep[k] if keep and len(keep) > k and same_boxes(keep[:k], boxes) else None
     return dict(hierarchy=H, boxes=boxes, phis=phis, info=info, steps=steps)

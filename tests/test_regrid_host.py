@@ -84,3 +84,12 @@ def test_tag_and_box_calls_refuse_bad_arguments_without_device_work():
                              lo, hi, ctypes.byref(has)) == E.EB_ERR_INVALID  # block < 1
     assert lib.eb_regrid_box(4, i3(32, 32, 1), i3(0, 0, 0), i3(0, 0, 0), i3(1, 1, 0), i3(2, 2, 1), 1, 2, 4,
                              lo, hi, ctypes.byref(has)) == E.EB_ERR_INVALID  # dim
+
+
+def test_keep_rule_needs_every_coarser_box_unchanged():
+    from paper_1809_03745_gb300 import regrid as R
+    a = [([8, 8], [24, 24]), ([4, 4], [20, 28])]
+    assert R.same_boxes(a[:1], [([8, 8], [24, 24])])
+    assert R.same_boxes(a, [((8, 8), (24, 24)), ((4, 4), (20, 28))])
+    assert not R.same_boxes(a, [([8, 8], [24, 28]), ([4, 4], [20, 28])])  # level 1 moved: level 2's grid differs
+    assert not R.same_boxes(a, a[:1])
