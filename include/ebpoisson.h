@@ -455,7 +455,8 @@ eb_status eb_amr_residual_levels(eb_amr* A, const double* const* d_rhs, const do
  * restricted under the boxes, constant per parent on level 1, then on every
  * finer level a correction of what remains there with zero Dirichlet data on
  * its CF sides), each correction one V-cycle of the persistent multigrid
- * solve.  d_phi holds the guess on entry; on return every level's values
+ * solve (3+3 sweeps, a relaxed bottom at most 32 sweeps).  d_phi holds the
+ * guess on entry; on return every level's values
  * under the next finer box hold the finer means.  info as eb_amr_solve. */
 eb_status eb_amr_solve_levels(eb_amr* A, const double* const* d_rhs, const double* const* d_sig,
                               double* const* d_phi, eb_solve_info* info, void* stream);
